@@ -1,0 +1,281 @@
+/*
+ * bgv.h -- C ABI of the GB300 BigGraphVis hot-path library (libbgv.so).
+ *
+ * The method: Moradi & Mondal, "BigGraphVis: Leveraging Streaming Algorithms
+ * and GPU Acceleration for Visualizing Big Graphs" (arXiv 2108.00529).  The
+ * library computes, on one GPU,
+ *   1. a count-min sketch of node degrees (Algorithm 2, Section 3.3),
+ *   2. streaming community labels over a few rounds on the edge list
+ *      (Algorithm 3, Section 3.2.1),
+ *   3. the supergraph: communities as supernodes with sketched sizes as
+ *      masses, cut edges merged into weighted superedges (Section 4.1),
+ *   4. ForceAtlas2 iterations on that supergraph (Section 3.1, Algorithm 1):
+ *      Barnes-Hut repulsion on a quadtree, attraction along weighted edges,
+ *      gravity, per-node swing and an adaptive global speed.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.   Array arguments are DEVICE pointers owned by the caller, unless
+ *             the entry point's name ends in _host.  The library never keeps a
+ *             pointer after the call's work on `stream` has finished.
+ * Streams.    `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *             default stream).  Calls only enqueue work; they do not
+ *             synchronise, except bgv_status, bgv_fa2_read_stats and the
+ *             bgv_layout* pipeline calls (documented there).
+ * Scratch.    The library allocates no memory.  Each stage takes a caller
+ *             workspace `ws` of `ws_bytes` bytes (256-byte aligned), sized by
+ *             the matching *_ws_size query.  The first 256 bytes of every
+ *             workspace hold a status word and counters; the rest is scratch
+ *             whose contents do not outlive the call, except where stated
+ *             (bgv_fa2_step keeps per-step statistics there).
+ * Status.     Every call returns an int: BGV_OK, or an error detected on the
+ *             host before any work is enqueued (BGV_EINVAL, BGV_ENOSPC), or
+ *             BGV_ECUDA when a launch fails.  Errors found on the device (an
+ *             edge endpoint outside [0, n), a label outside [0, n), a tree
+ *             deeper than the traversal stack) are OR-ed into the status word
+ *             in the workspace as BGV_DEV_* bits; read them with bgv_status.
+ *             Outputs of a call whose status word is non-zero are undefined.
+ * Sizes.      Data-dependent sizes (K communities, Es superedges) are written
+ *             to device int64 scalars, so a chain of calls needs no host
+ *             round trip.  Callers size outputs by their upper bounds
+ *             (K <= n, Es <= m).
+ * Edges.      An int32 array of m (u, v) pairs, 8 bytes per edge, row-major.
+ *             Undirected; each edge listed once; self-loops are allowed (they
+ *             count twice toward their node's degree and never move labels or
+ *             form superedges).  The pointer must be 16-byte aligned.
+ * Determinism. Integer outputs are unique and bit-exact (independent of
+ *             thread scheduling).  The ForceAtlas2 step is deterministic too:
+ *             the tree's opening decisions use exact integer moments, and all
+ *             sums run in a fixed order.
+ */
+#ifndef BGV_H
+#define BGV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BGV_OK 0
+#define BGV_EINVAL 1   /* bad size, null pointer, misaligned pointer or parameter */
+#define BGV_ENOSPC 2   /* ws_bytes smaller than the *_ws_size query */
+#define BGV_EDEVICE 3  /* the device reported an error (see the status word) */
+#define BGV_ECUDA 4    /* a CUDA launch or copy failed */
+
+/* Bits of the device status word. */
+#define BGV_DEV_BADEDGE 1u     /* an edge endpoint outside [0, n) */
+#define BGV_DEV_BADLABEL 2u    /* a label outside [0, n) */
+#define BGV_DEV_STACK 4u       /* Barnes-Hut traversal stack exhausted */
+
+/* Library version, (major << 16) | minor. */
+int bgv_version(void);
+
+/* Human-readable name of a return code. */
+const char *bgv_strerror(int code);
+
+/* Zero the 256-byte header (status word and counters) of a new workspace.
+ * Call once per workspace before its first use (or zero-fill it yourself). */
+int bgv_ws_init(void *ws, void *stream);
+
+/* Synchronise `stream` and return the device status word of workspace `ws`
+ * in *out (0 = no device error).  `clear` != 0 resets it to 0 afterwards. */
+int bgv_status(void *ws, void *stream, uint32_t *out, int clear);
+
+/* ------------------------------------------------------------------------
+ * 1. Degree count-min sketch (Algorithm 2; Section 3.3; Section 4.1).
+ *
+ * Hash family: h_i(x) = ((a_i x + b_i) mod (2^31 - 1)) mod width, where row i
+ * draws a_i = 1 + z1 mod (2^31 - 2) and b_i = z2 mod (2^31 - 1) from two
+ * SplitMix64 outputs of state seed + i.
+ * Every endpoint of every edge adds 1 to sketch[i][h_i(endpoint)] for all
+ * rows i; then deg_est[v] = min_i sketch[i][h_i(v)] (never below the true
+ * degree).
+ *   edges    [m][2] int32, 16-byte aligned      (in)
+ *   sketch   [rows][width] uint32, row-major     (out)
+ *   deg_est  [n] uint32                          (out)
+ * Limits: 0 <= m < 2^31, 1 <= n < 2^31 - 1, 1 <= rows <= 16, 1 <= width.
+ * ---------------------------------------------------------------------- */
+size_t bgv_sketch_degrees_ws_size(int64_t m, int32_t n, int32_t rows, int32_t width);
+int bgv_sketch_degrees(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width,
+                       uint64_t seed, uint32_t *sketch, uint32_t *deg_est,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * 2. Community rounds (Algorithm 3; Section 3.2.1; Section 4.2.2).
+ *
+ * labels[v] = v and d[v] = deg_est[v] to start; D = threshold (0 means the
+ * average degree floor(2m / n), Algorithm 3's first line).  Each of `passes`
+ * rounds reads labels and degrees as they stood at the start of the round.
+ * An edge (u, v), u != v, is skipped unless d[u] <= D and d[v] <= D and the
+ * labels differ; the endpoint with the smaller degree is proposed to take
+ * the other's label; on equal degrees nothing happens (tie_mode 0) or the
+ * lower id takes the higher id's label (tie_mode 1).  At the end of the
+ * round each node with proposals takes the one from the lowest edge index
+ * and its degree grows by 1 (saturating).  Then D = min(D * growth, 2^32-1).
+ *   deg_est  [n] uint32 (in)     labels [n] int32 (out)
+ *   deg_out  [n] uint32 (out, optional: final degrees, may be NULL)
+ * Limits: passes >= 0, growth >= 1, tie_mode in {0, 1}.
+ * ---------------------------------------------------------------------- */
+size_t bgv_communities_ws_size(int64_t m, int32_t n);
+int bgv_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est,
+                    int32_t passes, uint32_t threshold, uint32_t growth, int32_t tie_mode,
+                    int32_t *labels, uint32_t *deg_out, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * 3. Supergraph (Section 4.1; Algorithm 3, "compute community sizes" and
+ *    ForceAtlas2(Csrc, Cdst, Csize)).
+ *
+ * Supernodes are the distinct labels numbered in ascending label order:
+ * node_map[v] = rank of labels[v]; *K_dev = number of distinct labels.
+ * Superedges: the multiset {(min(map u, map v), max(...)) : labels[u] !=
+ * labels[v]} sorted ascending and collapsed: ssrc[s] < sdst[s], sw[s] =
+ * multiplicity; *Es_dev = count.  Community size: a count-min sketch (same
+ * hash family, rows, width, seed) where every node v adds deg_est[v] at
+ * h_i(labels[v]); mass[k] = 1 + min_i over the sketch at h_i(label of k),
+ * saturated at 2^32 - 1.  Symmetric CSR: csr_off[K+1]; row k lists its
+ * neighbours in ascending order in csr_adj with weights csr_w.
+ *   node_map [n] int32;  ssrc, sdst [m] int32; sw [m] uint32;
+ *   mass [n] uint32; csr_off [n+1] int32; csr_adj [2m] int32;
+ *   csr_w [2m] uint32; K_dev, Es_dev: one int64 each.
+ *   Optional (NULL allowed): vol [n] uint64 (exact sum of deg_est per
+ *   supernode), count [n] uint32 (nodes per supernode), comm_label [n] int32
+ *   (the label of each supernode).
+ * Entries past K / Es / 2 Es / K+1 are left undefined.
+ * ---------------------------------------------------------------------- */
+size_t bgv_supergraph_ws_size(int64_t m, int32_t n, int32_t rows, int32_t width);
+int bgv_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *labels,
+                   const uint32_t *deg_est, int32_t rows, int32_t width, uint64_t seed,
+                   int32_t *node_map, int64_t *K_dev, int32_t *ssrc, int32_t *sdst, uint32_t *sw,
+                   int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
+                   uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * 4. ForceAtlas2 (Section 3.1; Algorithm 1; the force model and adaptive
+ *    speed of Jacomy et al. 2014 that the paper's implementation follows).
+ *
+ * Forces on supernode i with mass m_i (FP32):
+ *   repulsion  kr m_i m_j (p_i - p_j) / |p_i - p_j|^2 summed over Barnes-Hut
+ *              cells and leaf bodies (zero for coincident points);
+ *   attraction -sum_j w_ij (p_i - p_j) over CSR neighbours;
+ *   gravity    -kg m_i p_i / |p_i| (strong_gravity: -kg m_i p_i).
+ * Step: swing_i = |F_i - Fprev_i|, traction_i = |F_i + Fprev_i| / 2;
+ * S = sum m_i swing_i, T = sum m_i traction_i in FP64 (pairwise within a
+ * block, Kahan-compensated across blocks); if S > 0,
+ * speed += min(tau T / S - speed, speed / 2); then
+ * s_i = ks speed / (1 + speed sqrt(swing_i)), capped at ksmax / |F_i|;
+ * p_i += s_i F_i; Fprev = F.
+ * Quadtree: frame lo = min p, side = max extent * (1 + 2^-20); body fixed
+ * point U = trunc((p - lo) / side * 2^32); Morton key over the top
+ * max_depth bits of U; a cell splits while it holds more than leaf_cap
+ * bodies and is above max_depth.  A cell containing the body is opened; a
+ * leaf is summed body by body; otherwise the cell is accepted iff
+ * (side 2^-level)^2 < theta^2 |p_i - c|^2, all in FP32, where c is the
+ * cell's centre of mass from exact integer moments of U.
+ * Layout: pos, F, Fprev are [K][2] float (x, y interleaved), 8-byte aligned.
+ * ---------------------------------------------------------------------- */
+typedef struct bgv_fa2_params {
+    float theta;            /* Barnes-Hut opening parameter (1.2) */
+    float kr;               /* repulsion scaling (2.0; the paper's runs used 80) */
+    float kg;               /* gravity (1.0) */
+    float tau;              /* jitter tolerance (1.0) */
+    float ks;               /* local speed constant (0.1) */
+    float ksmax;            /* local speed cap constant (10.0) */
+    int32_t strong_gravity; /* 0 or 1 (0) */
+    int32_t leaf_cap;       /* bodies per leaf, >= 1 (1) */
+    int32_t max_depth;      /* quadtree levels, 1..24 (24) */
+    int32_t reserved;       /* must be 0 */
+    uint64_t seed;          /* initial positions (1) */
+} bgv_fa2_params;
+
+/* Per-step statistics kept in the FA2 workspace. */
+typedef struct bgv_fa2_stats {
+    double S;                   /* sum of m_i swing_i, last step */
+    double T;                   /* sum of m_i traction_i, last step */
+    uint64_t interactions;      /* body-cell plus body-body terms, last step */
+    uint64_t tree_nodes;        /* quadtree internal nodes, last step */
+    uint32_t status;            /* device status word */
+    uint32_t reserved;
+} bgv_fa2_stats;
+
+void bgv_fa2_default_params(bgv_fa2_params *p);
+
+/* Initial state: pos[i] per axis = U * 2 R - R with R = sqrt(K) and U the top
+ * 24 bits of SplitMix64 at state seed + 2 i + axis (FP32); Fprev = 0;
+ * *speed = 1 (device double). */
+int bgv_fa2_init(int64_t K, const bgv_fa2_params *p, float *pos, float *Fprev, double *speed, void *stream);
+
+/* Workspace for bodies K and CSR entries nnz (= csr_off[K]). */
+size_t bgv_fa2_ws_size(int64_t K, int64_t nnz);
+
+/* Forces only, at positions pos, without changing any state:
+ * Fr, Fa, Fg [K][2] float (repulsion, attraction, gravity); any may be NULL. */
+int bgv_fa2_forces(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                   const uint32_t *mass, const bgv_fa2_params *p, const float *pos,
+                   float *Fr, float *Fa, float *Fg, void *ws, size_t ws_bytes, void *stream);
+
+/* One iteration in place: F receives the total force, pos/Fprev/speed are
+ * advanced.  Statistics of the step stay in `ws` (bgv_fa2_read_stats). */
+int bgv_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                 const uint32_t *mass, const bgv_fa2_params *p, float *pos, float *F, float *Fprev,
+                 double *speed, void *ws, size_t ws_bytes, void *stream);
+
+/* `iterations` steps; with use_graph != 0 one step is captured into a CUDA
+ * graph on `stream` and replayed (the stream must not be capturing). */
+int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, int32_t use_graph,
+                float *pos, float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronise `stream` and copy the statistics of the last step. */
+int bgv_fa2_read_stats(void *ws, void *stream, bgv_fa2_stats *out);
+
+/* ------------------------------------------------------------------------
+ * 5. The whole pipeline (Algorithm 3 end to end): sketch, rounds,
+ *    supergraph, initial positions and `iterations` ForceAtlas2 steps.
+ * ---------------------------------------------------------------------- */
+typedef struct bgv_layout_params {
+    int32_t rows;        /* sketch rows (4) */
+    int32_t width;       /* sketch columns (4096) */
+    uint64_t seed;       /* hash seed (1) */
+    int32_t passes;      /* community rounds (3) */
+    uint32_t threshold;  /* degree threshold; 0 = floor(2m / n) (0) */
+    uint32_t growth;     /* threshold factor per round (2) */
+    int32_t tie_mode;    /* 0 or 1 (0) */
+    int32_t iterations;  /* ForceAtlas2 steps (200) */
+    int32_t use_graph;   /* replay the FA2 step as a CUDA graph (1) */
+    bgv_fa2_params fa2;
+} bgv_layout_params;
+
+void bgv_layout_default_params(bgv_layout_params *p);
+
+/* Workspace for the device pipeline; it holds every intermediate
+ * (sketch, degrees, labels, supergraph, CSR, FA2 state and scratch). */
+size_t bgv_layout_ws_size(int64_t m, int32_t n, const bgv_layout_params *p);
+
+/* Device pipeline.  Synchronises `stream` once, after the supergraph, to
+ * learn K and Es (returned in *K_out, *Es_out, host int64), and once at the
+ * end.  Outputs: node_map [n] int32 (supernode of every node), xy [n][2]
+ * float (first K rows valid), radius [n] float (sqrt of mass, first K
+ * valid).  Returns BGV_EDEVICE if the device reported a bad edge. */
+int bgv_layout(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_params *p,
+               int32_t *node_map, float *xy, float *radius, int64_t *K_out, int64_t *Es_out,
+               void *ws, size_t ws_bytes, void *stream);
+
+/* The same pipeline from HOST memory: copies h_edges (pinned memory
+ * recommended) into the workspace, runs bgv_layout, copies node_map, xy and
+ * radius back to the host arrays, and synchronises `stream`. */
+int bgv_layout_host(const int32_t *h_edges, int64_t m, int32_t n, const bgv_layout_params *p,
+                    int32_t *h_node_map, float *h_xy, float *h_radius, int64_t *K_out, int64_t *Es_out,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace for bgv_layout_host: bgv_layout_ws_size plus room for the edges
+ * and the outputs. */
+size_t bgv_layout_host_ws_size(int64_t m, int32_t n, const bgv_layout_params *p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BGV_H */

@@ -476,8 +476,8 @@ static int32_t tree_build(otree *t, int32_t level, int64_t start, int64_t end)
     c.cx = sx / (double)c.M;
     c.cy = sy / (double)c.M;
     {
-        uint32_t qx = (uint32_t)(c.SX / (u128)c.M);
-        uint32_t qy = (uint32_t)(c.SY / (u128)c.M);
+        uint32_t qx = c.M ? (uint32_t)(c.SX / (u128)c.M) : 0u;
+        uint32_t qy = c.M ? (uint32_t)(c.SY / (u128)c.M) : 0u;
         float fx = (float)qx;
         float fy = (float)qy;
         float ux = fx * 0x1p-32f;

@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libbgv.so (the C ABI declared in include/bgv.h).
+
+Argument marshalling only: every function has the C name, converts torch
+tensors to their device pointers (``None`` -> NULL), passes the current CUDA
+stream when none is given, and raises :class:`BgvError` on a non-zero return
+code.  All work happens in the CUDA kernels of the library.  Importing this
+module raises if the library has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import pathlib
+
+import torch
+
+_LIB_PATH = pathlib.Path(__file__).resolve().parent / "libbgv.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"libbgv.so not found at {_LIB_PATH}; build it with paper_2108_00529_gb300.build.build()")
+_lib = C.CDLL(str(_LIB_PATH))
+
+BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA = 0, 1, 2, 3, 4
+BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_STACK = 1, 2, 4
+
+P = C.c_void_p
+i32, i64, u32, u64, sz = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t
+
+
+class bgv_fa2_params(C.Structure):
+    _fields_ = [("theta", C.c_float), ("kr", C.c_float), ("kg", C.c_float), ("tau", C.c_float),
+                ("ks", C.c_float), ("ksmax", C.c_float), ("strong_gravity", i32), ("leaf_cap", i32),
+                ("max_depth", i32), ("reserved", i32), ("seed", u64)]
+
+
+class bgv_fa2_stats(C.Structure):
+    _fields_ = [("S", C.c_double), ("T", C.c_double), ("interactions", u64), ("tree_nodes", u64),
+                ("status", u32), ("reserved", u32)]
+
+
+class bgv_layout_params(C.Structure):
+    _fields_ = [("rows", i32), ("width", i32), ("seed", u64), ("passes", i32), ("threshold", u32),
+                ("growth", u32), ("tie_mode", i32), ("iterations", i32), ("use_graph", i32),
+                ("fa2", bgv_fa2_params)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("bgv_version", C.c_int, [])
+_sig("bgv_strerror", C.c_char_p, [C.c_int])
+_sig("bgv_ws_init", C.c_int, [P, P])
+_sig("bgv_status", C.c_int, [P, P, C.POINTER(u32), C.c_int])
+_sig("bgv_sketch_degrees_ws_size", sz, [i64, i32, i32, i32])
+_sig("bgv_sketch_degrees", C.c_int, [P, i64, i32, i32, i32, u64, P, P, P, sz, P])
+_sig("bgv_communities_ws_size", sz, [i64, i32])
+_sig("bgv_communities", C.c_int, [P, i64, i32, P, i32, u32, u32, i32, P, P, P, sz, P])
+_sig("bgv_supergraph_ws_size", sz, [i64, i32, i32, i32])
+_sig("bgv_supergraph", C.c_int, [P, i64, i32, P, P, i32, i32, u64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, sz, P])
+_sig("bgv_fa2_default_params", None, [C.POINTER(bgv_fa2_params)])
+_sig("bgv_fa2_init", C.c_int, [i64, C.POINTER(bgv_fa2_params), P, P, P, P])
+_sig("bgv_fa2_ws_size", sz, [i64, i64])
+_sig("bgv_fa2_forces", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
+_sig("bgv_fa2_step", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
+_sig("bgv_fa2_run", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P, sz, P])
+_sig("bgv_fa2_read_stats", C.c_int, [P, P, C.POINTER(bgv_fa2_stats)])
+_sig("bgv_layout_default_params", None, [C.POINTER(bgv_layout_params)])
+_sig("bgv_layout_ws_size", sz, [i64, i32, C.POINTER(bgv_layout_params)])
+_sig("bgv_layout", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, P, P, C.POINTER(i64), C.POINTER(i64),
+                             P, sz, P])
+_sig("bgv_layout_host_ws_size", sz, [i64, i32, C.POINTER(bgv_layout_params)])
+_sig("bgv_layout_host", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, P, P, C.POINTER(i64),
+                                  C.POINTER(i64), P, sz, P])
+
+#: every symbol this binding resolves from the library
+EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees",
+           "bgv_communities_ws_size", "bgv_communities", "bgv_supergraph_ws_size", "bgv_supergraph",
+           "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
+           "bgv_fa2_run", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
+           "bgv_layout_host_ws_size", "bgv_layout_host"]
+
+
+class BgvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {_lib.bgv_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _chk(code: int, where: str):
+    if code != BGV_OK:
+        raise BgvError(code, where)
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return x.data_ptr()
+    return int(x)
+
+
+def _s(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _nbytes(ws, ws_bytes):
+    if ws_bytes is not None:
+        return int(ws_bytes)
+    return ws.numel() * ws.element_size()
+
+
+def alloc_ws(nbytes: int, device="cuda") -> torch.Tensor:
+    """A caller-owned workspace tensor (uint8, 256-byte aligned) whose
+    header has been zeroed with bgv_ws_init."""
+    t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    bgv_ws_init(t)
+    return t
+
+
+# ----------------------------------------------------------------- C names
+def bgv_version() -> int:
+    return _lib.bgv_version()
+
+
+def bgv_strerror(code: int) -> str:
+    return _lib.bgv_strerror(code).decode()
+
+
+def bgv_ws_init(ws, stream=None):
+    _chk(_lib.bgv_ws_init(_p(ws), _s(stream)), "bgv_ws_init")
+
+
+def bgv_status(ws, stream=None, clear: bool = False) -> int:
+    out = u32(0)
+    _chk(_lib.bgv_status(_p(ws), _s(stream), C.byref(out), 1 if clear else 0), "bgv_status")
+    return out.value
+
+
+def bgv_sketch_degrees_ws_size(m: int, n: int, rows: int, width: int) -> int:
+    return _lib.bgv_sketch_degrees_ws_size(m, n, rows, width)
+
+
+def bgv_sketch_degrees(edges, m, n, rows, width, seed, sketch, deg_est, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_sketch_degrees(_p(edges), m, n, rows, width, seed, _p(sketch), _p(deg_est), _p(ws),
+                                 _nbytes(ws, ws_bytes), _s(stream)), "bgv_sketch_degrees")
+
+
+def bgv_communities_ws_size(m: int, n: int) -> int:
+    return _lib.bgv_communities_ws_size(m, n)
+
+
+def bgv_communities(edges, m, n, deg_est, passes, threshold, growth, tie_mode, labels, deg_out, ws,
+                    ws_bytes=None, stream=None):
+    _chk(_lib.bgv_communities(_p(edges), m, n, _p(deg_est), passes, threshold, growth, tie_mode, _p(labels),
+                              _p(deg_out), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_communities")
+
+
+def bgv_supergraph_ws_size(m: int, n: int, rows: int, width: int) -> int:
+    return _lib.bgv_supergraph_ws_size(m, n, rows, width)
+
+
+def bgv_supergraph(edges, m, n, labels, deg_est, rows, width, seed, node_map, K_dev, ssrc, sdst, sw, Es_dev, mass,
+                   csr_off, csr_adj, csr_w, vol, count, comm_label, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_supergraph(_p(edges), m, n, _p(labels), _p(deg_est), rows, width, seed, _p(node_map), _p(K_dev),
+                             _p(ssrc), _p(sdst), _p(sw), _p(Es_dev), _p(mass), _p(csr_off), _p(csr_adj), _p(csr_w),
+                             _p(vol), _p(count), _p(comm_label), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_supergraph")
+
+
+def bgv_fa2_default_params() -> bgv_fa2_params:
+    p = bgv_fa2_params()
+    _lib.bgv_fa2_default_params(C.byref(p))
+    return p
+
+
+def bgv_fa2_init(K, params, pos, Fprev, speed, stream=None):
+    _chk(_lib.bgv_fa2_init(K, C.byref(params), _p(pos), _p(Fprev), _p(speed), _s(stream)), "bgv_fa2_init")
+
+
+def bgv_fa2_ws_size(K: int, nnz: int) -> int:
+    return _lib.bgv_fa2_ws_size(K, nnz)
+
+
+def bgv_fa2_forces(K, csr_off, csr_adj, csr_w, mass, params, pos, Fr, Fa, Fg, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_fa2_forces(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(Fr),
+                             _p(Fa), _p(Fg), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_forces")
+
+
+def bgv_fa2_step(K, csr_off, csr_adj, csr_w, mass, params, pos, F, Fprev, speed, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_fa2_step(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(F),
+                           _p(Fprev), _p(speed), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_step")
+
+
+def bgv_fa2_run(K, csr_off, csr_adj, csr_w, mass, params, iterations, use_graph, pos, F, Fprev, speed, ws,
+                ws_bytes=None, stream=None):
+    _chk(_lib.bgv_fa2_run(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
+                          1 if use_graph else 0, _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws),
+                          _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_run")
+
+
+def bgv_fa2_read_stats(ws, stream=None) -> bgv_fa2_stats:
+    st = bgv_fa2_stats()
+    _chk(_lib.bgv_fa2_read_stats(_p(ws), _s(stream), C.byref(st)), "bgv_fa2_read_stats")
+    return st
+
+
+def bgv_layout_default_params() -> bgv_layout_params:
+    p = bgv_layout_params()
+    _lib.bgv_layout_default_params(C.byref(p))
+    return p
+
+
+def bgv_layout_ws_size(m: int, n: int, params) -> int:
+    return _lib.bgv_layout_ws_size(m, n, C.byref(params))
+
+
+def bgv_layout(edges, m, n, params, node_map, xy, radius, ws, ws_bytes=None, stream=None):
+    """Returns ``(K, Es)``."""
+    K, Es = i64(0), i64(0)
+    _chk(_lib.bgv_layout(_p(edges), m, n, C.byref(params), _p(node_map), _p(xy), _p(radius), C.byref(K),
+                         C.byref(Es), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_layout")
+    return K.value, Es.value
+
+
+def bgv_layout_host_ws_size(m: int, n: int, params) -> int:
+    return _lib.bgv_layout_host_ws_size(m, n, C.byref(params))
+
+
+def bgv_layout_host(h_edges, m, n, params, h_node_map, h_xy, h_radius, ws, ws_bytes=None, stream=None):
+    """Host buffers (CPU tensors, ideally pinned); returns ``(K, Es)``."""
+    K, Es = i64(0), i64(0)
+    _chk(_lib.bgv_layout_host(_p(h_edges), m, n, C.byref(params), _p(h_node_map), _p(h_xy), _p(h_radius),
+                              C.byref(K), C.byref(Es), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_layout_host")
+    return K.value, Es.value

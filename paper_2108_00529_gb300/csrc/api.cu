@@ -1,0 +1,457 @@
+// api.cu -- the extern "C" entry points declared in include/bgv.h.
+//
+// Host-side validation, workspace sizing and carving, and the pipeline that
+// chains the stages (Algorithm 3 end to end).  Everything on the data path
+// runs in the kernels of sketch.cu, communities.cu, supergraph.cu and fa2.cu.
+#include <math.h>
+#include <string.h>
+
+#include "bgv_internal.cuh"
+
+using namespace bgv;
+
+namespace {
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_graph(const int32_t *edges, int64_t m, int32_t n) {
+    if (n < 1 || n >= 0x7FFFFFFF || m < 0 || m >= (int64_t(1) << 31)) return BGV_EINVAL;
+    if (m > 0 && (!edges || !aligned(edges, 16))) return BGV_EINVAL;
+    return BGV_OK;
+}
+
+int check_sketch_shape(int32_t rows, int32_t width) {
+    if (rows < 1 || rows > kMaxRows || width < 1) return BGV_EINVAL;
+    return BGV_OK;
+}
+
+int check_ws(void *ws, size_t ws_bytes, size_t need) {
+    if (!ws || !aligned(ws, kAlign)) return BGV_EINVAL;
+    if (ws_bytes < need) return BGV_ENOSPC;
+    return BGV_OK;
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+size_t sketch_ws(int64_t m, int32_t n, int32_t rows, int32_t width) {
+    Carver c(nullptr, kHeaderBytes);
+    SketchScratch s;
+    carve_sketch(c, m, n, rows, width, s);
+    return c.used();
+}
+
+size_t comm_ws(int64_t m, int32_t n) {
+    Carver c(nullptr, kHeaderBytes);
+    CommScratch s;
+    carve_comm(c, m, n, s);
+    return c.used();
+}
+
+size_t super_ws(int64_t m, int32_t n, int32_t rows, int32_t width) {
+    Carver c(nullptr, kHeaderBytes);
+    SuperScratch s;
+    carve_super(c, m, n, rows, width, s);
+    return c.used();
+}
+
+// ------------------------------------------------------------- pipeline
+struct LayoutBuffers {
+    uint32_t *sketch, *deg_est;
+    int32_t *labels;
+    int64_t *K_dev, *Es_dev;
+    int32_t *ssrc, *sdst;
+    uint32_t *sw, *mass;
+    int32_t *csr_off, *csr_adj;
+    uint32_t *csr_w;
+    float *F, *Fprev;
+    double *speed;
+    char *scratch;  // shared by the stages, which run one after another
+};
+
+size_t stage_scratch_bytes(int64_t m, int32_t n, const bgv_layout_params *p) {
+    size_t need = 0;
+    {
+        Carver c(nullptr, 0);
+        SketchScratch s;
+        carve_sketch(c, m, n, p->rows, p->width, s);
+        need = c.used() > need ? c.used() : need;
+    }
+    {
+        Carver c(nullptr, 0);
+        CommScratch s;
+        carve_comm(c, m, n, s);
+        need = c.used() > need ? c.used() : need;
+    }
+    {
+        Carver c(nullptr, 0);
+        SuperScratch s;
+        carve_super(c, m, n, p->rows, p->width, s);
+        need = c.used() > need ? c.used() : need;
+    }
+    size_t f = fa2_scratch_bytes(n, 2 * m);
+    return f > need ? f : need;
+}
+
+void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, LayoutBuffers &b) {
+    const size_t nn = size_t(n), mm = size_t(m > 0 ? m : 1);
+    b.sketch = c.take<uint32_t>(size_t(p->rows) * size_t(p->width));
+    b.deg_est = c.take<uint32_t>(nn);
+    b.labels = c.take<int32_t>(nn);
+    b.K_dev = c.take<int64_t>(1);
+    b.Es_dev = c.take<int64_t>(1);
+    b.ssrc = c.take<int32_t>(mm);
+    b.sdst = c.take<int32_t>(mm);
+    b.sw = c.take<uint32_t>(mm);
+    b.mass = c.take<uint32_t>(nn);
+    b.csr_off = c.take<int32_t>(nn + 1);
+    b.csr_adj = c.take<int32_t>(2 * mm);
+    b.csr_w = c.take<uint32_t>(2 * mm);
+    b.F = c.take<float>(2 * nn);
+    b.Fprev = c.take<float>(2 * nn);
+    b.speed = c.take<double>(1);
+    b.scratch = c.take<char>(stage_scratch_bytes(m, n, p));
+}
+
+int check_layout_params(const bgv_layout_params *p) {
+    if (!p) return BGV_EINVAL;
+    BGV_TRY(check_sketch_shape(p->rows, p->width));
+    if (p->passes < 0 || p->growth < 1 || (p->tie_mode != 0 && p->tie_mode != 1) || p->iterations < 0)
+        return BGV_EINVAL;
+    return fa2_check_params(&p->fa2);
+}
+
+int fa2_loop(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *w, const uint32_t *mass,
+             const bgv_fa2_params &p, int32_t iterations, int32_t use_graph, float *pos, float *F, float *Fprev,
+             double *speed, WsHeader *hdr, void *scratch, cudaStream_t st) {
+    if (iterations <= 0 || K <= 0) return BGV_OK;
+    if (!use_graph || st == nullptr || iterations < 2) {
+        for (int32_t t = 0; t < iterations; ++t)
+            BGV_TRY(run_fa2(1, K, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
+                            scratch, st));
+        return BGV_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = run_fa2(1, K, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (rc != BGV_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc != BGV_OK ? rc : BGV_ECUDA;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return BGV_ECUDA;
+    }
+    rc = BGV_OK;
+    for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = BGV_ECUDA;
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
+__global__ void k_radius(const uint32_t *mass, const int64_t *K_dev, float *radius) {
+    const int64_t K = *K_dev;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < K; k += int64_t(gridDim.x) * blockDim.x)
+        radius[k] = sqrtf(__uint2float_rn(mass[k]));
+}
+
+int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_params *p, int32_t *node_map,
+                  float *xy, float *radius, int64_t *K_out, int64_t *Es_out, void *ws, cudaStream_t st,
+                  LayoutBuffers &b) {
+    WsHeader *hdr = header(ws);
+    uint32_t *status = &hdr->status;
+    const HashFamily h = make_hash_family(p->seed, p->rows, uint32_t(p->width));
+    BGV_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
+    {
+        Carver c(b.scratch, 0);
+        SketchScratch s;
+        carve_sketch(c, m, n, p->rows, p->width, s);
+        BGV_TRY(run_sketch(edges, m, n, h, b.sketch, b.deg_est, s, status, st));
+    }
+    {
+        Carver c(b.scratch, 0);
+        CommScratch s;
+        carve_comm(c, m, n, s);
+        uint32_t D = p->threshold ? p->threshold : uint32_t((2 * m) / n);
+        BGV_TRY(run_communities(edges, m, n, b.deg_est, p->passes, D, p->growth, p->tie_mode, b.labels, nullptr, s,
+                                status, st));
+    }
+    {
+        Carver c(b.scratch, 0);
+        SuperScratch s;
+        carve_super(c, m, n, p->rows, p->width, s);
+        BGV_TRY(run_supergraph(edges, m, n, b.labels, b.deg_est, h, node_map, b.K_dev, b.ssrc, b.sdst, b.sw,
+                               b.Es_dev, b.mass, b.csr_off, b.csr_adj, b.csr_w, nullptr, nullptr, nullptr, s, status,
+                               st));
+    }
+    int64_t KE[2] = {0, 0};
+    uint32_t dev_status = 0;
+    BGV_CUDA(cudaMemcpyAsync(&KE[0], b.K_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaMemcpyAsync(&KE[1], b.Es_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaMemcpyAsync(&dev_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    if (dev_status) return BGV_EDEVICE;
+    const int64_t K = KE[0];
+    if (K_out) *K_out = K;
+    if (Es_out) *Es_out = KE[1];
+    BGV_TRY(run_fa2_init(K, p->fa2, xy, b.Fprev, b.speed, st));
+    BGV_TRY(fa2_loop(K, b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
+                     b.Fprev, b.speed, hdr, b.scratch, st));
+    if (radius) {
+        k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
+        BGV_TRY(launch_status());
+    }
+    return BGV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bgv_version(void) { return (0 << 16) | 1; }
+
+const char *bgv_strerror(int code) {
+    switch (code) {
+        case BGV_OK: return "ok";
+        case BGV_EINVAL: return "invalid argument";
+        case BGV_ENOSPC: return "workspace too small";
+        case BGV_EDEVICE: return "device reported an error (see the status word)";
+        case BGV_ECUDA: return "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+int bgv_ws_init(void *ws, void *stream) {
+    if (!ws || !aligned(ws, kAlign)) return BGV_EINVAL;
+    BGV_CUDA(cudaMemsetAsync(ws, 0, kHeaderBytes, as_stream(stream)));
+    return BGV_OK;
+}
+
+int bgv_status(void *ws, void *stream, uint32_t *out, int clear) {
+    if (!ws || !out) return BGV_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    BGV_CUDA(cudaMemcpyAsync(out, status_ptr(ws), sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (clear) BGV_CUDA(cudaMemsetAsync(status_ptr(ws), 0, sizeof(uint32_t), st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    return BGV_OK;
+}
+
+size_t bgv_sketch_degrees_ws_size(int64_t m, int32_t n, int32_t rows, int32_t width) {
+    return sketch_ws(m, n, rows, width);
+}
+
+int bgv_sketch_degrees(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width, uint64_t seed,
+                       uint32_t *sketch, uint32_t *deg_est, void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    BGV_TRY(check_sketch_shape(rows, width));
+    if (!sketch || !deg_est) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, sketch_ws(m, n, rows, width)));
+    Carver c(ws, kHeaderBytes);
+    SketchScratch s;
+    carve_sketch(c, m, n, rows, width, s);
+    const HashFamily h = make_hash_family(seed, rows, uint32_t(width));
+    return run_sketch(edges, m, n, h, sketch, deg_est, s, status_ptr(ws), as_stream(stream));
+}
+
+size_t bgv_communities_ws_size(int64_t m, int32_t n) { return comm_ws(m, n); }
+
+int bgv_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
+                    void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    if (!deg_est || !labels || passes < 0 || growth < 1 || (tie_mode != 0 && tie_mode != 1)) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, comm_ws(m, n)));
+    Carver c(ws, kHeaderBytes);
+    CommScratch s;
+    carve_comm(c, m, n, s);
+    const uint32_t D = threshold ? threshold : uint32_t((2 * m) / n);
+    return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, labels, deg_out, s, status_ptr(ws),
+                           as_stream(stream));
+}
+
+size_t bgv_supergraph_ws_size(int64_t m, int32_t n, int32_t rows, int32_t width) {
+    return super_ws(m, n, rows, width);
+}
+
+int bgv_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *labels, const uint32_t *deg_est,
+                   int32_t rows, int32_t width, uint64_t seed, int32_t *node_map, int64_t *K_dev, int32_t *ssrc,
+                   int32_t *sdst, uint32_t *sw, int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
+                   uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label, void *ws, size_t ws_bytes,
+                   void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    BGV_TRY(check_sketch_shape(rows, width));
+    if (!labels || !deg_est || !node_map || !K_dev || !ssrc || !sdst || !sw || !Es_dev || !mass || !csr_off ||
+        !csr_adj || !csr_w)
+        return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, super_ws(m, n, rows, width)));
+    Carver c(ws, kHeaderBytes);
+    SuperScratch s;
+    carve_super(c, m, n, rows, width, s);
+    const HashFamily h = make_hash_family(seed, rows, uint32_t(width));
+    return run_supergraph(edges, m, n, labels, deg_est, h, node_map, K_dev, ssrc, sdst, sw, Es_dev, mass, csr_off,
+                          csr_adj, csr_w, vol, count, comm_label, s, status_ptr(ws), as_stream(stream));
+}
+
+void bgv_fa2_default_params(bgv_fa2_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->theta = 1.2f;
+    p->kr = 2.0f;
+    p->kg = 1.0f;
+    p->tau = 1.0f;
+    p->ks = 0.1f;
+    p->ksmax = 10.0f;
+    p->strong_gravity = 0;
+    p->leaf_cap = 1;
+    p->max_depth = 24;
+    p->seed = 1;
+}
+
+int bgv_fa2_init(int64_t K, const bgv_fa2_params *p, float *pos, float *Fprev, double *speed, void *stream) {
+    if (K < 0 || K >= 0x7FFFFFFF || !speed || (K > 0 && (!pos || !Fprev))) return BGV_EINVAL;
+    BGV_TRY(fa2_check_params(p));
+    return run_fa2_init(K, *p, pos, Fprev, speed, as_stream(stream));
+}
+
+size_t bgv_fa2_ws_size(int64_t K, int64_t nnz) { return kHeaderBytes + fa2_scratch_bytes(K, nnz); }
+
+static int check_fa2_args(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *w,
+                          const uint32_t *mass, const bgv_fa2_params *p, const float *pos, void *ws,
+                          size_t ws_bytes) {
+    if (K < 0 || K >= 0x7FFFFFFF) return BGV_EINVAL;
+    BGV_TRY(fa2_check_params(p));
+    if (K == 0) return BGV_OK;
+    if (!off || !adj || !w || !mass || !pos || !aligned(pos, 8)) return BGV_EINVAL;
+    return check_ws(ws, ws_bytes, bgv_fa2_ws_size(K, 0));
+}
+
+int bgv_fa2_forces(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                   const uint32_t *mass, const bgv_fa2_params *p, const float *pos, float *Fr, float *Fa, float *Fg,
+                   void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    if (K == 0) return BGV_OK;
+    return run_fa2(0, K, csr_off, csr_adj, csr_w, mass, *p, const_cast<float *>(pos), nullptr, nullptr, nullptr, Fr,
+                   Fa, Fg, header(ws), static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
+}
+
+int bgv_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                 const uint32_t *mass, const bgv_fa2_params *p, float *pos, float *F, float *Fprev, double *speed,
+                 void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    if (K == 0) return BGV_OK;
+    if (!F || !Fprev || !speed) return BGV_EINVAL;
+    return run_fa2(1, K, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
+                   header(ws), static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
+}
+
+int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, int32_t use_graph, float *pos,
+                float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    if (K == 0 || iterations <= 0) return iterations < 0 ? BGV_EINVAL : BGV_OK;
+    if (!F || !Fprev || !speed) return BGV_EINVAL;
+    return fa2_loop(K, csr_off, csr_adj, csr_w, mass, *p, iterations, use_graph, pos, F, Fprev, speed, header(ws),
+                    static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
+}
+
+int bgv_fa2_read_stats(void *ws, void *stream, bgv_fa2_stats *out) {
+    if (!ws || !out) return BGV_EINVAL;
+    WsHeader h;
+    cudaStream_t st = as_stream(stream);
+    BGV_CUDA(cudaMemcpyAsync(&h, ws, sizeof(WsHeader), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    out->S = h.S;
+    out->T = h.T;
+    out->interactions = h.interactions;
+    out->tree_nodes = h.tree_nodes;
+    out->status = h.status;
+    out->reserved = 0;
+    return BGV_OK;
+}
+
+void bgv_layout_default_params(bgv_layout_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->rows = 4;
+    p->width = 4096;
+    p->seed = 1;
+    p->passes = 3;
+    p->threshold = 0;
+    p->growth = 2;
+    p->tie_mode = 0;
+    p->iterations = 200;
+    p->use_graph = 1;
+    bgv_fa2_default_params(&p->fa2);
+}
+
+size_t bgv_layout_ws_size(int64_t m, int32_t n, const bgv_layout_params *p) {
+    if (check_layout_params(p) != BGV_OK || n < 1 || m < 0) return 0;
+    Carver c(nullptr, kHeaderBytes);
+    LayoutBuffers b;
+    carve_layout(c, m, n, p, b);
+    return c.used();
+}
+
+int bgv_layout(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_params *p, int32_t *node_map, float *xy,
+               float *radius, int64_t *K_out, int64_t *Es_out, void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    BGV_TRY(check_layout_params(p));
+    if (!node_map || !xy || !aligned(xy, 8)) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_layout_ws_size(m, n, p)));
+    Carver c(ws, kHeaderBytes);
+    LayoutBuffers b;
+    carve_layout(c, m, n, p, b);
+    cudaStream_t st = as_stream(stream);
+    BGV_TRY(layout_device(edges, m, n, p, node_map, xy, radius, K_out, Es_out, ws, st, b));
+    uint32_t dev_status = 0;
+    BGV_CUDA(cudaMemcpyAsync(&dev_status, status_ptr(ws), sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    return dev_status ? BGV_EDEVICE : BGV_OK;
+}
+
+size_t bgv_layout_host_ws_size(int64_t m, int32_t n, const bgv_layout_params *p) {
+    size_t base = bgv_layout_ws_size(m, n, p);
+    if (!base) return 0;
+    Carver c(nullptr, base);
+    c.take<int32_t>(size_t(2 * (m > 0 ? m : 1)));
+    c.take<int32_t>(size_t(n));
+    c.take<float>(size_t(2) * size_t(n));
+    c.take<float>(size_t(n));
+    return c.used();
+}
+
+int bgv_layout_host(const int32_t *h_edges, int64_t m, int32_t n, const bgv_layout_params *p, int32_t *h_node_map,
+                    float *h_xy, float *h_radius, int64_t *K_out, int64_t *Es_out, void *ws, size_t ws_bytes,
+                    void *stream) {
+    if (n < 1 || m < 0 || (m > 0 && !h_edges) || !h_node_map || !h_xy) return BGV_EINVAL;
+    BGV_TRY(check_layout_params(p));
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_layout_host_ws_size(m, n, p)));
+    cudaStream_t st = as_stream(stream);
+    const size_t base = bgv_layout_ws_size(m, n, p);
+    Carver io(ws, base);
+    int32_t *d_edges = io.take<int32_t>(size_t(2 * (m > 0 ? m : 1)));
+    int32_t *d_map = io.take<int32_t>(size_t(n));
+    float *d_xy = io.take<float>(size_t(2) * size_t(n));
+    float *d_rad = io.take<float>(size_t(n));
+    if (m > 0) BGV_CUDA(cudaMemcpyAsync(d_edges, h_edges, sizeof(int32_t) * 2 * size_t(m), cudaMemcpyHostToDevice, st));
+    Carver c(ws, kHeaderBytes);
+    LayoutBuffers b;
+    carve_layout(c, m, n, p, b);
+    int64_t K = 0, Es = 0;
+    BGV_TRY(layout_device(d_edges, m, n, p, d_map, d_xy, d_rad, &K, &Es, ws, st, b));
+    BGV_CUDA(cudaMemcpyAsync(h_node_map, d_map, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost, st));
+    if (K > 0) {
+        BGV_CUDA(cudaMemcpyAsync(h_xy, d_xy, sizeof(float) * 2 * size_t(K), cudaMemcpyDeviceToHost, st));
+        if (h_radius) BGV_CUDA(cudaMemcpyAsync(h_radius, d_rad, sizeof(float) * size_t(K), cudaMemcpyDeviceToHost, st));
+    }
+    uint32_t dev_status = 0;
+    BGV_CUDA(cudaMemcpyAsync(&dev_status, status_ptr(ws), sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    if (K_out) *K_out = K;
+    if (Es_out) *Es_out = Es;
+    return dev_status ? BGV_EDEVICE : BGV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// bgv_internal.cuh -- shared internals of libbgv (GB300, sm_103a).
+//
+// Workspace carving, the hash family of the count-min sketches, the device
+// status word, and the interfaces of the generic scan and radix sort used by
+// the supergraph and ForceAtlas2 stages.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "bgv.h"
+
+namespace bgv {
+
+// ---------------------------------------------------------------- workspace
+// Every public workspace starts with this header (kHeaderBytes bytes).
+struct WsHeader {
+    uint32_t status;        // BGV_DEV_* bits
+    uint32_t pad0;
+    unsigned long long interactions;  // FA2: terms of the last step
+    unsigned long long tree_nodes;    // FA2: internal nodes of the last step
+    double S, T;                      // FA2: swing and traction of the last step
+    unsigned int bbox_ticket;         // last-block tickets (reset by the last block)
+    unsigned int node_ticket;
+    unsigned long long reserved[24];
+};
+static_assert(sizeof(WsHeader) <= 256, "header must fit in 256 bytes");
+constexpr size_t kHeaderBytes = 256;
+constexpr size_t kAlign = 256;
+
+// Sequential sub-allocator over a caller workspace.  With base == nullptr it
+// only measures, which is how the *_ws_size queries are computed, so the two
+// can never disagree.
+struct Carver {
+    char *base;
+    size_t off;
+    explicit Carver(void *b, size_t start = 0) : base(static_cast<char *>(b)), off(start) {}
+    template <class T>
+    T *take(size_t count) {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += (count ? count : 1) * sizeof(T);
+        return p;
+    }
+    size_t used() const { return (off + kAlign - 1) / kAlign * kAlign; }
+};
+
+inline WsHeader *header(void *ws) { return static_cast<WsHeader *>(ws); }
+inline uint32_t *status_ptr(void *ws) { return &header(ws)->status; }
+
+#define BGV_TRY(expr)                         \
+    do {                                      \
+        int rc_ = (expr);                     \
+        if (rc_ != BGV_OK) return rc_;        \
+    } while (0)
+
+#define BGV_CUDA(expr)                                   \
+    do {                                                 \
+        if ((expr) != cudaSuccess) return BGV_ECUDA;     \
+    } while (0)
+
+inline int launch_status() { return cudaGetLastError() == cudaSuccess ? BGV_OK : BGV_ECUDA; }
+
+inline int grid_for(int64_t work, int threads, int64_t cap_blocks = 152 * 16) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap_blocks) b = cap_blocks;
+    return static_cast<int>(b);
+}
+
+__device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
+
+// ------------------------------------------------------------- hash family
+// h_i(x) = ((a_i x + b_i) mod (2^31 - 1)) mod width; coefficients from
+// SplitMix64 (Steele, Lea, Flood 2014) at state seed + i.
+constexpr int kMaxRows = 16;
+struct HashFamily {
+    unsigned long long a[kMaxRows];
+    unsigned long long b[kMaxRows];
+    int rows;
+    uint32_t width;
+};
+
+HashFamily make_hash_family(uint64_t seed, int rows, uint32_t width);
+
+__device__ __forceinline__ uint32_t mod_p31(unsigned long long t) {
+    // t < 2^63; fold twice with 2^31 = 1 (mod 2^31 - 1), then one subtraction.
+    unsigned long long y = (t & 0x7FFFFFFFull) + (t >> 31);
+    y = (y & 0x7FFFFFFFull) + (y >> 31);
+    return static_cast<uint32_t>(y >= 0x7FFFFFFFull ? y - 0x7FFFFFFFull : y);
+}
+
+__device__ __forceinline__ uint32_t hash_eval(unsigned long long a, unsigned long long b, uint32_t x,
+                                              uint32_t width) {
+    return mod_p31(a * static_cast<unsigned long long>(x) + b) % width;
+}
+
+// ------------------------------------------------------------------- scan
+// Exclusive prefix sum of uint32 values.  The element count is `n_cap`, or
+// *d_n when d_n != nullptr (then n_cap is an upper bound used for the grid).
+// If `total_u64` is given it receives the sum; if `total_u32_at_end` the sum
+// is also stored at out[n].  Sums must fit in 32 bits.
+size_t scan_tmp_bytes(int64_t n_cap);
+int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64_t *d_n,
+                   unsigned long long *total_u64, bool total_u32_at_end, void *tmp, cudaStream_t s);
+
+// ------------------------------------------------------------- radix sort
+// Stable LSD radix sort of uint64 keys (bits [0, end_bit)) with optional
+// uint32 values.  Count = *d_count if given, else cap.  keys[0]/vals[0]
+// hold the input; the return value is the index (0 or 1) of the buffer pair
+// holding the sorted output.
+struct SortBuffers {
+    unsigned long long *keys[2];
+    uint32_t *vals[2];  // both nullptr for keys only
+    uint32_t *hist;     // 256 * tiles(cap) + 1 entries
+    void *scan_tmp;     // scan_tmp_bytes(256 * tiles(cap))
+};
+int64_t sort_tiles(int64_t cap);
+size_t sort_hist_entries(int64_t cap);
+void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
+int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
+               int *result_buffer);
+
+// Number of bits needed to hold values 0..n-1 (at least 1).
+inline int bits_for(int64_t n) {
+    int b = 1;
+    while (b < 62 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+// --------------------------------------------------------- stage internals
+// Enqueue-only stage bodies used by the public entry points and the
+// pipeline; `status` points at the device status word.
+struct SketchScratch {
+    uint32_t *deg;
+};
+void carve_sketch(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SketchScratch &s);
+int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, uint32_t *sketch,
+               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st);
+
+struct CommScratch {
+    uint2 *state;                   // (degree, label) per node
+    unsigned long long *best;       // packed (edge index, label) proposals
+};
+void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s);
+int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels,
+                    uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st);
+
+struct SuperScratch {
+    uint32_t *flags;        // [n] label present / CSR counts
+    uint32_t *rank;         // [n+1]
+    int32_t *label_of;      // [n]
+    uint32_t *incnt;        // [n]
+    uint32_t *first;        // [n]
+    int64_t *m_cut;         // device scalar
+    unsigned long long *sketch;  // [rows * width]
+    uint32_t *heads;        // [m]
+    uint32_t *segidx;       // [m + 1]
+    uint32_t *segstart;     // [m]
+    void *scan_tmp;
+    SortBuffers sort_cut;   // m keys
+    SortBuffers sort_dst;   // m keys + values
+};
+void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s);
+int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *labels, const uint32_t *deg_est,
+                   const HashFamily &h, int32_t *node_map, int64_t *K_dev, int32_t *ssrc, int32_t *sdst,
+                   uint32_t *sw, int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
+                   uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
+                   const SuperScratch &s, uint32_t *status, cudaStream_t st);
+
+// Scratch for one FA2 step, carved from `scratch` (not counting a header).
+size_t fa2_scratch_bytes(int64_t K, int64_t nnz);
+int fa2_check_params(const bgv_fa2_params *p);
+int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st);
+// mode 0: forces only (Fr/Fa/Fg outputs, any may be null); mode 1: full step.
+int run_fa2(int mode, int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+            const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
+            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st);
+
+}  // namespace bgv

@@ -1,0 +1,129 @@
+// communities.cu -- streaming community rounds (Algorithm 3, Section 3.2.1).
+//
+// Each round is two kernels.  The propose kernel streams the edge list
+// (int4 loads, two edges per load), gathers the start-of-round (degree,
+// label) pair of both endpoints as one 8-byte load each, applies the rule and
+// offers the move to the joining node with a 64-bit atomicMin of
+// (edge index << 32 | label): the lowest edge index wins whatever order the
+// threads run in, so labels are bit-identical to the sequential oracle.  The
+// apply kernel then updates every node that received a proposal and resets
+// the proposal slot for the next round.  No state is written during a
+// propose pass, so every edge reads the snapshot of the round.
+#include "bgv_internal.cuh"
+
+namespace bgv {
+namespace {
+constexpr int kThreads = 256;
+constexpr unsigned long long kNone = ~0ull;
+
+__global__ void __launch_bounds__(kThreads) k_comm_init(const uint32_t *__restrict__ deg_est, int32_t n,
+                                                        uint2 *__restrict__ state,
+                                                        unsigned long long *__restrict__ best) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        state[v] = make_uint2(deg_est[v], uint32_t(v));
+        best[v] = kNone;
+    }
+}
+
+__device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, int32_t n, const uint2 *state,
+                                             unsigned long long *best, uint32_t D, int tie_mode,
+                                             uint32_t *status) {
+    if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(n) || static_cast<uint32_t>(v) >= static_cast<uint32_t>(n)) {
+        raise_status(status, BGV_DEV_BADEDGE);
+        return;
+    }
+    if (u == v) return;
+    const uint2 su = state[u], sv = state[v];  // (degree, label)
+    if (su.x > D || sv.x > D) return;
+    if (su.y == sv.y) return;
+    int32_t w;
+    uint32_t lab;
+    if (su.x > sv.x) {
+        w = v; lab = su.y;
+    } else if (sv.x > su.x) {
+        w = u; lab = sv.y;
+    } else if (tie_mode) {
+        w = u < v ? u : v;
+        lab = u < v ? sv.y : su.y;
+    } else {
+        return;
+    }
+    const unsigned long long cand = (static_cast<unsigned long long>(e) << 32) | lab;
+    // The slot only decreases, so a stale read can only be larger than the
+    // current value: skipping when cand is not below it is always safe.
+    if (cand < best[w]) atomicMin(&best[w], cand);
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_propose(const int32_t *__restrict__ edges, int64_t m, int32_t n,
+                                                           const uint2 *__restrict__ state,
+                                                           unsigned long long *best, uint32_t D, int tie_mode,
+                                                           uint32_t *status) {
+    const int4 *e2 = reinterpret_cast<const int4 *>(edges);
+    const int64_t pairs = m >> 1;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
+        const int4 e = __ldcs(e2 + p);
+        propose_edge(e.x, e.y, uint32_t(2 * p), n, state, best, D, tie_mode, status);
+        propose_edge(e.z, e.w, uint32_t(2 * p + 1), n, state, best, D, tie_mode, status);
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        propose_edge(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, state, best, D, tie_mode,
+                     status);
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_apply(int32_t n, uint2 *__restrict__ state,
+                                                         unsigned long long *__restrict__ best) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long b = best[v];
+        if (b != kNone) {
+            uint2 s = state[v];
+            s.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
+            if (s.x != 0xFFFFFFFFu) s.x += 1;
+            state[v] = s;
+            best[v] = kNone;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_out(int32_t n, const uint2 *__restrict__ state,
+                                                       int32_t *__restrict__ labels, uint32_t *__restrict__ deg_out) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint2 s = state[v];
+        labels[v] = int32_t(s.y);
+        if (deg_out) deg_out[v] = s.x;
+    }
+}
+}  // namespace
+
+void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s) {
+    (void)m;
+    s.state = c.take<uint2>(size_t(n));
+    s.best = c.take<unsigned long long>(size_t(n));
+}
+
+int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
+                    const CommScratch &s, uint32_t *status, cudaStream_t st) {
+    const int gn = grid_for(n, kThreads, 152 * 8);
+    k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
+    BGV_TRY(launch_status());
+    unsigned long long D = threshold;
+    const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
+    for (int32_t p = 0; p < passes; ++p) {
+        if (m > 0) {
+            k_comm_propose<<<ge, kThreads, 0, st>>>(edges, m, n, s.state, s.best, uint32_t(D), tie_mode, status);
+            BGV_TRY(launch_status());
+        }
+        k_comm_apply<<<gn, kThreads, 0, st>>>(n, s.state, s.best);
+        BGV_TRY(launch_status());
+        D *= growth;
+        if (D > 0xFFFFFFFFull) D = 0xFFFFFFFFull;
+    }
+    k_comm_out<<<gn, kThreads, 0, st>>>(n, s.state, labels, deg_out);
+    return launch_status();
+}
+
+}  // namespace bgv

@@ -1,0 +1,110 @@
+// sketch.cu -- degree count-min sketch (Algorithm 2, Section 3.3).
+//
+// Algorithm 2 adds 1 to M[i][h_i(x)] for every event x; the events here are
+// the 2m edge endpoints.  Integer addition commutes, so the same matrix is
+// built from exact per-node degrees: one edge pass counts degrees (L2
+// atomics on an n-entry array), then every node with degree d adds d to its
+// r cells.  That turns 2 r m scattered sketch updates into 2m + r n.
+//
+// Edges are read as int4 (two edges per 16-byte load) with a grid-stride
+// loop over a grid sized to fill the GPU.
+#include "bgv_internal.cuh"
+
+namespace bgv {
+
+HashFamily make_hash_family(uint64_t seed, int rows, uint32_t width) {
+    HashFamily h{};
+    const unsigned long long p = 2147483647ull;
+    for (int i = 0; i < rows && i < kMaxRows; ++i) {
+        unsigned long long st = seed + static_cast<unsigned long long>(i);
+        unsigned long long z[2];
+        for (int k = 0; k < 2; ++k) {
+            st += 0x9E3779B97F4A7C15ull;
+            unsigned long long x = st;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            z[k] = x ^ (x >> 31);
+        }
+        h.a[i] = 1 + z[0] % (p - 1);
+        h.b[i] = z[1] % p;
+    }
+    h.rows = rows;
+    h.width = width;
+    return h;
+}
+
+namespace {
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void count_endpoint(int32_t x, int32_t n, uint32_t *deg, uint32_t *status) {
+    if (static_cast<uint32_t>(x) < static_cast<uint32_t>(n))
+        atomicAdd(&deg[x], 1u);
+    else
+        raise_status(status, BGV_DEV_BADEDGE);
+}
+
+__global__ void __launch_bounds__(kThreads) k_degree_count(const int32_t *__restrict__ edges, int64_t m, int32_t n,
+                                                           uint32_t *__restrict__ deg, uint32_t *status) {
+    const int4 *e2 = reinterpret_cast<const int4 *>(edges);
+    const int64_t pairs = m >> 1;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
+        int4 e = __ldcs(e2 + p);
+        count_endpoint(e.x, n, deg, status);
+        count_endpoint(e.y, n, deg, status);
+        count_endpoint(e.z, n, deg, status);
+        count_endpoint(e.w, n, deg, status);
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        count_endpoint(edges[2 * (m - 1)], n, deg, status);
+        count_endpoint(edges[2 * (m - 1) + 1], n, deg, status);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sketch_fill(const uint32_t *__restrict__ deg, int32_t n,
+                                                          const __grid_constant__ HashFamily h,
+                                                          uint32_t *__restrict__ sketch) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t d = deg[v];
+        if (d == 0) continue;
+        for (int i = 0; i < h.rows; ++i)
+            atomicAdd(&sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], uint32_t(v), h.width)], d);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sketch_query(const uint32_t *__restrict__ sketch, int32_t n,
+                                                           const __grid_constant__ HashFamily h,
+                                                           uint32_t *__restrict__ deg_est) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t best = 0xFFFFFFFFu;
+        for (int i = 0; i < h.rows; ++i) {
+            uint32_t c = sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], uint32_t(v), h.width)];
+            best = c < best ? c : best;
+        }
+        deg_est[v] = best;
+    }
+}
+}  // namespace
+
+void carve_sketch(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SketchScratch &s) {
+    (void)m; (void)rows; (void)width;
+    s.deg = c.take<uint32_t>(size_t(n));
+}
+
+int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, uint32_t *sketch,
+               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st) {
+    BGV_CUDA(cudaMemsetAsync(s.deg, 0, sizeof(uint32_t) * size_t(n), st));
+    BGV_CUDA(cudaMemsetAsync(sketch, 0, sizeof(uint32_t) * size_t(h.rows) * h.width, st));
+    if (m > 0) {
+        k_degree_count<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
+        BGV_TRY(launch_status());
+    }
+    k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch);
+    BGV_TRY(launch_status());
+    k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est);
+    return launch_status();
+}
+
+}  // namespace bgv

@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/bgv.h; host-side validation and workspace queries work without a GPU
+(no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bgv.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_00529_gb300 import build
+    path = build.build()
+    return C.CDLL(str(path))
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(bgv_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_pipeline_calls():
+    names = declared_functions()
+    for required in ("bgv_sketch_degrees", "bgv_communities", "bgv_supergraph", "bgv_fa2_step", "bgv_layout"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib):
+    from paper_2108_00529_gb300 import bgv
+    assert sorted(bgv.EXPORTS) == declared_functions()
+
+
+def test_struct_layouts(lib):
+    from paper_2108_00529_gb300 import bgv
+    assert C.sizeof(bgv.bgv_fa2_params) == 48
+    assert C.sizeof(bgv.bgv_layout_params) == 88
+    assert C.sizeof(bgv.bgv_fa2_stats) == 40
+    p = bgv.bgv_layout_default_params()
+    assert (p.rows, p.width, p.passes, p.growth, p.iterations) == (4, 4096, 3, 2, 200)
+    assert abs(p.fa2.theta - 1.2) < 1e-6 and p.fa2.max_depth == 24 and p.fa2.leaf_cap == 1
+
+
+def test_workspace_queries_are_monotone(lib):
+    from paper_2108_00529_gb300 import bgv
+    a = bgv.bgv_sketch_degrees_ws_size(1000, 100, 4, 64)
+    b = bgv.bgv_sketch_degrees_ws_size(1000, 100000, 4, 64)
+    assert 256 <= a < b and a % 256 == 0
+    assert bgv.bgv_supergraph_ws_size(10, 10, 4, 16) < bgv.bgv_supergraph_ws_size(10**6, 10, 4, 16)
+    assert bgv.bgv_fa2_ws_size(10, 0) < bgv.bgv_fa2_ws_size(10**5, 0)
+    p = bgv.bgv_layout_default_params()
+    assert bgv.bgv_layout_ws_size(100, 50, p) < bgv.bgv_layout_host_ws_size(100, 50, p)
+
+
+def test_host_validation_rejects_bad_arguments(lib):
+    # Rejected on the host before any CUDA call: no GPU needed.
+    from paper_2108_00529_gb300 import bgv
+    L = bgv._lib
+    fake_ws = C.c_void_p(256 * 1024)  # never dereferenced: validation fails first
+    assert L.bgv_sketch_degrees(None, 0, 0, 4, 16, 1, None, None, fake_ws, 1 << 20, None) == bgv.BGV_EINVAL
+    assert L.bgv_sketch_degrees(C.c_void_p(16), 1, 10, 0, 16, 1, C.c_void_p(16), C.c_void_p(16), fake_ws, 1 << 20,
+                                None) == bgv.BGV_EINVAL
+    assert L.bgv_sketch_degrees(C.c_void_p(8), 1, 10, 4, 16, 1, C.c_void_p(16), C.c_void_p(16), fake_ws, 1 << 20,
+                                None) == bgv.BGV_EINVAL  # edges not 16-byte aligned
+    assert L.bgv_sketch_degrees(C.c_void_p(16), 1, 10, 4, 16, 1, C.c_void_p(16), C.c_void_p(16), fake_ws, 64,
+                                None) == bgv.BGV_ENOSPC
+    assert L.bgv_communities(C.c_void_p(16), 1, 10, C.c_void_p(16), 1, 5, 0, 0, C.c_void_p(16), None, fake_ws,
+                             1 << 20, None) == bgv.BGV_EINVAL  # growth 0
+    p = bgv.bgv_fa2_default_params()
+    p.max_depth = 25
+    assert L.bgv_fa2_step(10, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.byref(p),
+                          C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), fake_ws, 1 << 30,
+                          None) == bgv.BGV_EINVAL
+    assert bgv.bgv_strerror(bgv.BGV_ENOSPC) == "workspace too small"

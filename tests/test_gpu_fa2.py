@@ -1,0 +1,200 @@
+"""GPU parity of the ForceAtlas2 stage (Section 3.1, Algorithm 1).
+
+Same quadtree and theta as the oracle: the interaction sets must be identical
+(the interaction counts equal exactly) and every per-node force within 1e-3
+relative error of the FP64 oracle; against exact all-pairs forces the error
+bounds of the method hold.  Calls go through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from oracle import FA2Params
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import gpu_pipeline as G  # noqa: E402
+
+TOL = 1e-3
+
+
+def _case(K, seed, mass_hi=1, layout="uniform"):
+    rng = np.random.default_rng(seed)
+    if layout == "uniform":
+        pos = (rng.random((K, 2)) * 200 - 100).astype(np.float32)
+    elif layout == "clustered":
+        c = rng.normal(size=(max(K // 50, 1), 2)) * 100
+        pos = (c[rng.integers(0, c.shape[0], K)] + rng.normal(size=(K, 2))).astype(np.float32)
+    else:  # init positions of the method
+        pos = oracle.fa2_init(K, seed)
+    mass = rng.integers(1, mass_hi + 1, K).astype(np.uint32)
+    e = graphgen.random_graph(K, 3 * K, seed=seed + 1) if K > 1 else np.zeros((0, 2), np.int32)
+    off, adj, w = G.csr_from_edges(e, K)
+    w = rng.integers(1, 5, w.shape[0]).astype(np.uint32)
+    # symmetric weights: weight of (i, j) equals weight of (j, i)
+    src = np.repeat(np.arange(K), np.diff(off))
+    key = np.minimum(src, adj).astype(np.int64) * K + np.maximum(src, adj)
+    _, inv = np.unique(key, return_inverse=True)
+    w = (inv % 4 + 1).astype(np.uint32)
+    return pos, mass, off, adj, w
+
+
+CASES = [(2, 0, 1, "uniform"), (3, 1, 5, "uniform"), (33, 2, 1, "uniform"), (1000, 3, 50, "clustered"),
+         (4097, 4, 1, "init"), (20011, 5, 1000, "uniform"), (70001, 6, 3, "clustered")]
+
+
+@pytest.mark.parametrize("K,seed,mass_hi,layout", CASES)
+@pytest.mark.parametrize("theta,leaf_cap", [(1.2, 1), (0.5, 4), (0.0, 1)])
+def test_forces_match_oracle(K, seed, mass_hi, layout, theta, leaf_cap):
+    if theta == 0.0 and K > 5000:
+        pytest.skip("all-pairs oracle too slow at this size")
+    pos, mass, off, adj, w = _case(K, seed, mass_hi, layout)
+    p = FA2Params(theta=theta, leaf_cap=leaf_cap, kr=2.0, kg=1.0)
+    r = G.fa2_forces(pos, mass, off, adj, w, p)
+    assert r["status"] == 0
+    Fr0, inter0 = oracle.bh_repulsion(pos, mass, p)
+    assert r["interactions"] == inter0
+    assert G.rel_err(r["Fr"], Fr0) <= TOL
+    assert G.rel_err(r["Fa"], oracle.attraction(off, adj, w, pos)) <= TOL
+    assert G.rel_err(r["Fg"], oracle.gravity(mass, pos, 1.0, 0)) <= TOL
+
+
+def test_coincident_points_and_duplicates():
+    rng = np.random.default_rng(3)
+    pos = np.concatenate([rng.random((500, 2)) * 10, np.repeat([[5.0, 5.0]], 40, axis=0),
+                          np.repeat([[1.0, 9.0]], 3, axis=0)]).astype(np.float32)
+    K = pos.shape[0]
+    mass = rng.integers(1, 9, K).astype(np.uint32)
+    off, adj, w = G.csr_from_edges(np.zeros((0, 2), np.int32), K)
+    for leaf_cap in (1, 2, 64):
+        p = FA2Params(theta=0.8, leaf_cap=leaf_cap)
+        r = G.fa2_forces(pos, mass, off, adj, w, p)
+        Fr0, inter0 = oracle.bh_repulsion(pos, mass, p)
+        assert r["interactions"] == inter0
+        assert G.rel_err(r["Fr"], Fr0) <= TOL
+
+
+def test_shallow_tree_depth():
+    pos, mass, off, adj, w = _case(3000, 8, 7, "clustered")
+    for L in (1, 2, 5):
+        p = FA2Params(theta=1.0, max_depth=L, leaf_cap=1)
+        r = G.fa2_forces(pos, mass, off, adj, w, p)
+        Fr0, inter0 = oracle.bh_repulsion(pos, mass, p)
+        assert r["interactions"] == inter0
+        assert G.rel_err(r["Fr"], Fr0) <= TOL
+
+
+def test_theta_zero_equals_exact_all_pairs():
+    pos, mass, off, adj, w = _case(1500, 9, 20, "uniform")
+    r = G.fa2_forces(pos, mass, off, adj, w, FA2Params(theta=0.0))
+    assert r["interactions"] == 1500 * 1499
+    assert G.rel_err(r["Fr"], oracle.exact_repulsion(pos, mass, 2.0)) <= TOL
+
+
+def test_error_against_exact_forces():
+    # Method accuracy: at theta = 0.3 the 99th percentile and aggregate errors
+    # are below 1e-2; at theta = 1.2 the aggregate error is below 2e-2.
+    pos, mass, off, adj, w = _case(4000, 10, 1, "uniform")
+    ex = oracle.exact_repulsion(pos, mass, 2.0)
+    nrm = np.linalg.norm(ex, axis=1)
+    r = G.fa2_forces(pos, mass, off, adj, w, FA2Params(theta=0.3))
+    rel = np.linalg.norm(r["Fr"] - ex, axis=1) / nrm
+    assert np.percentile(rel, 99) <= 1e-2
+    assert np.linalg.norm(r["Fr"] - ex) / np.linalg.norm(ex) <= 1e-2
+    r = G.fa2_forces(pos, mass, off, adj, w, FA2Params(theta=1.2))
+    assert np.linalg.norm(r["Fr"] - ex) / np.linalg.norm(ex) <= 2e-2
+
+
+def test_strong_gravity_and_single_body():
+    pos, mass, off, adj, w = _case(200, 11, 3, "uniform")
+    p = FA2Params(strong_gravity=1, kg=0.7)
+    r = G.fa2_forces(pos, mass, off, adj, w, p)
+    assert G.rel_err(r["Fg"], oracle.gravity(mass, pos, 0.7, 1)) <= TOL
+    one = G.fa2_forces(np.array([[3.0, 4.0]], np.float32), np.array([2], np.uint32), np.array([0, 0], np.int32),
+                       np.zeros(0, np.int32), np.zeros(0, np.uint32), FA2Params())
+    assert np.all(one["Fr"] == 0) and one["interactions"] == 0
+    assert np.allclose(one["Fg"], [[-1.2, -1.6]], rtol=1e-6)
+
+
+def _supergraph_case():
+    n, e, _ = graphgen.load("sbm16")
+    _, dh = oracle.sketch_degrees(e, n, 4, 4096, 1)
+    lab, _ = oracle.communities(e, n, dh, 3, 64, 2, 0)
+    return oracle.supergraph(e, n, lab, dh, 4, 4096, 1)
+
+
+def test_one_step_matches_oracle():
+    sg = _supergraph_case()
+    K = sg["K"]
+    pos = oracle.fa2_init(K, 1)
+    p = FA2Params()
+    dv = G.Fa2Device(pos, sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], p)
+    dv.step()
+    st = oracle.FA2State(pos)
+    r0 = oracle.fa2_step(st, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p)
+    pos1, F1, Fprev1, speed1 = dv.state()
+    stats = dv.stats()
+    assert stats.status == 0 and stats.interactions == r0["interactions"]
+    assert G.rel_err(F1, r0["F"]) <= TOL
+    assert abs(stats.S - r0["S"]) <= 1e-4 * r0["S"] and abs(stats.T - r0["T"]) <= 1e-4 * r0["T"]
+    assert abs(speed1 - st.speed) <= 1e-4 * st.speed
+    # displacement: compare p1 - p0 per node
+    assert G.rel_err(pos1 - pos, st.pos - pos.astype(np.float64)) <= 2e-3
+
+
+def test_step_from_a_mid_run_state():
+    # A later state (non-zero Fprev, speed != 1) from the oracle's own run.
+    sg = _supergraph_case()
+    p = FA2Params()
+    st = oracle.layout(sg["K"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p, 20, 2)
+    pos = st.pos.astype(np.float32)
+    Fprev = st.Fprev.astype(np.float32)
+    st32 = oracle.FA2State(pos, Fprev, st.speed)
+    r0 = oracle.fa2_step(st32, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p)
+    dv = G.Fa2Device(pos, sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], p, Fprev=Fprev, speed=st.speed)
+    dv.step()
+    _, F1, _, speed1 = dv.state()
+    assert dv.stats().interactions == r0["interactions"]
+    assert G.rel_err(F1, r0["F"]) <= TOL
+    assert abs(speed1 - st32.speed) <= 1e-3 * st32.speed
+
+
+def test_steps_are_deterministic_and_graph_replay_matches():
+    sg = _supergraph_case()
+    pos = oracle.fa2_init(sg["K"], 4)
+    p = FA2Params()
+    runs = []
+    for use_graph in (False, True, True):
+        dv = G.Fa2Device(pos, sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], p)
+        s = torch.cuda.Stream()
+        dv.run(25, use_graph, stream=s)
+        s.synchronize()
+        runs.append(dv.state())
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and r[3] == runs[0][3]
+
+
+def test_layout_invariants_over_many_steps():
+    # Trajectories are chaotic, so a long run is checked by invariants:
+    # finite state, bounded speed growth, communities pulled together.
+    e, memb = graphgen.planted_partition([100] * 5, 0.2, 0.002, seed=12)
+    n = 500
+    off, adj, w = G.csr_from_edges(e, n)
+    mass = (np.diff(off) + 1).astype(np.uint32)
+    dv = G.Fa2Device(oracle.fa2_init(n, 3), mass, off, adj, w, FA2Params())
+    prev = 1.0
+    for _ in range(60):
+        dv.step()
+        _, _, _, sp = dv.state()
+        assert 0 < sp <= 1.5 * prev * (1 + 1e-9)
+        prev = sp
+    pos = dv.state()[0]
+    assert np.all(np.isfinite(pos))
+    cent = np.stack([pos[memb == c].mean(axis=0) for c in range(5)])
+    spread = np.mean([np.linalg.norm(pos[memb == c] - cent[c], axis=1).mean() for c in range(5)])
+    sep = np.mean([np.linalg.norm(cent[a] - cent[b]) for a in range(5) for b in range(a + 1, 5)])
+    assert sep > 2 * spread
