@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the BigGraphVis hot path on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the workload with its inputs
+resident in HBM: degree sketch -> community rounds -> supergraph -> initial
+positions -> ForceAtlas2 iterations.  Each step is timed on the device with
+CUDA events on the launching stream; L2 is flushed (a 256 MiB write) before
+every timed step.  `value` is edges per second of whole steps (m * N / the
+slowest rank's mean step time).  `e2e` repeats the step through
+bgv_layout_host from pinned host memory (host-to-device copy of the edges and
+device-to-host copy of the layout inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+    python bench.py --impl reference ...   # the CPU oracle, bounded sample
+
+Under torchrun (N > 1) every rank lays out its own replica of the workload on
+its own GPU (the path needs no exchange between GPUs); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import platform
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+METRIC = "edges/s streamed (sketch+community), FA2 iters/s, % of HBM/FP32 peak"
+HBM_PEAK_GBS = 6798.2          # measured copy bandwidth of this machine's GB300
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FLOPS_PER_INTERACTION = 12     # dx, dy, d2 (3), division, k*m*M (2), two FMAs (4)
+
+WORKLOADS = {
+    "rmat20": dict(desc="R-MAT scale 20 (1,048,576 node ids), 10,000,000 unique edges, a,b,c,d=.57,.19,.19,.05, "
+                        "shuffled int32 edge list", rows=4, width=65536, passes=3, threshold=0, growth=2,
+                   iterations=500),
+    "sbm16": dict(desc="planted partition, 10,000 nodes in 16 communities, p_in=0.01, p_out=0.0002, seed 1",
+                  rows=4, width=4096, passes=3, threshold=64, growth=2, iterations=200),
+    "rmat22x": dict(desc="R-MAT scale 22 restricted to 3,200,000 nodes, 34,000,000 unique edges, "
+                         "a,b,c,d=.45,.22,.22,.11", rows=4, width=65536, passes=3, threshold=0, growth=2,
+                    iterations=500),
+}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Dist:
+    def __init__(self):
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            td.init_process_group("gloo", rank=self.rank, world_size=self.world)
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpus):
+        self.gpus = gpus
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                idx = int(parts[0])
+            except ValueError:
+                continue
+            if self.gpus is not None and idx not in self.gpus:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(n, edges, cfg, fa2_iters_sample=1):
+    """Time the oracle (single-threaded C) on a bounded sample of one step:
+    the three edge stages on the full graph plus `fa2_iters_sample` FA2
+    iterations on the resulting supergraph.  Returns a dict with the
+    extrapolated step time (edge stages + iterations x FA2 iteration)."""
+    import oracle
+    m = edges.shape[0]
+    thr = cfg["threshold"] or (2 * m) // n
+    t0 = time.perf_counter()
+    _, dh = oracle.sketch_degrees(edges, n, cfg["rows"], cfg["width"], 1)
+    lab, _ = oracle.communities(edges, n, dh, cfg["passes"], thr, cfg["growth"], 0)
+    sg = oracle.supergraph(edges, n, lab, dh, cfg["rows"], cfg["width"], 1)
+    t1 = time.perf_counter()
+    st = oracle.FA2State(oracle.fa2_init(sg["K"], 1))
+    p = oracle.FA2Params()
+    for _ in range(fa2_iters_sample):
+        oracle.fa2_step(st, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p)
+    t2 = time.perf_counter()
+    t_fa2 = (t2 - t1) / max(fa2_iters_sample, 1)
+    step = (t1 - t0) + cfg["iterations"] * t_fa2
+    return dict(edge_s=t1 - t0, fa2_iter_s=t_fa2, step_s=step, wall_s=t2 - t0, K=sg["K"], Es=sg["Es"])
+
+
+def cpu_info():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model, os.cpu_count()
+
+
+# --------------------------------------------------------------- GPU arm
+def gpu_arm(args, dist: Dist):
+    import torch
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        from paper_2108_00529_gb300 import build
+        build.build()
+        graphgen.load(args.workload)
+    dist.barrier()
+    from paper_2108_00529_gb300 import load
+    B = load()
+
+    cfg = WORKLOADS[args.workload]
+    n, edges_np, _ = graphgen.load(args.workload)
+    m = edges_np.shape[0]
+    thr = cfg["threshold"] or (2 * m) // n
+    rows, width, passes, growth, iters = cfg["rows"], cfg["width"], cfg["passes"], cfg["growth"], cfg["iterations"]
+
+    s = torch.cuda.Stream(device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    E = torch.from_numpy(edges_np).to(dev)
+    S = torch.zeros(rows * width, **i32)
+    dh = torch.zeros(n, **i32)
+    labels = torch.zeros(n, **i32)
+    node_map = torch.zeros(n, **i32)
+    Kd = torch.zeros(1, dtype=torch.int64, device=dev)
+    Esd = torch.zeros(1, dtype=torch.int64, device=dev)
+    ssrc, sdst, sw = (torch.zeros(m, **i32) for _ in range(3))
+    mass = torch.zeros(n, **i32)
+    off = torch.zeros(n + 1, **i32)
+    adj, cw = torch.zeros(2 * m, **i32), torch.zeros(2 * m, **i32)
+    pos = torch.zeros((n, 2), dtype=torch.float32, device=dev)
+    F, Fprev = torch.zeros_like(pos), torch.zeros_like(pos)
+    speed = torch.zeros(1, dtype=torch.float64, device=dev)
+    ws_sk = B.alloc_ws(B.bgv_sketch_degrees_ws_size(m, n, rows, width), dev)
+    ws_cm = B.alloc_ws(B.bgv_communities_ws_size(m, n), dev)
+    ws_sg = B.alloc_ws(B.bgv_supergraph_ws_size(m, n, rows, width), dev)
+    ws_fa = B.alloc_ws(B.bgv_fa2_ws_size(n, 2 * m), dev)
+    fp = B.bgv_fa2_default_params()
+    K_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        with torch.cuda.stream(s):
+            ev[0].record(s)
+            B.bgv_sketch_degrees(E, m, n, rows, width, 1, S, dh, ws_sk, stream=s)
+            ev[1].record(s)
+            B.bgv_communities(E, m, n, dh, passes, thr, growth, 0, labels, None, ws_cm, stream=s)
+            ev[2].record(s)
+            B.bgv_supergraph(E, m, n, labels, dh, rows, width, 1, node_map, Kd, ssrc, sdst, sw, Esd, mass, off, adj,
+                             cw, None, None, None, ws_sg, stream=s)
+            ev[3].record(s)
+            K_host.copy_(Kd, non_blocking=True)
+        s.synchronize()
+        K = int(K_host.item())
+        with torch.cuda.stream(s):
+            B.bgv_fa2_init(K, fp, pos, Fprev, speed, stream=s)
+            stages = B.bgv_fa2_run_timed(K, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa, stream=s)
+            ev[4].record(s)
+        s.synchronize()
+        t = [ev[0].elapsed_time(ev[i]) for i in range(1, 5)]
+        return dict(total=t[3], sketch=t[0], communities=t[1] - t[0], supergraph=t[2] - t[1], fa2=t[3] - t[2],
+                    fa2_stages=stages, K=K)
+
+    def flush_l2():
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        step()
+    st0 = B.bgv_fa2_read_stats(ws_fa, s)
+    launches0 = B.bgv_launch_count()
+    clocks = ClockSampler([dist.local] if dist.world == 1 else None)
+    clocks.start()
+    results = []
+    for _ in range(args.steps):
+        flush_l2()
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        results.append(step())
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+    clk = clocks.stop()
+    launches = B.bgv_launch_count() - launches0
+    st1 = B.bgv_fa2_read_stats(ws_fa, s)
+    if st1.status:
+        raise RuntimeError(f"device status {st1.status}")
+
+    ms = float(np.mean([r["total"] for r in results]))
+    ms_max = dist.max(ms)
+    K = results[-1]["K"]
+    Es = int(Esd.item())
+    m_cut = int(sw[:Es].to(torch.int64).sum().item())
+    stage_ms = {k: float(np.mean([r[k] for r in results])) for k in ("sketch", "communities", "supergraph", "fa2")}
+    fa2_stage_ms = {nm: float(np.mean([r["fa2_stages"][i] for r in results]))
+                    for i, nm in enumerate(B.FA2_STAGE_NAMES)}
+
+    # dominant kernel: Barnes-Hut repulsion (one launch per FA2 iteration)
+    steps_run = st1.steps_total - st0.steps_total
+    inter_per_launch = (st1.interactions_total - st0.interactions_total) / max(steps_run, 1)
+    rep_launch_ms = fa2_stage_ms["repulsion"] / iters
+    achieved_tf = inter_per_launch * FLOPS_PER_INTERACTION / (rep_launch_ms * 1e-3) / 1e12
+    peak_tf = fp32_peak_tflops()
+    roofline = {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(achieved_tf, 3),
+                "peak": round(peak_tf, 2), "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
+                "traffic": None, "interactions_per_launch": int(inter_per_launch),
+                "launch_ms": round(rep_launch_ms, 4),
+                "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe unit counts, max clock)"}
+
+    # edge stages against HBM
+    sort_passes = math.ceil(2 * max(1, math.ceil(math.log2(max(n, 2)))) / 8)
+    edge_bytes = (passes + 2) * 8 * m + sort_passes * 16 * m_cut
+    edge_ms = stage_ms["sketch"] + stage_ms["communities"] + stage_ms["supergraph"]
+    edge_gbs = edge_bytes / (edge_ms * 1e-3) / 1e9
+    edge_roofline = {"bound": "hbm", "achieved": round(edge_gbs, 1), "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                     "frac": round(edge_gbs / HBM_PEAK_GBS, 4), "algorithmic_bytes": int(edge_bytes),
+                     "edges_per_s": round(m / (edge_ms * 1e-3), 1), "ms": round(edge_ms, 4)}
+
+    # end to end through the host-buffer entry point
+    lp = B.bgv_layout_default_params()
+    lp.rows, lp.width, lp.passes, lp.threshold, lp.growth, lp.iterations = rows, width, passes, thr, growth, iters
+    ws_e2e = B.alloc_ws(B.bgv_layout_host_ws_size(m, n, lp), dev)
+    he = torch.from_numpy(edges_np).pin_memory()
+    hmap = torch.zeros(n, dtype=torch.int32).pin_memory()
+    hxy = torch.zeros((n, 2), dtype=torch.float32).pin_memory()
+    hrad = torch.zeros(n, dtype=torch.float32).pin_memory()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        K2, _ = B.bgv_layout_host(he, m, n, lp, hmap, hxy, hrad, ws_e2e, stream=s)
+        e1.record(s)
+        s.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    e2e_ms = dist.max(float(np.mean(e2e)))
+
+    out = {
+        "metric": METRIC,
+        "value": round(m * dist.world / (ms_max * 1e-3), 1),
+        "unit": "edges/s",
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "i32+f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m, "sketch": f"{rows}x{width}",
+                   "passes": passes, "threshold": thr, "growth": growth, "fa2_iterations": iters, "theta": 1.2,
+                   "kr": 2.0, "kg": 1.0, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "K": K, "Es": Es, "m_cut": m_cut,
+        "fa2_iters_per_s": round(iters / (stage_ms["fa2"] * 1e-3), 2),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "fa2_stage_ms": {k: round(v, 4) for k, v in fa2_stage_ms.items()},
+        "roofline": roofline,
+        "edge_roofline": edge_roofline,
+        "e2e": {"value": round(m * dist.world / (e2e_ms * 1e-3), 1), "unit": "edges/s",
+                "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(8 * m),
+                "d2h_bytes_per_step": int(4 * n + 12 * K2), "entry": "bgv_layout_host"},
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches // max(args.steps, 1)),
+        "clocks": clk,
+    }
+    if dist.world == 1 and dist.rank == 0 and not args.no_cpu_baseline:
+        r = oracle_sample(n, edges_np, cfg)
+        model, ncpu = cpu_info()
+        out["cpu_baseline"] = {"value": round(m / r["step_s"], 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": (f"oracle (single-threaded C) on {args.workload}: the three edge stages on "
+                                          f"the full graph ({r['edge_s']:.2f} s) plus 1 FA2 iteration on its "
+                                          f"{r['K']}-node supergraph ({r['fa2_iter_s']:.2f} s); step time = edge "
+                                          f"stages + {iters} x FA2 iteration = {r['step_s']:.1f} s"),
+                               "cpu": model, "host_cpus": ncpu}
+    return out
+
+
+def reference_arm(args, dist: Dist):
+    """The oracle as the reference implementation, on the host cores."""
+    if dist.rank != 0:
+        return None
+    cfg = WORKLOADS[args.workload]
+    n, edges_np, _ = graphgen.load(args.workload)
+    m = edges_np.shape[0]
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(n, edges_np, cfg)
+        if i >= args.warmup:
+            steps.append(r)
+    step_s = float(np.mean([r["step_s"] for r in steps]))
+    model, ncpu = cpu_info()
+    value = round(m / step_s, 1)
+    sample = (f"each step: the three edge stages on the full {args.workload} graph plus 1 FA2 iteration on its "
+              f"supergraph; step time = edge stages + {cfg['iterations']} x FA2 iteration")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m,
+                       "sketch": f"{cfg['rows']}x{cfg['width']}", "passes": cfg["passes"],
+                       "fa2_iterations": cfg["iterations"]},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": model, "host_cpus": ncpu},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    dist = Dist()
+    try:
+        out = reference_arm(args, dist) if args.impl == "reference" else gpu_arm(args, dist)
+    finally:
+        dist.close()
+    if out is not None and dist.rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

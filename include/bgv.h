@@ -196,6 +196,8 @@ typedef struct bgv_fa2_stats {
     double T;                   /* sum of m_i traction_i, last step */
     uint64_t interactions;      /* body-cell plus body-body terms, last step */
     uint64_t tree_nodes;        /* quadtree internal nodes, last step */
+    uint64_t interactions_total;/* terms summed over all steps since bgv_ws_init */
+    uint64_t steps_total;       /* steps completed since bgv_ws_init */
     uint32_t status;            /* device status word */
     uint32_t reserved;
 } bgv_fa2_stats;
@@ -227,6 +229,23 @@ int bgv_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, cons
 int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                 const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, int32_t use_graph,
                 float *pos, float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
+
+/* Profiling form of bgv_fa2_run: `iterations` steps launched one by one
+ * (no graph) with CUDA events recorded on `stream` at the boundaries of the
+ * BGV_FA2_STAGES stages of each step; synchronises `stream` and returns in
+ * stage_ms[BGV_FA2_STAGES] the summed milliseconds per stage:
+ *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order,
+ *   3 tree build, 4 quadtree nodes, 5 Barnes-Hut repulsion,
+ *   6 attraction + gravity + swing/traction + speed, 7 displacement.
+ * Creates and destroys (BGV_FA2_STAGES + 1) * iterations CUDA events. */
+#define BGV_FA2_STAGES 8
+int bgv_fa2_run_timed(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                      const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, float *pos, float *F,
+                      float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream, float *stage_ms);
+
+/* Number of kernel launches this library has issued in the process so far
+ * (a kernel replayed from a CUDA graph counts once per replay). */
+uint64_t bgv_launch_count(void);
 
 /* Synchronise `stream` and copy the statistics of the last step. */
 int bgv_fa2_read_stats(void *ws, void *stream, bgv_fa2_stats *out);

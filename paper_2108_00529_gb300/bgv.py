@@ -33,7 +33,7 @@ class bgv_fa2_params(C.Structure):
 
 class bgv_fa2_stats(C.Structure):
     _fields_ = [("S", C.c_double), ("T", C.c_double), ("interactions", u64), ("tree_nodes", u64),
-                ("status", u32), ("reserved", u32)]
+                ("interactions_total", u64), ("steps_total", u64), ("status", u32), ("reserved", u32)]
 
 
 class bgv_layout_params(C.Structure):
@@ -65,6 +65,9 @@ _sig("bgv_fa2_ws_size", sz, [i64, i64])
 _sig("bgv_fa2_forces", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
 _sig("bgv_fa2_step", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
 _sig("bgv_fa2_run", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P, sz, P])
+_sig("bgv_fa2_run_timed", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, P, P, P, P, P, sz, P,
+                                    C.POINTER(C.c_float)])
+_sig("bgv_launch_count", u64, [])
 _sig("bgv_fa2_read_stats", C.c_int, [P, P, C.POINTER(bgv_fa2_stats)])
 _sig("bgv_layout_default_params", None, [C.POINTER(bgv_layout_params)])
 _sig("bgv_layout_ws_size", sz, [i64, i32, C.POINTER(bgv_layout_params)])
@@ -78,7 +81,7 @@ _sig("bgv_layout_host", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, 
 EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees",
            "bgv_communities_ws_size", "bgv_communities", "bgv_supergraph_ws_size", "bgv_supergraph",
            "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
-           "bgv_fa2_run", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
+           "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
            "bgv_layout_host_ws_size", "bgv_layout_host"]
 
 
@@ -203,6 +206,24 @@ def bgv_fa2_run(K, csr_off, csr_adj, csr_w, mass, params, iterations, use_graph,
     _chk(_lib.bgv_fa2_run(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
                           1 if use_graph else 0, _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws),
                           _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_run")
+
+
+BGV_FA2_STAGES = 8
+FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "quad", "repulsion", "node_speed", "update"]
+
+
+def bgv_fa2_run_timed(K, csr_off, csr_adj, csr_w, mass, params, iterations, pos, F, Fprev, speed, ws,
+                      ws_bytes=None, stream=None):
+    """Returns the summed milliseconds per stage (list of BGV_FA2_STAGES)."""
+    out = (C.c_float * BGV_FA2_STAGES)()
+    _chk(_lib.bgv_fa2_run_timed(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
+                                _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws), _nbytes(ws, ws_bytes), _s(stream), out),
+         "bgv_fa2_run_timed")
+    return list(out)
+
+
+def bgv_launch_count() -> int:
+    return int(_lib.bgv_launch_count())
 
 
 def bgv_fa2_read_stats(ws, stream=None) -> bgv_fa2_stats:

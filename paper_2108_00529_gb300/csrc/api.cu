@@ -4,6 +4,7 @@
 // chains the stages (Algorithm 3 end to end).  Everything on the data path
 // runs in the kernels of sketch.cu, communities.cu, supergraph.cu and fa2.cu.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "bgv_internal.cuh"
@@ -133,7 +134,9 @@ int fa2_loop(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long before = launches_issued();
     int rc = run_fa2(1, K, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st);
+    const unsigned long long per_step = launches_issued() - before;  // captured, not yet run
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc != BGV_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -144,8 +147,10 @@ int fa2_loop(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *
         return BGV_ECUDA;
     }
     rc = BGV_OK;
-    for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
+    int32_t replays = 0;
+    for (; replays < iterations && rc == BGV_OK; ++replays)
         if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = BGV_ECUDA;
+    add_launches(per_step * static_cast<unsigned long long>(replays) - per_step);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     return rc;
@@ -200,7 +205,7 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
     BGV_TRY(fa2_loop(K, b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
                      b.Fprev, b.speed, hdr, b.scratch, st));
     if (radius) {
-        k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
+        note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
         BGV_TRY(launch_status());
     }
     return BGV_OK;
@@ -356,6 +361,46 @@ int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const
                     static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
 }
 
+int bgv_fa2_run_timed(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                      const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, float *pos, float *F,
+                      float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream, float *stage_ms) {
+    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    if (iterations < 0 || !stage_ms) return BGV_EINVAL;
+    for (int i = 0; i < BGV_FA2_STAGES; ++i) stage_ms[i] = 0.0f;
+    if (K == 0 || iterations == 0) return BGV_OK;
+    if (!F || !Fprev || !speed) return BGV_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int per = kFa2Stages + 1;
+    const size_t nev = size_t(iterations) * per;
+    cudaEvent_t *ev = static_cast<cudaEvent_t *>(calloc(nev, sizeof(cudaEvent_t)));
+    if (!ev) return BGV_EINVAL;
+    int rc = BGV_OK;
+    size_t made = 0;
+    for (; made < nev; ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) {
+            rc = BGV_ECUDA;
+            break;
+        }
+    for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
+        rc = run_fa2(1, K, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
+                     header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per);
+    if (rc == BGV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = BGV_ECUDA;
+    for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
+        for (int k = 0; k < kFa2Stages; ++k) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ev[size_t(t) * per + k], ev[size_t(t) * per + k + 1]) != cudaSuccess) {
+                rc = BGV_ECUDA;
+                break;
+            }
+            stage_ms[k] += ms;
+        }
+    for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    free(ev);
+    return rc;
+}
+
+uint64_t bgv_launch_count(void) { return launches_issued(); }
+
 int bgv_fa2_read_stats(void *ws, void *stream, bgv_fa2_stats *out) {
     if (!ws || !out) return BGV_EINVAL;
     WsHeader h;
@@ -366,6 +411,8 @@ int bgv_fa2_read_stats(void *ws, void *stream, bgv_fa2_stats *out) {
     out->T = h.T;
     out->interactions = h.interactions;
     out->tree_nodes = h.tree_nodes;
+    out->interactions_total = h.interactions_total;
+    out->steps_total = h.steps_total;
     out->status = h.status;
     out->reserved = 0;
     return BGV_OK;

@@ -18,12 +18,16 @@ namespace bgv {
 struct WsHeader {
     uint32_t status;        // BGV_DEV_* bits
     uint32_t pad0;
+    // accumulated since bgv_ws_init
+    unsigned long long interactions_total;  // FA2 terms over all steps
+    unsigned long long steps_total;         // FA2 steps completed
+    // per step (cleared at the start of every FA2 step)
     unsigned long long interactions;  // FA2: terms of the last step
-    unsigned long long tree_nodes;    // FA2: internal nodes of the last step
+    unsigned long long tree_nodes;    // FA2: quadtree internal nodes of the last step
     double S, T;                      // FA2: swing and traction of the last step
     unsigned int bbox_ticket;         // last-block tickets (reset by the last block)
     unsigned int node_ticket;
-    unsigned long long reserved[24];
+    unsigned long long reserved[22];
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit in 256 bytes");
 constexpr size_t kHeaderBytes = 256;
@@ -61,6 +65,12 @@ inline uint32_t *status_ptr(void *ws) { return &header(ws)->status; }
     } while (0)
 
 inline int launch_status() { return cudaGetLastError() == cudaSuccess ? BGV_OK : BGV_ECUDA; }
+
+// Process-wide count of kernel launches issued by the library (every launch
+// site calls note_launch; graph replays are added by the replay loop).
+void note_launch();
+void add_launches(unsigned long long n);
+unsigned long long launches_issued();
 
 inline int grid_for(int64_t work, int threads, int64_t cap_blocks = 152 * 16) {
     int64_t b = (work + threads - 1) / threads;
@@ -175,8 +185,12 @@ size_t fa2_scratch_bytes(int64_t K, int64_t nnz);
 int fa2_check_params(const bgv_fa2_params *p);
 int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st);
 // mode 0: forces only (Fr/Fa/Fg outputs, any may be null); mode 1: full step.
+// `marks` (optional) receives kFa2Stages + 1 event records at the stage
+// boundaries: frame+keys, sort, gather, tree, quad, repulsion, node, update.
+constexpr int kFa2Stages = 8;
 int run_fa2(int mode, int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
-            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st);
+            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
+            cudaEvent_t *marks = nullptr);
 
 }  // namespace bgv

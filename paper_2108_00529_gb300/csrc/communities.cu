@@ -108,21 +108,21 @@ int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
                     const CommScratch &s, uint32_t *status, cudaStream_t st) {
     const int gn = grid_for(n, kThreads, 152 * 8);
-    k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
+    note_launch(), k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
     BGV_TRY(launch_status());
     unsigned long long D = threshold;
     const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
     for (int32_t p = 0; p < passes; ++p) {
         if (m > 0) {
-            k_comm_propose<<<ge, kThreads, 0, st>>>(edges, m, n, s.state, s.best, uint32_t(D), tie_mode, status);
+            note_launch(), k_comm_propose<<<ge, kThreads, 0, st>>>(edges, m, n, s.state, s.best, uint32_t(D), tie_mode, status);
             BGV_TRY(launch_status());
         }
-        k_comm_apply<<<gn, kThreads, 0, st>>>(n, s.state, s.best);
+        note_launch(), k_comm_apply<<<gn, kThreads, 0, st>>>(n, s.state, s.best);
         BGV_TRY(launch_status());
         D *= growth;
         if (D > 0xFFFFFFFFull) D = 0xFFFFFFFFull;
     }
-    k_comm_out<<<gn, kThreads, 0, st>>>(n, s.state, labels, deg_out);
+    note_launch(), k_comm_out<<<gn, kThreads, 0, st>>>(n, s.state, labels, deg_out);
     return launch_status();
 }
 

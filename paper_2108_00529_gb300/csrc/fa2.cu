@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(kThreads) k_quad(const unsigned long long *__r
             const int2 rg = range[p];
             const int cnt = rg.y - rg.x + 1;
             const bool leaf = cnt <= leaf_cap || lev >= L;
+            // A leaf made by the depth limit (coincident keys, more than
+            // leaf_cap bodies) hides a chain of non-leaf cells with the same
+            // bodies between its parent's level and L; the deepest of them,
+            // at level L - 1, takes the opening test for the whole chain.
+            const int par_lev = (par < 0 || int64_t(par) >= K - 1) ? -1 : sep_level(keys, par, L);
+            const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
             int4 ch = make_int4(kNone, kNone, kNone, kNone);
             if (!leaf) {
                 int refs[4];
@@ -270,10 +276,10 @@ __global__ void __launch_bounds__(kThreads) k_quad(const unsigned long long *__r
             const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
             const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), 2.3283064365386963e-10f)));
             const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), 2.3283064365386963e-10f)));
-            const float sl = __fmul_rn(fr.z, pow2_neg(lev));
+            const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
             QNode nd;
             nd.a = make_float4(cx, cy, __ull2float_rn(M), __fmul_rn(sl, sl));
-            nd.info = make_int4(rg.x, rg.y, leaf ? 1 : 0, lev);
+            nd.info = make_int4(rg.x, rg.y, testable ? 2 : (leaf ? 1 : 0), lev);
             nd.ch = ch;
             nd.pad = make_int4(0, 0, 0, 0);
             q[p] = nd;
@@ -297,6 +303,7 @@ __device__ __forceinline__ void add_body(float xi, float yi, float kmi, float4 b
 __global__ void __launch_bounds__(kThreads) k_repulse(const QNode *__restrict__ q, const int32_t *__restrict__ root_p,
                                                       const float4 *__restrict__ body, int64_t K, float kr,
                                                       float theta2, float2 *__restrict__ Frep,
+                                                      unsigned long long *inter_step,
                                                       unsigned long long *inter_total, uint32_t *status) {
     __shared__ int2 stack[kThreads / 32][kStack];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -335,12 +342,27 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const QNode *__restrict__ 
         }
         const QNode *nd = q + e.x;
         const int4 info = nd->info;
-        if (info.z) {  // leaf: every body, except self
-            for (int t = info.x; t <= info.y; ++t) {
-                const float4 bj = body[t];
-                if (mine && t != si) {
-                    add_body(xi, yi, kmi, bj, fx, fy);
+        if (info.z) {  // leaf: every body except self (a depth leaf may be accepted whole)
+            bool direct = mine;
+            if (mine && info.z == 2 && !(si >= info.x && si <= info.y)) {
+                const float4 a = nd->a;
+                const float dx = __fsub_rn(xi, a.x), dy = __fsub_rn(yi, a.y);
+                const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                if (a.w < __fmul_rn(theta2, d2)) {
+                    const float f = kmi * a.z / d2;
+                    fx += f * dx;
+                    fy += f * dy;
                     ++inter;
+                    direct = false;
+                }
+            }
+            if (__any_sync(0xFFFFFFFFu, direct)) {
+                for (int t = info.x; t <= info.y; ++t) {
+                    const float4 bj = body[t];
+                    if (direct && t != si) {
+                        add_body(xi, yi, kmi, bj, fx, fy);
+                        ++inter;
+                    }
                 }
             }
             continue;
@@ -388,7 +410,10 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const QNode *__restrict__ 
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) inter += __shfl_xor_sync(0xFFFFFFFFu, inter, d);
-    if (lane == 0 && inter) atomicAdd(inter_total, static_cast<unsigned long long>(inter));
+    if (lane == 0 && inter) {
+        atomicAdd(inter_step, static_cast<unsigned long long>(inter));
+        atomicAdd(inter_total, static_cast<unsigned long long>(inter));
+    }
 }
 
 // ------------------------------------------------------ node forces, speed
@@ -487,6 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
     *speed = sp;
     hdr->S = S;
     hdr->T = T;
+    hdr->steps_total += 1;
     hdr->node_ticket = 0u;
 }
 
@@ -597,17 +623,17 @@ int fa2_check_params(const bgv_fa2_params *p) {
 int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st) {
     if (K > 0) {
         const float R = __builtin_sqrtf(float(K));
-        k_init<<<grid_for(K, kThreads, 152 * 8), kThreads, 0, st>>>(K, p.seed, R, reinterpret_cast<float2 *>(pos),
+        note_launch(), k_init<<<grid_for(K, kThreads, 152 * 8), kThreads, 0, st>>>(K, p.seed, R, reinterpret_cast<float2 *>(pos),
                                                                    reinterpret_cast<float2 *>(Fprev));
         BGV_TRY(launch_status());
     }
-    k_set_speed<<<1, 1, 0, st>>>(speed);
+    note_launch(), k_set_speed<<<1, 1, 0, st>>>(speed);
     return launch_status();
 }
 
 int run_fa2(int mode, int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
-            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st) {
+            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks) {
     if (K <= 0) return BGV_OK;
     Carver c(scratch, 0);
     Fa2Scratch s;
@@ -616,45 +642,62 @@ int run_fa2(int mode, int64_t K, const int32_t *csr_off, const int32_t *csr_adj,
     float2 *F = reinterpret_cast<float2 *>(F_f);
     float2 *Fprev = reinterpret_cast<float2 *>(Fprev_f);
     const int L = p.max_depth;
+    auto mark = [&](int i) -> int {
+        if (marks && cudaEventRecord(marks[i], st) != cudaSuccess) return BGV_ECUDA;
+        return BGV_OK;
+    };
 
     // per-step counters and last-block tickets
     BGV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(hdr) + offsetof(WsHeader, interactions), 0,
                              offsetof(WsHeader, reserved) - offsetof(WsHeader, interactions), st));
-    k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
+    BGV_TRY(mark(0));
+    note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
     const int gk = grid_for(K, kThreads, 152 * 16);
-    k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, L, s.sort.keys[0], s.sort.vals[0], s.U);
+    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, L, s.sort.keys[0], s.sort.vals[0], s.U);
     BGV_TRY(launch_status());
+    BGV_TRY(mark(1));
     int res = 0;
     BGV_TRY(radix_sort(s.sort, K, nullptr, 2 * L, st, &res));
-    k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass, s.other);
+    BGV_TRY(mark(2));
+    note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass,
+                                                     s.other);
     BGV_TRY(launch_status());
+    BGV_TRY(mark(3));
     if (K >= 2) {
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         BGV_CUDA(cudaMemsetAsync(s.root, 0xFF, sizeof(int32_t), st));
-        k_tree<<<gt, kThreads, 0, st>>>(s.sort.keys[res], K, s.sU, s.smass, s.other, s.left, s.right, s.parent,
-                                        s.range, s.nM, s.nX, s.nY, s.root);
+        note_launch(), k_tree<<<gt, kThreads, 0, st>>>(s.sort.keys[res], K, s.sU, s.smass, s.other, s.left, s.right,
+                                                       s.parent, s.range, s.nM, s.nX, s.nY, s.root);
         BGV_TRY(launch_status());
-        k_quad<<<unsigned((K - 1 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        BGV_TRY(mark(4));
+        note_launch(), k_quad<<<unsigned((K - 1 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
             s.sort.keys[res], K, L, p.leaf_cap, s.frame, s.left, s.right, s.parent, s.range, s.nM, s.nX, s.nY, s.q,
             &hdr->tree_nodes);
         BGV_TRY(launch_status());
+        BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;
-        k_repulse<<<gt, kThreads, 0, st>>>(s.q, s.root, s.body, K, p.kr, theta2, s.Frep, &hdr->interactions,
-                                           &hdr->status);
+        note_launch(), k_repulse<<<gt, kThreads, 0, st>>>(s.q, s.root, s.body, K, p.kr, theta2, s.Frep,
+                                                          &hdr->interactions, &hdr->interactions_total,
+                                                          &hdr->status);
         BGV_TRY(launch_status());
     } else {
         BGV_CUDA(cudaMemsetAsync(s.Frep, 0, sizeof(float2), st));
+        BGV_TRY(mark(4));
+        BGV_TRY(mark(5));
     }
-    k_node<<<kNodeBlocks, kThreads, 0, st>>>(mode, K, csr_off, csr_adj, csr_w, mass, pos, s.Frep, p.kg,
-                                             p.strong_gravity, F, Fprev, reinterpret_cast<float2 *>(Fr),
-                                             reinterpret_cast<float2 *>(Fa), reinterpret_cast<float2 *>(Fg), s.part,
-                                             speed, p.tau, hdr);
+    BGV_TRY(mark(6));
+    note_launch(), k_node<<<kNodeBlocks, kThreads, 0, st>>>(mode, K, csr_off, csr_adj, csr_w, mass, pos, s.Frep, p.kg,
+                                                            p.strong_gravity, F, Fprev, reinterpret_cast<float2 *>(Fr),
+                                                            reinterpret_cast<float2 *>(Fa),
+                                                            reinterpret_cast<float2 *>(Fg), s.part, speed, p.tau, hdr);
     BGV_TRY(launch_status());
+    BGV_TRY(mark(7));
     if (mode == 1) {
-        k_update<<<gk, kThreads, 0, st>>>(K, F, Fprev, pos, speed, p.ks, p.ksmax);
+        note_launch(), k_update<<<gk, kThreads, 0, st>>>(K, F, Fprev, pos, speed, p.ks, p.ksmax);
         BGV_TRY(launch_status());
     }
+    BGV_TRY(mark(8));
     return BGV_OK;
 }
 

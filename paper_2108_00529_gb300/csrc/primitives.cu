@@ -5,9 +5,16 @@
 // trip.  Grids are sized for the host-side upper bound; blocks past the
 // device count do no work (the radix histogram still writes zeros for them so
 // the digit offsets stay consistent).
+#include <atomic>
+
 #include "bgv_internal.cuh"
 
 namespace bgv {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------- scan
 namespace {
@@ -154,9 +161,9 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
     int64_t nb = (n_cap + kScanTile - 1) / kScanTile;
     if (nb < 1) nb = 1;
     uint32_t *partials = static_cast<uint32_t *>(tmp);
-    k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, partials);
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb);
-    k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, out, n_cap, d_n, partials, nb, total_u64,
+    note_launch(), k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, partials);
+    note_launch(), k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb);
+    note_launch(), k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, out, n_cap, d_n, partials, nb, total_u64,
                                                                    total_u32_at_end ? 1 : 0);
     return launch_status();
 }
@@ -282,14 +289,14 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     const int64_t nh = int64_t(kBins) * tiles;
     int cur = 0;
     for (int shift = 0; shift < end_bit; shift += 8) {
-        k_sort_hist<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(b.keys[cur], cap, d_count, shift, b.hist,
+        note_launch(), k_sort_hist<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(b.keys[cur], cap, d_count, shift, b.hist,
                                                                          tiles);
         BGV_TRY(scan_exclusive(b.hist, b.hist, nh, nullptr, nullptr, false, b.scan_tmp, s));
         if (b.vals[0]) {
-            k_sort_scatter<true><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+            note_launch(), k_sort_scatter<true><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
                 b.keys[cur], b.keys[cur ^ 1], b.vals[cur], b.vals[cur ^ 1], cap, d_count, shift, b.hist, tiles);
         } else {
-            k_sort_scatter<false><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+            note_launch(), k_sort_scatter<false><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
                 b.keys[cur], b.keys[cur ^ 1], nullptr, nullptr, cap, d_count, shift, b.hist, tiles);
         }
         BGV_TRY(launch_status());

@@ -98,12 +98,12 @@ int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, 
     BGV_CUDA(cudaMemsetAsync(s.deg, 0, sizeof(uint32_t) * size_t(n), st));
     BGV_CUDA(cudaMemsetAsync(sketch, 0, sizeof(uint32_t) * size_t(h.rows) * h.width, st));
     if (m > 0) {
-        k_degree_count<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
+        note_launch(), k_degree_count<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
         BGV_TRY(launch_status());
     }
-    k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch);
+    note_launch(), k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch);
     BGV_TRY(launch_status());
-    k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est);
+    note_launch(), k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est);
     return launch_status();
 }
 

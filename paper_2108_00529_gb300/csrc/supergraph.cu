@@ -264,58 +264,58 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
 
     // 1. dense relabel
     BGV_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(uint32_t) * (size_t(n) + 1), st));
-    k_mark_labels<<<gn, kThreads, 0, st>>>(labels, n, s.flags, status);
+    note_launch(), k_mark_labels<<<gn, kThreads, 0, st>>>(labels, n, s.flags, status);
     BGV_TRY(launch_status());
     BGV_TRY(scan_exclusive(s.flags, s.rank, n, nullptr, reinterpret_cast<unsigned long long *>(K_dev), false,
                            s.scan_tmp, st));
-    k_map_nodes<<<gn, kThreads, 0, st>>>(labels, n, s.flags, s.rank, node_map, s.label_of);
+    note_launch(), k_map_nodes<<<gn, kThreads, 0, st>>>(labels, n, s.flags, s.rank, node_map, s.label_of);
     BGV_TRY(launch_status());
 
     // 2-4. cut edges -> sorted keys -> superedges with multiplicities
     BGV_CUDA(cudaMemsetAsync(s.m_cut, 0, sizeof(int64_t), st));
     SortBuffers cut = s.sort_cut;
     if (m > 0) {
-        k_cut_keys<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, labels, node_map,
+        note_launch(), k_cut_keys<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, labels, node_map,
                                                                                  shift, cut.keys[0], s.m_cut, status);
         BGV_TRY(launch_status());
     }
     int res = 0;
     BGV_TRY(radix_sort(cut, m > 0 ? m : 1, s.m_cut, 2 * shift, st, &res));
     const unsigned long long *sorted = cut.keys[res];
-    k_run_heads<<<gm, kThreads, 0, st>>>(sorted, s.m_cut, m, s.heads);
+    note_launch(), k_run_heads<<<gm, kThreads, 0, st>>>(sorted, s.m_cut, m, s.heads);
     BGV_TRY(launch_status());
     BGV_TRY(scan_exclusive(s.heads, s.segidx, m > 0 ? m : 1, s.m_cut, reinterpret_cast<unsigned long long *>(Es_dev),
                            false, s.scan_tmp, st));
-    k_emit_superedges<<<gm, kThreads, 0, st>>>(sorted, s.m_cut, m, s.heads, s.segidx, shift, ssrc, sdst,
+    note_launch(), k_emit_superedges<<<gm, kThreads, 0, st>>>(sorted, s.m_cut, m, s.heads, s.segidx, shift, ssrc, sdst,
                                                 s.segstart);
     BGV_TRY(launch_status());
-    k_weights<<<gm, kThreads, 0, st>>>(s.segstart, Es_dev, s.m_cut, sw);
+    note_launch(), k_weights<<<gm, kThreads, 0, st>>>(s.segstart, Es_dev, s.m_cut, sw);
     BGV_TRY(launch_status());
 
     // 5. community sizes
     BGV_CUDA(cudaMemsetAsync(s.sketch, 0, sizeof(unsigned long long) * size_t(h.rows) * h.width, st));
     if (vol) BGV_CUDA(cudaMemsetAsync(vol, 0, sizeof(uint64_t) * size_t(n), st));
     if (count) BGV_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t) * size_t(n), st));
-    k_size_sketch<<<gn, kThreads, 0, st>>>(labels, deg_est, node_map, n, h, s.sketch,
+    note_launch(), k_size_sketch<<<gn, kThreads, 0, st>>>(labels, deg_est, node_map, n, h, s.sketch,
                                           reinterpret_cast<unsigned long long *>(vol), count);
     BGV_TRY(launch_status());
-    k_mass<<<gn, kThreads, 0, st>>>(s.label_of, K_dev, h, s.sketch, mass, comm_label);
+    note_launch(), k_mass<<<gn, kThreads, 0, st>>>(s.label_of, K_dev, h, s.sketch, mass, comm_label);
     BGV_TRY(launch_status());
 
     // 6. symmetric CSR
     BGV_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(uint32_t) * (size_t(n) + 1), st));
     BGV_CUDA(cudaMemsetAsync(s.incnt, 0, sizeof(uint32_t) * size_t(n), st));
-    k_csr_count<<<gm, kThreads, 0, st>>>(ssrc, sdst, Es_dev, s.flags, s.incnt, s.first);
+    note_launch(), k_csr_count<<<gm, kThreads, 0, st>>>(ssrc, sdst, Es_dev, s.flags, s.incnt, s.first);
     BGV_TRY(launch_status());
     BGV_TRY(scan_exclusive(s.flags, reinterpret_cast<uint32_t *>(csr_off), n, nullptr, nullptr, true, s.scan_tmp,
                            st));
     SortBuffers dsort = s.sort_dst;
-    k_csr_fill_src<<<gm, kThreads, 0, st>>>(ssrc, sdst, sw, Es_dev, csr_off, s.incnt, s.first, csr_adj, csr_w,
+    note_launch(), k_csr_fill_src<<<gm, kThreads, 0, st>>>(ssrc, sdst, sw, Es_dev, csr_off, s.incnt, s.first, csr_adj, csr_w,
                                             dsort.keys[0], dsort.vals[0]);
     BGV_TRY(launch_status());
     int dres = 0;
     BGV_TRY(radix_sort(dsort, m > 0 ? m : 1, Es_dev, shift, st, &dres));
-    k_csr_fill_dst<<<gm, kThreads, 0, st>>>(dsort.keys[dres], dsort.vals[dres], Es_dev, ssrc, sw, csr_off, csr_adj,
+    note_launch(), k_csr_fill_dst<<<gm, kThreads, 0, st>>>(dsort.keys[dres], dsort.vals[dres], Es_dev, ssrc, sw, csr_off, csr_adj,
                                             csr_w);
     return launch_status();
 }

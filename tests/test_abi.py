@@ -45,7 +45,7 @@ def test_struct_layouts(lib):
     from paper_2108_00529_gb300 import bgv
     assert C.sizeof(bgv.bgv_fa2_params) == 48
     assert C.sizeof(bgv.bgv_layout_params) == 88
-    assert C.sizeof(bgv.bgv_fa2_stats) == 40
+    assert C.sizeof(bgv.bgv_fa2_stats) == 56
     p = bgv.bgv_layout_default_params()
     assert (p.rows, p.width, p.passes, p.growth, p.iterations) == (4, 4096, 3, 2, 200)
     assert abs(p.fa2.theta - 1.2) < 1e-6 and p.fa2.max_depth == 24 and p.fa2.leaf_cap == 1
