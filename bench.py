@@ -317,7 +317,7 @@ def gpu_arm(args, dist: Dist):
     hxy = torch.zeros((n, 2), dtype=torch.float32).pin_memory()
     hrad = torch.zeros(n, dtype=torch.float32).pin_memory()
     e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
@@ -325,7 +325,8 @@ def gpu_arm(args, dist: Dist):
         e1.record(s)
         s.synchronize()
         e2e.append(e0.elapsed_time(e1))
-    e2e_ms = dist.max(float(np.mean(e2e)))
+    e2e_ms = dist.max(float(np.mean(e2e))) if e2e else float("nan")
+    K2 = K2 if e2e else K
 
     out = {
         "metric": METRIC,
@@ -406,6 +407,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
