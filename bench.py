@@ -204,7 +204,8 @@ def gpu_arm(args, dist: Dist):
     n, edges_np, _ = graphgen.load(args.workload)
     m = edges_np.shape[0]
     thr = cfg["threshold"] or (2 * m) // n
-    rows, width, passes, growth, iters = cfg["rows"], cfg["width"], cfg["passes"], cfg["growth"], cfg["iterations"]
+    rows, width, passes, growth = cfg["rows"], cfg["width"], cfg["passes"], cfg["growth"]
+    iters = args.fa2_iterations or cfg["iterations"]
 
     s = torch.cuda.Stream(device=dev)
     i32 = dict(dtype=torch.int32, device=dev)
@@ -227,7 +228,7 @@ def gpu_arm(args, dist: Dist):
     ws_sg = B.alloc_ws(B.bgv_supergraph_ws_size(m, n, rows, width), dev)
     ws_fa = B.alloc_ws(B.bgv_fa2_ws_size(n, 2 * m), dev)
     fp = B.bgv_fa2_default_params()
-    K_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+    K_host = torch.zeros(2, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -241,12 +242,15 @@ def gpu_arm(args, dist: Dist):
             B.bgv_supergraph(E, m, n, labels, dh, rows, width, 1, node_map, Kd, ssrc, sdst, sw, Esd, mass, off, adj,
                              cw, None, None, None, ws_sg, stream=s)
             ev[3].record(s)
-            K_host.copy_(Kd, non_blocking=True)
+            K_host[0:1].copy_(Kd, non_blocking=True)
+            K_host[1:2].copy_(Esd, non_blocking=True)
         s.synchronize()
-        K = int(K_host.item())
+        K = int(K_host[0].item())
+        nnz = 2 * int(K_host[1].item())
         with torch.cuda.stream(s):
             B.bgv_fa2_init(K, fp, pos, Fprev, speed, stream=s)
-            stages = B.bgv_fa2_run_timed(K, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa, stream=s)
+            stages = B.bgv_fa2_run_timed(K, nnz, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa,
+                                         stream=s)
             ev[4].record(s)
         s.synchronize()
         t = [ev[0].elapsed_time(ev[i]) for i in range(1, 5)]
@@ -406,6 +410,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--fa2-iterations", type=int, default=0,
+                    help="override the workload's FA2 iteration count (short profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     args = ap.parse_args()

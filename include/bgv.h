@@ -68,6 +68,7 @@ extern "C" {
 #define BGV_DEV_BADEDGE 1u     /* an edge endpoint outside [0, n) */
 #define BGV_DEV_BADLABEL 2u    /* a label outside [0, n) */
 #define BGV_DEV_STACK 4u       /* Barnes-Hut traversal stack exhausted */
+#define BGV_DEV_TIMEOUT 8u     /* a bounded device-side wait gave up */
 
 /* Library version, (major << 16) | minor. */
 int bgv_version(void);
@@ -209,24 +210,25 @@ void bgv_fa2_default_params(bgv_fa2_params *p);
  * *speed = 1 (device double). */
 int bgv_fa2_init(int64_t K, const bgv_fa2_params *p, float *pos, float *Fprev, double *speed, void *stream);
 
-/* Workspace for bodies K and CSR entries nnz (= csr_off[K]). */
+/* Workspace for bodies K and CSR entries nnz.  Every FA2 call below takes
+ * the same nnz, which must equal csr_off[K] (2 Es for a supergraph). */
 size_t bgv_fa2_ws_size(int64_t K, int64_t nnz);
 
 /* Forces only, at positions pos, without changing any state:
  * Fr, Fa, Fg [K][2] float (repulsion, attraction, gravity); any may be NULL. */
-int bgv_fa2_forces(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_forces(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                    const uint32_t *mass, const bgv_fa2_params *p, const float *pos,
                    float *Fr, float *Fa, float *Fg, void *ws, size_t ws_bytes, void *stream);
 
 /* One iteration in place: F receives the total force, pos/Fprev/speed are
  * advanced.  Statistics of the step stay in `ws` (bgv_fa2_read_stats). */
-int bgv_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_step(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                  const uint32_t *mass, const bgv_fa2_params *p, float *pos, float *F, float *Fprev,
                  double *speed, void *ws, size_t ws_bytes, void *stream);
 
 /* `iterations` steps; with use_graph != 0 one step is captured into a CUDA
  * graph on `stream` and replayed (the stream must not be capturing). */
-int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                 const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, int32_t use_graph,
                 float *pos, float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
 
@@ -239,7 +241,7 @@ int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const
  *   6 attraction + gravity + swing/traction + speed, 7 displacement.
  * Creates and destroys (BGV_FA2_STAGES + 1) * iterations CUDA events. */
 #define BGV_FA2_STAGES 8
-int bgv_fa2_run_timed(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                       const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, float *pos, float *F,
                       float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream, float *stage_ms);
 

@@ -19,7 +19,7 @@ if not _LIB_PATH.exists():
 _lib = C.CDLL(str(_LIB_PATH))
 
 BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA = 0, 1, 2, 3, 4
-BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_STACK = 1, 2, 4
+BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_STACK, BGV_DEV_TIMEOUT = 1, 2, 4, 8
 
 P = C.c_void_p
 i32, i64, u32, u64, sz = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t
@@ -62,10 +62,10 @@ _sig("bgv_supergraph", C.c_int, [P, i64, i32, P, P, i32, i32, u64, P, P, P, P, P
 _sig("bgv_fa2_default_params", None, [C.POINTER(bgv_fa2_params)])
 _sig("bgv_fa2_init", C.c_int, [i64, C.POINTER(bgv_fa2_params), P, P, P, P])
 _sig("bgv_fa2_ws_size", sz, [i64, i64])
-_sig("bgv_fa2_forces", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
-_sig("bgv_fa2_step", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
-_sig("bgv_fa2_run", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P, sz, P])
-_sig("bgv_fa2_run_timed", C.c_int, [i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, P, P, P, P, P, sz, P,
+_sig("bgv_fa2_forces", C.c_int, [i64, i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
+_sig("bgv_fa2_step", C.c_int, [i64, i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz, P])
+_sig("bgv_fa2_run", C.c_int, [i64, i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P, sz, P])
+_sig("bgv_fa2_run_timed", C.c_int, [i64, i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, P, P, P, P, P, sz, P,
                                     C.POINTER(C.c_float)])
 _sig("bgv_launch_count", u64, [])
 _sig("bgv_fa2_read_stats", C.c_int, [P, P, C.POINTER(bgv_fa2_stats)])
@@ -191,19 +191,19 @@ def bgv_fa2_ws_size(K: int, nnz: int) -> int:
     return _lib.bgv_fa2_ws_size(K, nnz)
 
 
-def bgv_fa2_forces(K, csr_off, csr_adj, csr_w, mass, params, pos, Fr, Fa, Fg, ws, ws_bytes=None, stream=None):
-    _chk(_lib.bgv_fa2_forces(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(Fr),
+def bgv_fa2_forces(K, nnz, csr_off, csr_adj, csr_w, mass, params, pos, Fr, Fa, Fg, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_fa2_forces(K, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(Fr),
                              _p(Fa), _p(Fg), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_forces")
 
 
-def bgv_fa2_step(K, csr_off, csr_adj, csr_w, mass, params, pos, F, Fprev, speed, ws, ws_bytes=None, stream=None):
-    _chk(_lib.bgv_fa2_step(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(F),
+def bgv_fa2_step(K, nnz, csr_off, csr_adj, csr_w, mass, params, pos, F, Fprev, speed, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_fa2_step(K, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos), _p(F),
                            _p(Fprev), _p(speed), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_step")
 
 
-def bgv_fa2_run(K, csr_off, csr_adj, csr_w, mass, params, iterations, use_graph, pos, F, Fprev, speed, ws,
+def bgv_fa2_run(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, use_graph, pos, F, Fprev, speed, ws,
                 ws_bytes=None, stream=None):
-    _chk(_lib.bgv_fa2_run(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
+    _chk(_lib.bgv_fa2_run(K, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
                           1 if use_graph else 0, _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws),
                           _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_run")
 
@@ -212,11 +212,11 @@ BGV_FA2_STAGES = 8
 FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "quad", "repulsion", "node_speed", "update"]
 
 
-def bgv_fa2_run_timed(K, csr_off, csr_adj, csr_w, mass, params, iterations, pos, F, Fprev, speed, ws,
+def bgv_fa2_run_timed(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, pos, F, Fprev, speed, ws,
                       ws_bytes=None, stream=None):
     """Returns the summed milliseconds per stage (list of BGV_FA2_STAGES)."""
     out = (C.c_float * BGV_FA2_STAGES)()
-    _chk(_lib.bgv_fa2_run_timed(K, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
+    _chk(_lib.bgv_fa2_run_timed(K, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), iterations,
                                 _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws), _nbytes(ws, ws_bytes), _s(stream), out),
          "bgv_fa2_run_timed")
     return list(out)

@@ -121,13 +121,13 @@ int check_layout_params(const bgv_layout_params *p) {
     return fa2_check_params(&p->fa2);
 }
 
-int fa2_loop(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *w, const uint32_t *mass,
+int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w, const uint32_t *mass,
              const bgv_fa2_params &p, int32_t iterations, int32_t use_graph, float *pos, float *F, float *Fprev,
              double *speed, WsHeader *hdr, void *scratch, cudaStream_t st) {
     if (iterations <= 0 || K <= 0) return BGV_OK;
     if (!use_graph || st == nullptr || iterations < 2) {
         for (int32_t t = 0; t < iterations; ++t)
-            BGV_TRY(run_fa2(1, K, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
+            BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
                             scratch, st));
         return BGV_OK;
     }
@@ -135,7 +135,7 @@ int fa2_loop(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *
     cudaGraphExec_t exec = nullptr;
     BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const unsigned long long before = launches_issued();
-    int rc = run_fa2(1, K, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st);
+    int rc = run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st);
     const unsigned long long per_step = launches_issued() - before;  // captured, not yet run
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc != BGV_OK || ce != cudaSuccess) {
@@ -202,7 +202,7 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
     if (K_out) *K_out = K;
     if (Es_out) *Es_out = KE[1];
     BGV_TRY(run_fa2_init(K, p->fa2, xy, b.Fprev, b.speed, st));
-    BGV_TRY(fa2_loop(K, b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
+    BGV_TRY(fa2_loop(K, 2 * KE[1], b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
                      b.Fprev, b.speed, hdr, b.scratch, st));
     if (radius) {
         note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
@@ -322,49 +322,49 @@ int bgv_fa2_init(int64_t K, const bgv_fa2_params *p, float *pos, float *Fprev, d
 
 size_t bgv_fa2_ws_size(int64_t K, int64_t nnz) { return kHeaderBytes + fa2_scratch_bytes(K, nnz); }
 
-static int check_fa2_args(int64_t K, const int32_t *off, const int32_t *adj, const uint32_t *w,
+static int check_fa2_args(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w,
                           const uint32_t *mass, const bgv_fa2_params *p, const float *pos, void *ws,
                           size_t ws_bytes) {
-    if (K < 0 || K >= 0x7FFFFFFF) return BGV_EINVAL;
+    if (K < 0 || K >= 0x7FFFFFFF || nnz < 0 || nnz >= (int64_t(1) << 31)) return BGV_EINVAL;
     BGV_TRY(fa2_check_params(p));
     if (K == 0) return BGV_OK;
     if (!off || !adj || !w || !mass || !pos || !aligned(pos, 8)) return BGV_EINVAL;
-    return check_ws(ws, ws_bytes, bgv_fa2_ws_size(K, 0));
+    return check_ws(ws, ws_bytes, bgv_fa2_ws_size(K, nnz));
 }
 
-int bgv_fa2_forces(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_forces(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                    const uint32_t *mass, const bgv_fa2_params *p, const float *pos, float *Fr, float *Fa, float *Fg,
                    void *ws, size_t ws_bytes, void *stream) {
-    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    BGV_TRY(check_fa2_args(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
     if (K == 0) return BGV_OK;
-    return run_fa2(0, K, csr_off, csr_adj, csr_w, mass, *p, const_cast<float *>(pos), nullptr, nullptr, nullptr, Fr,
+    return run_fa2(0, K, nnz, csr_off, csr_adj, csr_w, mass, *p, const_cast<float *>(pos), nullptr, nullptr, nullptr, Fr,
                    Fa, Fg, header(ws), static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
 }
 
-int bgv_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_step(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                  const uint32_t *mass, const bgv_fa2_params *p, float *pos, float *F, float *Fprev, double *speed,
                  void *ws, size_t ws_bytes, void *stream) {
-    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    BGV_TRY(check_fa2_args(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
     if (K == 0) return BGV_OK;
     if (!F || !Fprev || !speed) return BGV_EINVAL;
-    return run_fa2(1, K, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
+    return run_fa2(1, K, nnz, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
                    header(ws), static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
 }
 
-int bgv_fa2_run(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                 const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, int32_t use_graph, float *pos,
                 float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream) {
-    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    BGV_TRY(check_fa2_args(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
     if (K == 0 || iterations <= 0) return iterations < 0 ? BGV_EINVAL : BGV_OK;
     if (!F || !Fprev || !speed) return BGV_EINVAL;
-    return fa2_loop(K, csr_off, csr_adj, csr_w, mass, *p, iterations, use_graph, pos, F, Fprev, speed, header(ws),
+    return fa2_loop(K, nnz, csr_off, csr_adj, csr_w, mass, *p, iterations, use_graph, pos, F, Fprev, speed, header(ws),
                     static_cast<char *>(ws) + kHeaderBytes, as_stream(stream));
 }
 
-int bgv_fa2_run_timed(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                       const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations, float *pos, float *F,
                       float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream, float *stage_ms) {
-    BGV_TRY(check_fa2_args(K, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
+    BGV_TRY(check_fa2_args(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos, ws, ws_bytes));
     if (iterations < 0 || !stage_ms) return BGV_EINVAL;
     for (int i = 0; i < BGV_FA2_STAGES; ++i) stage_ms[i] = 0.0f;
     if (K == 0 || iterations == 0) return BGV_OK;
@@ -382,7 +382,7 @@ int bgv_fa2_run_timed(int64_t K, const int32_t *csr_off, const int32_t *csr_adj,
             break;
         }
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
-        rc = run_fa2(1, K, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
+        rc = run_fa2(1, K, nnz, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
                      header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per);
     if (rc == BGV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = BGV_ECUDA;
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)

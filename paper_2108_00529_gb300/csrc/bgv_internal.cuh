@@ -116,21 +116,21 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
                    unsigned long long *total_u64, bool total_u32_at_end, void *tmp, cudaStream_t s);
 
 // ------------------------------------------------------------- radix sort
-// Stable LSD radix sort of uint64 keys (bits [0, end_bit)) with optional
-// uint32 values.  Count = *d_count if given, else cap.  keys[0]/vals[0]
-// hold the input; the return value is the index (0 or 1) of the buffer pair
-// holding the sorted output.
+// Stable LSD radix sort of uint64 keys (bits [0, end_bit), end_bit <= 64)
+// with optional uint32 values.  Count = *d_count if given, else cap.
+// keys[0]/vals[0] hold the input; *result_buffer receives the index (0 or 1)
+// of the buffer pair holding the sorted output.  A look-back wait that hits
+// its bound sets BGV_DEV_TIMEOUT in *dev_status.
 struct SortBuffers {
     unsigned long long *keys[2];
-    uint32_t *vals[2];  // both nullptr for keys only
-    uint32_t *hist;     // 256 * tiles(cap) + 1 entries
-    void *scan_tmp;     // scan_tmp_bytes(256 * tiles(cap))
+    uint32_t *vals[2];               // both nullptr for keys only
+    unsigned long long *status;      // 256 look-back words per tile
+    uint32_t *counts;                // per-pass digit offsets, then tile counters
 };
 int64_t sort_tiles(int64_t cap);
-size_t sort_hist_entries(int64_t cap);
 void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
-               int *result_buffer);
+               int *result_buffer, uint32_t *dev_status);
 
 // Number of bits needed to hold values 0..n-1 (at least 1).
 inline int bits_for(int64_t n) {
@@ -188,7 +188,7 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
 // `marks` (optional) receives kFa2Stages + 1 event records at the stage
 // boundaries: frame+keys, sort, gather, tree, quad, repulsion, node, update.
 constexpr int kFa2Stages = 8;
-int run_fa2(int mode, int64_t K, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
             cudaEvent_t *marks = nullptr);

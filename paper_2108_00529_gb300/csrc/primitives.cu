@@ -169,74 +169,96 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
 }
 
 // ------------------------------------------------------------- radix sort
+// Stable LSD radix sort, 8-bit digits, in the one-sweep form: one kernel
+// counts the digits of every pass at once; each pass is then a single
+// kernel in which a block takes the next tile number from a counter, ranks
+// its keys (warp match_any plus per-warp digit counters, in (item, lane)
+// order, which keeps the sort stable), publishes its per-digit tile count,
+// and looks back over the tiles before it to find its global offsets
+// (decoupled look-back).  A block only ever waits for tiles with smaller
+// numbers, which were handed to blocks that are already running, so the
+// waits end; each wait is still bounded and reports BGV_DEV_TIMEOUT if the
+// bound is hit.
 namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
 constexpr int kBins = 256;
+constexpr int kMaxPasses = 8;
 constexpr uint32_t kInvalidDigit = 0xFFFFu;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kCountMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const unsigned long long *__restrict__ keys, int64_t cap,
-                                                            const int64_t *d_count, int shift,
-                                                            uint32_t *__restrict__ hist, int64_t tiles) {
-    __shared__ uint32_t h[kSortWarps][kBins];
-    for (int i = threadIdx.x; i < kSortWarps * kBins; i += kSortThreads) (&h[0][0])[i] = 0;
+__global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long long *__restrict__ keys, int64_t cap,
+                                                             const int64_t *d_count, int passes,
+                                                             uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[kMaxPasses][kBins];
+    for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = load_count(d_count, cap);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * (32 * kSortItems);
-    if (int64_t(blockIdx.x) * kSortTile < n) {
-#pragma unroll 4
-        for (int k = 0; k < kSortItems; ++k) {
-            int64_t i = base + int64_t(k) * 32 + lane;
-            if (i < n) {
-                uint32_t d = static_cast<uint32_t>(keys[i] >> shift) & 0xFFu;
-                atomicAdd(&h[warp][d], 1u);
-            }
+    const int64_t base = int64_t(blockIdx.x) * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int64_t i = base + int64_t(k) * kSortThreads + threadIdx.x;
+        if (i < n) {
+            const unsigned long long key = keys[i];
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][uint32_t(key >> (8 * p)) & 0xFFu], 1u);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kBins; d += kSortThreads) {
-        uint32_t t = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) t += h[w][d];
-        hist[int64_t(d) * tiles + blockIdx.x] = t;
+    for (int i = threadIdx.x; i < passes * kBins; i += kSortThreads) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&counts[i], c);
+    }
+}
+
+// Exclusive scan of each pass's 256 digit counts, in place.
+__global__ void __launch_bounds__(kSortThreads) k_sort_offsets(uint32_t *counts, int passes) {
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t c = counts[p * kBins + threadIdx.x];
+        uint32_t tot;
+        const uint32_t ex = block_exclusive(c, &tot);
+        counts[p * kBins + threadIdx.x] = ex;
     }
 }
 
 template <bool kVals>
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const unsigned long long *__restrict__ kin,
-                                                               unsigned long long *__restrict__ kout,
-                                                               const uint32_t *__restrict__ vin,
-                                                               uint32_t *__restrict__ vout, int64_t cap,
-                                                               const int64_t *d_count, int shift,
-                                                               const uint32_t *__restrict__ offsets, int64_t tiles) {
+__global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned long long *__restrict__ kin,
+                                                                unsigned long long *__restrict__ kout,
+                                                                const uint32_t *__restrict__ vin,
+                                                                uint32_t *__restrict__ vout, int64_t cap,
+                                                                const int64_t *d_count, int shift,
+                                                                const uint32_t *__restrict__ digit_base,
+                                                                unsigned int *tile_counter,
+                                                                unsigned long long *status, uint32_t *dev_status) {
     __shared__ uint32_t cnt[kSortWarps][kBins];
-    const int64_t n = load_count(d_count, cap);
-    if (int64_t(blockIdx.x) * kSortTile >= n) return;
+    __shared__ uint32_t tile_base[kBins];
+    __shared__ unsigned int tile_sh;
+    if (threadIdx.x == 0) tile_sh = atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kSortWarps * kBins; i += kSortThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
+    const int64_t tile = tile_sh;
+    const int64_t n = load_count(d_count, cap);
+    if (tile * kSortTile >= n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const int64_t base = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * (32 * kSortItems);
+    const int64_t base = tile * kSortTile + int64_t(warp) * (32 * kSortItems);
     unsigned long long key[kSortItems];
     uint32_t val[kSortItems];
     uint32_t digit[kSortItems];
     uint32_t rank[kSortItems];
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        int64_t i = base + int64_t(k) * 32 + lane;
-        bool ok = i < n;
+        const int64_t i = base + int64_t(k) * 32 + lane;
+        const bool ok = i < n;
         key[k] = ok ? kin[i] : 0ull;
         if (kVals) val[k] = ok ? vin[i] : 0u;
         digit[k] = ok ? (static_cast<uint32_t>(key[k] >> shift) & 0xFFu) : kInvalidDigit;
     }
-    // Stable rank within the warp, items in (k, lane) order.
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        uint32_t d = digit[k];
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t d = digit[k];
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         uint32_t before = 0;
         if (d != kInvalidDigit) before = cnt[warp][d];
         rank[k] = before + __popc(peers & lt_mask);
@@ -245,22 +267,49 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const unsigned lo
         __syncwarp();
     }
     __syncthreads();
-    // Per digit: exclusive prefix over warps plus the global offset of this tile.
-    for (int d = threadIdx.x; d < kBins; d += kSortThreads) {
-        uint32_t run = offsets[int64_t(d) * tiles + blockIdx.x];
+    {
+        // thread d owns digit d: warp prefixes, tile total, look-back
+        const int d = threadIdx.x;
+        uint32_t total = 0;
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t c = cnt[w][d];
-            cnt[w][d] = run;
-            run += c;
+            const uint32_t c = cnt[w][d];
+            cnt[w][d] = total;
+            total += c;
         }
+        volatile unsigned long long *st = status;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            st[d] = kFlagIncl | total;
+        } else {
+            st[tile * kBins + d] = kFlagAgg | total;
+            int64_t j = tile - 1;
+            int spins = 0;
+            while (j >= 0) {
+                const unsigned long long v = st[j * kBins + d];
+                const unsigned long long flag = v & ~kCountMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        raise_status(dev_status, BGV_DEV_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += v & kCountMask;
+                if (flag == kFlagIncl) break;
+                --j;
+            }
+            st[tile * kBins + d] = kFlagIncl | (excl + total);
+        }
+        tile_base[d] = digit_base[d] + uint32_t(excl);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        uint32_t d = digit[k];
+        const uint32_t d = digit[k];
         if (d == kInvalidDigit) continue;
-        uint32_t pos = cnt[warp][d] + rank[k];
+        const uint32_t pos = tile_base[d] + cnt[warp][d] + rank[k];
         kout[pos] = key[k];
         if (kVals) vout[pos] = val[k];
     }
@@ -272,32 +321,37 @@ int64_t sort_tiles(int64_t cap) {
     return t < 1 ? 1 : t;
 }
 
-size_t sort_hist_entries(int64_t cap) { return size_t(kBins) * size_t(sort_tiles(cap)) + 1; }
-
 void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out) {
     out.keys[0] = c.take<unsigned long long>(size_t(cap));
     out.keys[1] = c.take<unsigned long long>(size_t(cap));
     out.vals[0] = with_vals ? c.take<uint32_t>(size_t(cap)) : nullptr;
     out.vals[1] = with_vals ? c.take<uint32_t>(size_t(cap)) : nullptr;
-    out.hist = c.take<uint32_t>(sort_hist_entries(cap));
-    out.scan_tmp = c.take<char>(scan_tmp_bytes(int64_t(sort_hist_entries(cap))));
+    out.status = c.take<unsigned long long>(size_t(kBins) * size_t(sort_tiles(cap)));
+    out.counts = c.take<uint32_t>(size_t(kMaxPasses) * kBins + kMaxPasses);
 }
 
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
-               int *result_buffer) {
+               int *result_buffer, uint32_t *dev_status) {
     const int64_t tiles = sort_tiles(cap);
-    const int64_t nh = int64_t(kBins) * tiles;
+    const int passes = (end_bit + 7) / 8;
+    if (passes > kMaxPasses) return BGV_EINVAL;
+    uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
+    BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
+    note_launch(), k_sort_count<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(b.keys[0], cap, d_count,
+                                                                                    passes, b.counts);
+    note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
+    BGV_TRY(launch_status());
     int cur = 0;
-    for (int shift = 0; shift < end_bit; shift += 8) {
-        note_launch(), k_sort_hist<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(b.keys[cur], cap, d_count, shift, b.hist,
-                                                                         tiles);
-        BGV_TRY(scan_exclusive(b.hist, b.hist, nh, nullptr, nullptr, false, b.scan_tmp, s));
+    for (int p = 0; p < passes; ++p) {
+        BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
         if (b.vals[0]) {
-            note_launch(), k_sort_scatter<true><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-                b.keys[cur], b.keys[cur ^ 1], b.vals[cur], b.vals[cur ^ 1], cap, d_count, shift, b.hist, tiles);
+            note_launch(), k_sort_onesweep<true><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+                b.keys[cur], b.keys[cur ^ 1], b.vals[cur], b.vals[cur ^ 1], cap, d_count, 8 * p, b.counts + p * kBins,
+                tile_counters + p, b.status, dev_status);
         } else {
-            note_launch(), k_sort_scatter<false><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-                b.keys[cur], b.keys[cur ^ 1], nullptr, nullptr, cap, d_count, shift, b.hist, tiles);
+            note_launch(), k_sort_onesweep<false><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+                b.keys[cur], b.keys[cur ^ 1], nullptr, nullptr, cap, d_count, 8 * p, b.counts + p * kBins,
+                tile_counters + p, b.status, dev_status);
         }
         BGV_TRY(launch_status());
         cur ^= 1;

@@ -280,7 +280,7 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
         BGV_TRY(launch_status());
     }
     int res = 0;
-    BGV_TRY(radix_sort(cut, m > 0 ? m : 1, s.m_cut, 2 * shift, st, &res));
+    BGV_TRY(radix_sort(cut, m > 0 ? m : 1, s.m_cut, 2 * shift, st, &res, status));
     const unsigned long long *sorted = cut.keys[res];
     note_launch(), k_run_heads<<<gm, kThreads, 0, st>>>(sorted, s.m_cut, m, s.heads);
     BGV_TRY(launch_status());
@@ -314,7 +314,7 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
                                             dsort.keys[0], dsort.vals[0]);
     BGV_TRY(launch_status());
     int dres = 0;
-    BGV_TRY(radix_sort(dsort, m > 0 ? m : 1, Es_dev, shift, st, &dres));
+    BGV_TRY(radix_sort(dsort, m > 0 ? m : 1, Es_dev, shift, st, &dres, status));
     note_launch(), k_csr_fill_dst<<<gm, kThreads, 0, st>>>(dsort.keys[dres], dsort.vals[dres], Es_dev, ssrc, sw, csr_off, csr_adj,
                                             csr_w);
     return launch_status();

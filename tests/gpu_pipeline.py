@@ -115,7 +115,7 @@ def fa2_forces(pos, mass, off, adj, w, params):
     O, A, W = _csr_dev(off, adj, w)
     Fr, Fa, Fg = (torch.zeros((max(K, 1), 2), dtype=torch.float32, device="cuda") for _ in range(3))
     ws = B.alloc_ws(B.bgv_fa2_ws_size(K, int(np.asarray(off)[-1]) if K else 0))
-    B.bgv_fa2_forces(K, O, A, W, M, fa2_params(params), P, Fr, Fa, Fg, ws)
+    B.bgv_fa2_forces(K, int(np.asarray(off)[-1]) if K else 0, O, A, W, M, fa2_params(params), P, Fr, Fa, Fg, ws)
     st = B.bgv_fa2_read_stats(ws)
     return dict(Fr=host(Fr)[:K].astype(np.float64), Fa=host(Fa)[:K].astype(np.float64),
                 Fg=host(Fg)[:K].astype(np.float64), interactions=int(st.interactions), status=int(st.status),
@@ -135,14 +135,15 @@ class Fa2Device:
         self.mass = dev(np.asarray(mass, np.uint32))
         self.off, self.adj, self.w = _csr_dev(off, adj, w)
         self.params = fa2_params(params)
-        self.ws = B.alloc_ws(B.bgv_fa2_ws_size(self.K, int(np.asarray(off)[-1])))
+        self.nnz = int(np.asarray(off)[-1])
+        self.ws = B.alloc_ws(B.bgv_fa2_ws_size(self.K, self.nnz))
 
     def step(self):
-        B.bgv_fa2_step(self.K, self.off, self.adj, self.w, self.mass, self.params, self.pos, self.F, self.Fprev,
+        B.bgv_fa2_step(self.K, self.nnz, self.off, self.adj, self.w, self.mass, self.params, self.pos, self.F, self.Fprev,
                        self.speed, self.ws)
 
     def run(self, iterations, use_graph, stream=None):
-        B.bgv_fa2_run(self.K, self.off, self.adj, self.w, self.mass, self.params, iterations, use_graph, self.pos,
+        B.bgv_fa2_run(self.K, self.nnz, self.off, self.adj, self.w, self.mass, self.params, iterations, use_graph, self.pos,
                       self.F, self.Fprev, self.speed, self.ws, stream=stream)
 
     def stats(self):

@@ -78,7 +78,7 @@ def test_host_validation_rejects_bad_arguments(lib):
                              1 << 20, None) == bgv.BGV_EINVAL  # growth 0
     p = bgv.bgv_fa2_default_params()
     p.max_depth = 25
-    assert L.bgv_fa2_step(10, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.byref(p),
+    assert L.bgv_fa2_step(10, 20, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.byref(p),
                           C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), fake_ws, 1 << 30,
                           None) == bgv.BGV_EINVAL
     assert bgv.bgv_strerror(bgv.BGV_ENOSPC) == "workspace too small"
