@@ -128,14 +128,20 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
     if (!use_graph || st == nullptr || iterations < 2) {
         for (int32_t t = 0; t < iterations; ++t)
             BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
-                            scratch, st));
+                            scratch, st, nullptr, t == 0));
         return BGV_OK;
     }
+    // The first step runs outside the graph and builds the attraction plan;
+    // the captured step reuses it.
+    BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch,
+                    st, nullptr, true));
+    if (iterations == 1) return BGV_OK;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const unsigned long long before = launches_issued();
-    int rc = run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st);
+    int rc = run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st,
+                     nullptr, false);
     const unsigned long long per_step = launches_issued() - before;  // captured, not yet run
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc != BGV_OK || ce != cudaSuccess) {
@@ -148,7 +154,7 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
     }
     rc = BGV_OK;
     int32_t replays = 0;
-    for (; replays < iterations && rc == BGV_OK; ++replays)
+    for (; replays < iterations - 1 && rc == BGV_OK; ++replays)
         if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = BGV_ECUDA;
     add_launches(per_step * static_cast<unsigned long long>(replays) - per_step);
     cudaGraphExecDestroy(exec);
@@ -383,7 +389,7 @@ int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         }
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
         rc = run_fa2(1, K, nnz, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
-                     header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per);
+                     header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per, t == 0);
     if (rc == BGV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = BGV_ECUDA;
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
         for (int k = 0; k < kFa2Stages; ++k) {

@@ -187,10 +187,12 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
 // mode 0: forces only (Fr/Fa/Fg outputs, any may be null); mode 1: full step.
 // `marks` (optional) receives kFa2Stages + 1 event records at the stage
 // boundaries: frame+keys, sort, gather, tree, quad, repulsion, node, update.
+// `build_plan` rebuilds the per-CSR attraction plan in the scratch; a loop
+// over one CSR builds it on the first step only.
 constexpr int kFa2Stages = 8;
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
-            cudaEvent_t *marks = nullptr);
+            cudaEvent_t *marks = nullptr, bool build_plan = true);
 
 }  // namespace bgv

@@ -9,14 +9,14 @@
 //               internal node (exponential + binary search on key prefixes)
 //   k_mom_*     exact prefix sums of (m, m*Ux, m*Uy) in 64/128-bit integers
 //               over the Morton order, so a node's moments are a difference
-//   k_quad      quadtree nodes: binary nodes whose 2-bit level exceeds their
-//               parent's; up to four children each; FP32 centre of mass from
-//               the exact moments; leaf flags
+//   k_cells     quadtree cells: binary nodes whose 2-bit level exceeds their
+//               parent's; FP32 centre of mass from the exact moments
+//   k_preorder  cells and bodies laid out in depth-first pre-order with skip
+//               indices (positions from a prefix count of cells per body)
 //   k_repulse   Barnes-Hut repulsion: one warp per 32 Morton-consecutive
-//               bodies walks the union of their traversals with a shared
-//               stack of (node, lane mask) entries; every lane takes its own
-//               opening decisions, so each body's interaction set is exactly
-//               the one the sequential definition gives
+//               bodies walks the union of their traversals without a stack;
+//               every lane takes its own opening decisions, so each body's
+//               interaction set is exactly the one the definition gives
 //   k_attract   attraction over fixed 8-entry chunks of the CSR (balanced
 //               whatever the degrees), row pieces kept per chunk
 //   k_node      per node: attraction pieces in chunk order, gravity, total
@@ -41,12 +41,6 @@ constexpr int kNone = INT32_MIN;       // empty child slot
 
 typedef unsigned __int128 u128;
 
-struct __align__(16) QNode {
-    float4 a;    // decision/force centre x, y; mass; (cell side)^2
-    int4 info;   // first body, last body (Morton positions), leaf flag, level
-    int4 ch;     // children: >= 0 node id, < 0 ~body position, kNone empty
-    int4 pad;
-};
 
 __device__ __forceinline__ unsigned long long spread_bits(uint32_t v) {
     unsigned long long x = v;
@@ -328,14 +322,20 @@ __global__ void __launch_bounds__(kThreads) k_mom_down(const uint2 *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_quad(int64_t K, int L, int leaf_cap, const float4 *__restrict__ frame,
-                                                   const int32_t *__restrict__ left, const int32_t *__restrict__ right,
-                                                   const int32_t *__restrict__ parent, const int2 *__restrict__ range,
-                                                   const int8_t *__restrict__ level,
-                                                   const unsigned long long *__restrict__ PM,
-                                                   const ulonglong2 *__restrict__ PX,
-                                                   const ulonglong2 *__restrict__ PY, QNode *__restrict__ q,
-                                                   unsigned long long *tree_nodes) {
+// Quadtree cells: the binary nodes whose 2-bit level exceeds their parent's
+// (a chain of single-child cells collapses into its deepest cell, which
+// takes the opening test for the whole chain).  For each cell: FP32 centre
+// from the exact moments, mass, and the squared side used by the opening
+// test (+inf for a leaf that is never accepted).  Cells are counted by their
+// first body for the pre-order layout.
+__global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_cap, const float4 *__restrict__ frame,
+                                                    const int32_t *__restrict__ parent,
+                                                    const int2 *__restrict__ range, const int8_t *__restrict__ level,
+                                                    const unsigned long long *__restrict__ PM,
+                                                    const ulonglong2 *__restrict__ PX,
+                                                    const ulonglong2 *__restrict__ PY, float4 *__restrict__ cell,
+                                                    int8_t *__restrict__ topflag, uint32_t *__restrict__ start_count,
+                                                    unsigned long long *tree_nodes) {
     const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     bool top = false;
     if (p < K - 1) {
@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_quad(int64_t K, int L, int leaf_ca
         const int32_t par = parent[p];
         const int par_lev = (par < 0 || int64_t(par) >= K - 1) ? -1 : int(level[par]);
         top = par_lev < lev;
+        topflag[p] = top ? 1 : 0;
         if (top) {
             const int2 rg = range[p];
             const int cnt = rg.y - rg.x + 1;
@@ -352,26 +353,6 @@ __global__ void __launch_bounds__(kThreads) k_quad(int64_t K, int L, int leaf_ca
             // bodies between its parent's level and L; the deepest of them,
             // at level L - 1, takes the opening test for the whole chain.
             const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
-            int4 ch = make_int4(kNone, kNone, kNone, kNone);
-            if (!leaf) {
-                int refs[4];
-                int nref = 0;
-                const int32_t kids[2] = {left[p], right[p]};
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int32_t k = kids[c];
-                    if (k < 0 || int(level[k]) > lev) {
-                        refs[nref++] = k;
-                    } else {  // same 2-bit level: part of this quadtree node
-                        refs[nref++] = left[k];
-                        refs[nref++] = right[k];
-                    }
-                }
-                ch.x = refs[0];
-                ch.y = nref > 1 ? refs[1] : kNone;
-                ch.z = nref > 2 ? refs[2] : kNone;
-                ch.w = nref > 3 ? refs[3] : kNone;
-            }
             const float4 fr = *frame;
             const Mom hi = mom_load(PM, PX, PY, rg.y + 1), lo = mom_load(PM, PX, PY, rg.x);
             const unsigned long long M = hi.M - lo.M;
@@ -380,16 +361,47 @@ __global__ void __launch_bounds__(kThreads) k_quad(int64_t K, int L, int leaf_ca
             const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), 2.3283064365386963e-10f)));
             const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), 2.3283064365386963e-10f)));
             const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
-            QNode nd;
-            nd.a = make_float4(cx, cy, __ull2float_rn(M), __fmul_rn(sl, sl));
-            nd.info = make_int4(rg.x, rg.y, testable ? 2 : (leaf ? 1 : 0), lev);
-            nd.ch = ch;
-            nd.pad = make_int4(0, 0, 0, 0);
-            q[p] = nd;
+            const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
+            cell[p] = make_float4(cx, cy, __ull2float_rn(M), side2);
+            atomicAdd(&start_count[rg.x], 1u);
         }
     }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, top);
     if ((threadIdx.x & 31) == 0 && mask) atomicAdd(tree_nodes, static_cast<unsigned long long>(__popc(mask)));
+}
+
+// Pre-order layout of cells and bodies.  With T[s] = number of cells whose
+// first body precedes s (exclusive scan of the per-body counts):
+//   body s           -> s + T[s+1]       (every cell starting at or before s
+//                                          comes first)
+//   cell [a, b]      -> a + T[a] + (its ancestors that also start at a)
+//   skip(cell [a,b]) -> b + 1 + T[b+1]   (the element after its subtree)
+// Elements are float4 (x, y, mass, side^2), side^2 = -1 for a body.
+__global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int32_t *__restrict__ parent,
+                                                       const int2 *__restrict__ range,
+                                                       const int8_t *__restrict__ topflag,
+                                                       const float4 *__restrict__ cell,
+                                                       const uint32_t *__restrict__ T,
+                                                       const float4 *__restrict__ body, float4 *__restrict__ geo,
+                                                       int32_t *__restrict__ skip) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < K) {
+        const int64_t pre = t + T[t + 1];
+        const float4 b = body[t];
+        geo[pre] = make_float4(b.x, b.y, b.z, -1.0f);
+        skip[pre] = int32_t(pre + 1);
+    }
+    if (t < K - 1 && topflag[t]) {
+        const int2 rg = range[t];
+        int dep = 0;
+        for (int32_t par = parent[t]; par >= 0 && int64_t(par) < K - 1; par = parent[par]) {
+            if (range[par].x != rg.x) break;
+            dep += topflag[par];
+        }
+        const int64_t pre = rg.x + int64_t(T[rg.x]) + dep;
+        geo[pre] = cell[t];
+        skip[pre] = int32_t(int64_t(rg.y) + 1 + T[rg.y + 1]);
+    }
 }
 
 // -------------------------------------------------------------- repulsion
@@ -403,129 +415,57 @@ __device__ __forceinline__ void add_body(float xi, float yi, float kmi, float4 b
     }
 }
 
-// Opening test of the quadtree definition, operation by operation in FP32
-// round-to-nearest (no contraction), so it decides exactly as the oracle.
-__device__ __forceinline__ bool accept_cell(float xi, float yi, float4 a, float theta2, float &dx, float &dy,
-                                            float &d2) {
-    dx = __fsub_rn(xi, a.x);
-    dy = __fsub_rn(yi, a.y);
-    d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-    return a.w < __fmul_rn(theta2, d2);
-}
-
-__global__ void __launch_bounds__(kThreads) k_repulse(const QNode *__restrict__ q, const int32_t *__restrict__ root_p,
+// Barnes-Hut traversal without a stack.  A warp serves 32 Morton-consecutive
+// bodies; every lane holds the pre-order index where its own traversal
+// resumes.  Each step the warp takes the smallest resume index (one redux),
+// loads that element once for all lanes, and only the lanes waiting at it
+// act: a body is summed directly (not self) and passed; a cell holding the
+// lane's body is entered; any other cell is accepted (summed, resume after
+// its subtree) or entered, by the FP32 opening test of the definition.  Each
+// body therefore sees exactly its own interaction set, in depth-first order.
+__global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
+                                                      const uint32_t *__restrict__ T,
                                                       const float4 *__restrict__ body, int64_t K, float kr,
                                                       float theta2, float2 *__restrict__ Frep,
                                                       unsigned long long *inter_step,
-                                                      unsigned long long *inter_total, uint32_t *status) {
-    __shared__ int2 stack[kThreads / 32][kStack];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                                      unsigned long long *inter_total) {
+    const int lane = threadIdx.x & 31;
     const int64_t s0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31);
     if (s0 >= K) return;  // whole warp leaves together
     const int64_t s = s0 + lane;
     const bool active = s < K;
     const float4 bi = active ? body[s] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float xi = bi.x, yi = bi.y, kmi = kr * bi.z;
-    const int si = int(s);
+    const uint32_t total = uint32_t(K + T[K]);
+    const uint32_t self = active ? uint32_t(s + T[s + 1]) : 0xFFFFFFFFu;
+    uint32_t resume = active ? 0u : 0xFFFFFFFFu;
     float fx = 0.0f, fy = 0.0f;
     unsigned inter = 0;
-    int2 *stk = stack[warp];
-    const unsigned am = __ballot_sync(0xFFFFFFFFu, active);
-    const int root = *root_p;
-    if (root < 0 || int64_t(root) >= K - 1) {  // the tree build did not finish
-        if (lane == 0) raise_status(status, BGV_DEV_STACK);
-        return;
+    while (true) {
+        const uint32_t cur = __reduce_min_sync(0xFFFFFFFFu, resume);
+        if (cur >= total) break;
+        const float4 e = geo[cur];
+        const uint32_t sk = uint32_t(skip[cur]);
+        if (resume != cur) continue;
+        resume = cur + 1;
+        if (e.w < 0.0f) {  // a body
+            if (cur != self) {
+                add_body(xi, yi, kmi, e, fx, fy);
+                ++inter;
+            }
+        } else if (!(self > cur && self < sk)) {  // a cell not holding this body
+            const float dx = __fsub_rn(xi, e.x), dy = __fsub_rn(yi, e.y);
+            const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            if (e.w < __fmul_rn(theta2, d2)) {
+                const float f = __fdividef(kmi * e.z, d2);
+                fx += f * dx;
+                fy += f * dy;
+                ++inter;
+                resume = sk;
+            }
+        }
     }
-    if (lane == 0) stk[0] = make_int2(root, int(am));
-    int sp = 1;
-    __syncwarp();
-    while (sp > 0) {
-        --sp;
-        const int2 e = stk[sp];
-        __syncwarp();
-        const QNode *nd = q + e.x;
-        const int4 info = nd->info;
-        const float4 a = nd->a;
-        const int4 ch = nd->ch;
-        const bool mine = (unsigned(e.y) >> lane) & 1u;
-        const bool own = si >= info.x && si <= info.y;
-        if (info.z) {  // leaf: every body except self (a depth leaf may be accepted whole)
-            bool direct = mine;
-            if (mine && info.z == 2 && !own) {
-                float dx, dy, d2;
-                if (accept_cell(xi, yi, a, theta2, dx, dy, d2)) {
-                    const float f = __fdividef(kmi * a.z, d2);
-                    fx += f * dx;
-                    fy += f * dy;
-                    ++inter;
-                    direct = false;
-                }
-            }
-            if (__any_sync(0xFFFFFFFFu, direct)) {
-                for (int t = info.x; t <= info.y; ++t) {
-                    const float4 bj = body[t];
-                    if (direct && t != si) {
-                        add_body(xi, yi, kmi, bj, fx, fy);
-                        ++inter;
-                    }
-                }
-            }
-            continue;
-        }
-        bool open = false;
-        if (mine) {
-            if (own) {
-                open = true;  // the cell holds this body
-            } else {
-                float dx, dy, d2;
-                if (accept_cell(xi, yi, a, theta2, dx, dy, d2)) {
-                    const float f = __fdividef(kmi * a.z, d2);
-                    fx += f * dx;
-                    fy += f * dy;
-                    ++inter;
-                } else {
-                    open = true;
-                }
-            }
-        }
-        const unsigned om = __ballot_sync(0xFFFFFFFFu, open);
-        if (!om) continue;
-        // Children in order; single bodies are summed at once, cells pushed
-        // (last child first, so the first child is visited next).
-        const int kids[4] = {ch.x, ch.y, ch.z, ch.w};
-        int npush = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = kids[c];
-            if (k == kNone) continue;
-            if (k < 0) {
-                const int b = ~k;
-                const float4 bj = body[b];
-                if (open && b != si) {
-                    add_body(xi, yi, kmi, bj, fx, fy);
-                    ++inter;
-                }
-            } else {
-                ++npush;
-            }
-        }
-        if (sp + npush > kStack) {
-            if (lane == 0) raise_status(status, BGV_DEV_STACK);
-            break;
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int c = 3; c >= 0; --c)
-                if (kids[c] >= 0) stk[sp++] = make_int2(kids[c], int(om));
-        } else {
-            sp += npush;
-        }
-        __syncwarp();
-    }
-    if (active) {
-        const int orig = __float_as_int(bi.w);
-        Frep[orig] = make_float2(fx, fy);
-    }
+    if (active) Frep[__float_as_int(bi.w)] = make_float2(fx, fy);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) inter += __shfl_xor_sync(0xFFFFFFFFu, inter, d);
     if (lane == 0 && inter) {
@@ -545,16 +485,38 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const QNode *__restrict__ 
 // k_node adds a row's pieces in chunk order, so the sum order is fixed.
 constexpr int kChunk = 8;
 
-__device__ __forceinline__ int64_t row_containing(const int32_t *__restrict__ off, int64_t K, int64_t e) {
-    int64_t lo = 0, hi = K;  // off[lo] <= e < off[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (int64_t(__ldg(&off[mid])) <= e) lo = mid; else hi = mid;
+// The row of each chunk's first entry, written once per CSR (the plan): the
+// thread of row r writes r into every chunk that starts inside the row; a
+// warp shares the writes of rows that cover many chunks.
+constexpr int kLongRowChunks = 32;
+
+__global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+                                                         int32_t *__restrict__ chunk_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); base < K; base += stride) {
+        const int64_t r = base + lane;
+        int64_t g0 = 0, g1 = 0;
+        if (r < K) {
+            const int64_t b = off[r], e = off[r + 1] < nnz ? off[r + 1] : nnz;
+            g0 = (b + kChunk - 1) / kChunk;
+            g1 = (e + kChunk - 1) / kChunk;
+        }
+        const bool longrow = g1 - g0 > kLongRowChunks;
+        if (!longrow)
+            for (int64_t g = g0; g < g1; ++g) chunk_row[g] = int32_t(r);
+        unsigned lm = __ballot_sync(0xFFFFFFFFu, longrow);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t a = __shfl_sync(0xFFFFFFFFu, g0, src), z = __shfl_sync(0xFFFFFFFFu, g1, src);
+            for (int64_t g = a + lane; g < z; g += 32) chunk_row[g] = int32_t(base + src);
+        }
     }
-    return lo;
 }
 
 __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+                                                      const int32_t *__restrict__ chunk_row,
                                                       const int32_t *__restrict__ adj,
                                                       const uint32_t *__restrict__ w, const float2 *__restrict__ pos,
                                                       float2 *__restrict__ full, float2 *__restrict__ head,
@@ -563,7 +525,7 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
         const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
-        int64_t r = row_containing(off, K, e0);
+        int64_t r = chunk_row[g];
         int64_t rs = off[r], re = off[r + 1];
         float2 pi = pos[r];
         float ax = 0.0f, ay = 0.0f;
@@ -646,12 +608,22 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
                                                    float2 *__restrict__ Fg_out, double2 *part, double *speed,
                                                    float tau, WsHeader *hdr) {
     Comp S{0.0, 0.0}, T{0.0, 0.0};
+    const int lane = threadIdx.x & 31;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
-        const int64_t b = off[i], e = off[i + 1];
+    for (int64_t base = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); base < K; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < K;
+        int64_t g1 = 0, g2 = -1;
         float ax = 0.0f, ay = 0.0f;
-        if (e > b) {
-            const int64_t g1 = b / kChunk, g2 = (e - 1) / kChunk;
+        if (valid) {
+            const int64_t b = off[i], e = off[i + 1];
+            if (e > b) {
+                g1 = b / kChunk;
+                g2 = (e - 1) / kChunk;
+            }
+        }
+        const bool longrow = g2 - g1 > kLongRowChunks;
+        if (valid && g2 >= g1 && !longrow) {
             if (g1 == g2) {
                 const float2 v = full[i];
                 ax = v.x;
@@ -667,6 +639,31 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
                 }
             }
         }
+        // Rows spread over many chunks: the warp sums their pieces, each lane
+        // a strided subset, then a fixed butterfly; the order is fixed.
+        unsigned lm = __ballot_sync(0xFFFFFFFFu, longrow);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t a = __shfl_sync(0xFFFFFFFFu, g1, src), z = __shfl_sync(0xFFFFFFFFu, g2, src);
+            float px = 0.0f, py = 0.0f;
+            for (int64_t g = a + 1 + lane; g <= z; g += 32) {
+                const float2 v = head[g];
+                px += v.x;
+                py += v.y;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                px += __shfl_xor_sync(0xFFFFFFFFu, px, d);
+                py += __shfl_xor_sync(0xFFFFFFFFu, py, d);
+            }
+            if (lane == src) {
+                const float2 t = tail[a];
+                ax = t.x + px;
+                ay = t.y + py;
+            }
+        }
+        if (!valid) continue;
         const float2 pi = pos[i];
         const float m = __uint2float_rn(mass[i]);
         float gx, gy;
@@ -788,9 +785,16 @@ struct Fa2Scratch {
     int8_t *level;
     unsigned long long *PM, *TM;   // moment prefix sums, per-tile sums
     ulonglong2 *PX, *PY, *TX, *TY;
-    QNode *q;
+    float4 *cell;          // per binary node: centre, mass, side^2 (cells only)
+    int8_t *topflag;       // per binary node: is a quadtree cell
+    uint32_t *start_count; // cells per first body
+    uint32_t *T;           // exclusive scan of start_count, K + 1 entries
+    void *scan_tmp;
+    float4 *geo;           // pre-order elements (cells and bodies)
+    int32_t *skip;         // pre-order index after each element's subtree
     float2 *Frep;
     float2 *full, *head, *tail;
+    int32_t *chunk_row;   // plan: row of each chunk's first entry
     double2 *part;  // two per block: (S, comp), (T, comp)
 };
 
@@ -817,11 +821,18 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, Fa2Scratch &s) {
     s.TM = c.take<unsigned long long>(tiles);
     s.TX = c.take<ulonglong2>(tiles);
     s.TY = c.take<ulonglong2>(tiles);
-    s.q = c.take<QNode>(k);
+    s.cell = c.take<float4>(k);
+    s.topflag = c.take<int8_t>(k);
+    s.start_count = c.take<uint32_t>(k + 1);
+    s.T = c.take<uint32_t>(k + 1);
+    s.scan_tmp = c.take<char>(scan_tmp_bytes(int64_t(k) + 1));
+    s.geo = c.take<float4>(2 * k);
+    s.skip = c.take<int32_t>(2 * k);
     s.Frep = c.take<float2>(k);
     s.full = c.take<float2>(k);
     s.head = c.take<float2>(chunks);
     s.tail = c.take<float2>(chunks);
+    s.chunk_row = c.take<int32_t>(chunks);
     s.part = c.take<double2>(2 * kNodeBlocks);
 }
 
@@ -855,7 +866,8 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
 
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
-            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks) {
+            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
+            bool build_plan) {
     if (K <= 0) return BGV_OK;
     Carver c(scratch, 0);
     Fa2Scratch s;
@@ -897,14 +909,19 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         note_launch(), k_mom_down<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY, s.PM, s.PX, s.PY);
         BGV_TRY(launch_status());
         BGV_TRY(mark(4));
-        note_launch(), k_quad<<<gi, kThreads, 0, st>>>(K, L, p.leaf_cap, s.frame, s.left, s.right, s.parent, s.range,
-                                                       s.level, s.PM, s.PX, s.PY, s.q, &hdr->tree_nodes);
+        BGV_CUDA(cudaMemsetAsync(s.start_count, 0, sizeof(uint32_t) * size_t(K), st));
+        note_launch(), k_cells<<<gi, kThreads, 0, st>>>(K, L, p.leaf_cap, s.frame, s.parent, s.range, s.level, s.PM,
+                                                        s.PX, s.PY, s.cell, s.topflag, s.start_count,
+                                                        &hdr->tree_nodes);
+        BGV_TRY(launch_status());
+        BGV_TRY(scan_exclusive(s.start_count, s.T, K, nullptr, nullptr, true, s.scan_tmp, st));
+        note_launch(), k_preorder<<<gt, kThreads, 0, st>>>(K, s.parent, s.range, s.topflag, s.cell, s.T, s.body,
+                                                           s.geo, s.skip);
         BGV_TRY(launch_status());
         BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;
-        note_launch(), k_repulse<<<gt, kThreads, 0, st>>>(s.q, s.root, s.body, K, p.kr, theta2, s.Frep,
-                                                          &hdr->interactions, &hdr->interactions_total,
-                                                          &hdr->status);
+        note_launch(), k_repulse<<<gt, kThreads, 0, st>>>(s.geo, s.skip, s.T, s.body, K, p.kr, theta2, s.Frep,
+                                                          &hdr->interactions, &hdr->interactions_total);
         BGV_TRY(launch_status());
     } else {
         BGV_CUDA(cudaMemsetAsync(s.Frep, 0, sizeof(float2), st));
@@ -913,8 +930,13 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     }
     BGV_TRY(mark(6));
     if (nnz > 0) {
+        if (build_plan) {
+            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, st>>>(K, nnz, csr_off,
+                                                                                             s.chunk_row);
+            BGV_TRY(launch_status());
+        }
         note_launch(), k_attract<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0, st>>>(
-            K, nnz, csr_off, csr_adj, csr_w, pos, s.full, s.head, s.tail);
+            K, nnz, csr_off, s.chunk_row, csr_adj, csr_w, pos, s.full, s.head, s.tail);
         BGV_TRY(launch_status());
     }
     note_launch(), k_node<<<kNodeBlocks, kThreads, 0, st>>>(mode, K, csr_off, s.full, s.head, s.tail, mass, pos,
