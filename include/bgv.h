@@ -63,6 +63,7 @@ extern "C" {
 #define BGV_ENOSPC 2   /* ws_bytes smaller than the *_ws_size query */
 #define BGV_EDEVICE 3  /* the device reported an error (see the status word) */
 #define BGV_ECUDA 4    /* a CUDA launch or copy failed */
+#define BGV_ELIMIT 5   /* a size exceeds the fixed scratch of a no-allocation entry point */
 
 /* Bits of the device status word. */
 #define BGV_DEV_BADEDGE 1u     /* an edge endpoint outside [0, n) */
@@ -102,6 +103,23 @@ size_t bgv_sketch_degrees_ws_size(int64_t m, int32_t n, int32_t rows, int32_t wi
 int bgv_sketch_degrees(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width,
                        uint64_t seed, uint32_t *sketch, uint32_t *deg_est,
                        void *ws, size_t ws_bytes, void *stream);
+
+/* The same degree sketch for callers that cannot allocate device memory
+ * (for example code running while a stream is captured, or a plugin whose
+ * host application owns all device memory).  The paper has no counterpart:
+ * this entry point only changes where the scratch lives.  The per-node
+ * degree counters sit in a fixed array of device memory inside the library
+ * (at most 4,194,304 nodes, 16 MiB, held by every GPU that loads the
+ * library until exit) instead of a caller workspace; larger n returns
+ * BGV_ELIMIT.  The first call on each device looks up the array's device
+ * address (make it before any stream capture); every call clears the
+ * counters, and all calls on a device share them, so calls whose work can
+ * overlap on the GPU race and must be ordered on one stream.  Device-detected
+ * bad edges are OR-ed into *status (device uint32, may be NULL).
+ * Arguments otherwise as bgv_sketch_degrees. */
+int bgv_sketch_degrees_noalloc(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width,
+                               uint64_t seed, uint32_t *sketch, uint32_t *deg_est, uint32_t *status,
+                               void *stream);
 
 /* ------------------------------------------------------------------------
  * 2. Community rounds (Algorithm 3; Section 3.2.1; Section 4.2.2).

@@ -18,7 +18,7 @@ if not _LIB_PATH.exists():
     raise ImportError(f"libbgv.so not found at {_LIB_PATH}; build it with paper_2108_00529_gb300.build.build()")
 _lib = C.CDLL(str(_LIB_PATH))
 
-BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA = 0, 1, 2, 3, 4
+BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA, BGV_ELIMIT = 0, 1, 2, 3, 4, 5
 BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_STACK, BGV_DEV_TIMEOUT = 1, 2, 4, 8
 
 P = C.c_void_p
@@ -55,6 +55,7 @@ _sig("bgv_ws_init", C.c_int, [P, P])
 _sig("bgv_status", C.c_int, [P, P, C.POINTER(u32), C.c_int])
 _sig("bgv_sketch_degrees_ws_size", sz, [i64, i32, i32, i32])
 _sig("bgv_sketch_degrees", C.c_int, [P, i64, i32, i32, i32, u64, P, P, P, sz, P])
+_sig("bgv_sketch_degrees_noalloc", C.c_int, [P, i64, i32, i32, i32, u64, P, P, P, P])
 _sig("bgv_communities_ws_size", sz, [i64, i32])
 _sig("bgv_communities", C.c_int, [P, i64, i32, P, i32, u32, u32, i32, P, P, P, sz, P])
 _sig("bgv_supergraph_ws_size", sz, [i64, i32, i32, i32])
@@ -78,7 +79,7 @@ _sig("bgv_layout_host", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, 
                                   C.POINTER(i64), P, sz, P])
 
 #: every symbol this binding resolves from the library
-EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees",
+EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees", "bgv_sketch_degrees_noalloc",
            "bgv_communities_ws_size", "bgv_communities", "bgv_supergraph_ws_size", "bgv_supergraph",
            "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
            "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
@@ -153,6 +154,13 @@ def bgv_sketch_degrees_ws_size(m: int, n: int, rows: int, width: int) -> int:
 def bgv_sketch_degrees(edges, m, n, rows, width, seed, sketch, deg_est, ws, ws_bytes=None, stream=None):
     _chk(_lib.bgv_sketch_degrees(_p(edges), m, n, rows, width, seed, _p(sketch), _p(deg_est), _p(ws),
                                  _nbytes(ws, ws_bytes), _s(stream)), "bgv_sketch_degrees")
+
+
+def bgv_sketch_degrees_noalloc(edges, m, n, rows, width, seed, sketch, deg_est, status=None, stream=None):
+    """Degree sketch without a workspace, for callers that cannot allocate
+    device memory (scratch in a fixed device array, n <= 4,194,304)."""
+    _chk(_lib.bgv_sketch_degrees_noalloc(_p(edges), m, n, rows, width, seed, _p(sketch), _p(deg_est), _p(status),
+                                         _s(stream)), "bgv_sketch_degrees_noalloc")
 
 
 def bgv_communities_ws_size(m: int, n: int) -> int:

@@ -230,6 +230,7 @@ const char *bgv_strerror(int code) {
         case BGV_ENOSPC: return "workspace too small";
         case BGV_EDEVICE: return "device reported an error (see the status word)";
         case BGV_ECUDA: return "CUDA error";
+        case BGV_ELIMIT: return "size exceeds the fixed scratch of a no-allocation entry point";
         default: return "unknown error";
     }
 }

@@ -8,6 +8,8 @@
 //
 // Edges are read as int4 (two edges per 16-byte load) with a grid-stride
 // loop over a grid sized to fill the GPU.
+#include <mutex>
+
 #include "bgv_internal.cuh"
 
 namespace bgv {
@@ -108,3 +110,71 @@ int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, 
 }
 
 }  // namespace bgv
+
+// ------------------------------------------------------------------------
+// bgv_sketch_degrees_noalloc: the degree sketch for callers that cannot
+// allocate device memory.
+//
+// Some callers may not call cudaMalloc at all: a plugin running inside a
+// host application whose device memory is owned by another allocator, code
+// that runs while a stream is being captured (cudaMalloc is not allowed
+// there), or real-time callers that must not allocate on their hot path.
+// They cannot hand this library a workspace, so this entry point keeps the
+// one scratch array the sketch needs -- the per-node degree counters -- in a
+// fixed-size array of device memory that is part of the library image.  The
+// caller still provides the edges, the sketch and the estimates.
+//
+// Size limit: n <= kNoAllocMaxNodes (4,194,304 nodes, 16 MiB of counters).
+// Every GPU that loads the library holds that array until the process exits.
+// All calls on a device share it and it keeps the last call's contents; the
+// counters are cleared at the start of every call.  Calls whose work
+// overlaps on the GPU (different streams, no ordering between them) race on
+// the shared counters and give wrong results: order them on one stream.
+namespace bgv {
+namespace {
+constexpr int32_t kNoAllocMaxNodes = 1 << 22;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Degree counters followed by one status word used when the caller passes
+// no status pointer.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxNodes + 64];
+
+std::mutex g_noalloc_mutex;
+uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// The array's name is a host-side stand-in in host code, not a device
+// address: the address a kernel may use is looked up once per device, with
+// that device current, on the first call.
+int noalloc_scratch(uint32_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return BGV_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BGV_ECUDA;
+        g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return BGV_OK;
+}
+}  // namespace
+
+}  // namespace bgv
+
+extern "C" int bgv_sketch_degrees_noalloc(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width,
+                                          uint64_t seed, uint32_t *sketch, uint32_t *deg_est, uint32_t *status,
+                                          void *stream) {
+    using namespace bgv;
+    if (n < 1 || m < 0 || m >= (int64_t(1) << 31)) return BGV_EINVAL;
+    if (m > 0 && (!edges || reinterpret_cast<uintptr_t>(edges) % 16 != 0)) return BGV_EINVAL;
+    if (rows < 1 || rows > kMaxRows || width < 1 || !sketch || !deg_est) return BGV_EINVAL;
+    if (n > kNoAllocMaxNodes) return BGV_ELIMIT;
+    uint32_t *scratch = nullptr;
+    BGV_TRY(noalloc_scratch(&scratch));
+    SketchScratch s;
+    s.deg = scratch;
+    uint32_t *st = status ? status : scratch + kNoAllocMaxNodes;
+    const HashFamily h = make_hash_family(seed, rows, uint32_t(width));
+    return run_sketch(edges, m, n, h, sketch, deg_est, s, st, static_cast<cudaStream_t>(stream));
+}
+
