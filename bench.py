@@ -52,6 +52,10 @@ WORKLOADS = {
     "rmat22x": dict(desc="R-MAT scale 22 restricted to 3,200,000 nodes, 34,000,000 unique edges, "
                          "a,b,c,d=.45,.22,.22,.11", rows=4, width=65536, passes=3, threshold=0, growth=2,
                     iterations=500),
+    "lnpp1m": dict(desc="precision form: ForceAtlas2 on the whole 1,000,000-node, 8,000,000-edge planted "
+                        "partition (256 communities of lognormal(8, 1) size), nodes coloured by their streamed "
+                        "community", rows=4, width=65536, passes=3, threshold=0, growth=2, iterations=500,
+                   whole=True),
 }
 
 
@@ -374,6 +378,161 @@ def gpu_arm(args, dist: Dist):
     return out
 
 
+def gpu_arm_whole(args, dist: Dist):
+    """Precision form: ForceAtlas2 directly on the whole graph (mass = degree
+    + 1, unit weights), nodes coloured by their streamed community.  A step
+    is sketch + community rounds + colour groups + whole-graph CSR + initial
+    positions + the FA2 iterations."""
+    import torch
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        from paper_2108_00529_gb300 import build
+        build.build()
+        graphgen.load(args.workload)
+    dist.barrier()
+    from paper_2108_00529_gb300 import load
+    B = load()
+    cfg = WORKLOADS[args.workload]
+    n, edges_np, _ = graphgen.load(args.workload)
+    m = edges_np.shape[0]
+    thr = cfg["threshold"] or (2 * m) // n
+    rows, width, passes, growth = cfg["rows"], cfg["width"], cfg["passes"], cfg["growth"]
+    iters = args.fa2_iterations or cfg["iterations"]
+    s = torch.cuda.Stream(device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    E = torch.from_numpy(edges_np).to(dev)
+    S, dh, labels = torch.zeros(rows * width, **i32), torch.zeros(n, **i32), torch.zeros(n, **i32)
+    node_map, Kd, Esd = torch.zeros(n, **i32), torch.zeros(1, dtype=torch.int64, device=dev), \
+        torch.zeros(1, dtype=torch.int64, device=dev)
+    ssrc, sdst, sw = (torch.zeros(m, **i32) for _ in range(3))
+    smass, soff = torch.zeros(n, **i32), torch.zeros(n + 1, **i32)
+    sadj, scw = torch.zeros(2 * m, **i32), torch.zeros(2 * m, **i32)
+    group = torch.zeros(n, dtype=torch.uint8, device=dev)
+    colour = torch.zeros(n, dtype=torch.uint8, device=dev)
+    off, adj, cw = torch.zeros(n + 1, **i32), torch.zeros(2 * m, **i32), torch.zeros(2 * m, **i32)
+    mass, nnz_d = torch.zeros(n, **i32), torch.zeros(1, dtype=torch.int64, device=dev)
+    pos = torch.zeros((n, 2), dtype=torch.float32, device=dev)
+    F, Fprev = torch.zeros_like(pos), torch.zeros_like(pos)
+    speed = torch.zeros(1, dtype=torch.float64, device=dev)
+    ws_sk = B.alloc_ws(B.bgv_sketch_degrees_ws_size(m, n, rows, width), dev)
+    ws_cm = B.alloc_ws(B.bgv_communities_ws_size(m, n), dev)
+    ws_cs = B.alloc_ws(B.bgv_graph_csr_ws_size(m, n), dev)
+    ws_sg = B.alloc_ws(B.bgv_supergraph_ws_size(m, n, rows, width), dev)
+    ws_cg = B.alloc_ws(B.bgv_colour_groups_ws_size(n), dev)
+    ws_fa = B.alloc_ws(B.bgv_fa2_ws_size(n, 2 * m), dev)
+    fp = B.bgv_fa2_default_params()
+    nnz_h = torch.zeros(1, dtype=torch.int64).pin_memory()
+    K_h = torch.zeros(1, dtype=torch.int64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(s):
+            ev[0].record(s)
+            B.bgv_sketch_degrees(E, m, n, rows, width, 1, S, dh, ws_sk, stream=s)
+            B.bgv_communities(E, m, n, dh, passes, thr, growth, 0, labels, None, ws_cm, stream=s)
+            # each node takes the colour of its community's supernode
+            B.bgv_supergraph(E, m, n, labels, dh, rows, width, 1, node_map, Kd, ssrc, sdst, sw, Esd, smass, soff,
+                             sadj, scw, None, None, None, ws_sg, stream=s)
+            K_h.copy_(Kd, non_blocking=True)
+        s.synchronize()
+        K = int(K_h.item())
+        with torch.cuda.stream(s):
+            B.bgv_colour_groups(K, smass, group, ws_cg, n=n, node_map=node_map, node_colour=colour, stream=s)
+            ev[1].record(s)
+            B.bgv_graph_csr(E, m, n, off, adj, cw, mass, nnz_d, ws_cs, stream=s)
+            ev[2].record(s)
+            nnz_h.copy_(nnz_d, non_blocking=True)
+        s.synchronize()
+        nnz = int(nnz_h.item())
+        with torch.cuda.stream(s):
+            B.bgv_fa2_init(n, fp, pos, Fprev, speed, stream=s)
+            stages = B.bgv_fa2_run_timed(n, nnz, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa,
+                                         stream=s)
+            ev[3].record(s)
+        s.synchronize()
+        t = [ev[0].elapsed_time(ev[i]) for i in range(1, 4)]
+        return dict(total=t[2], communities=t[0], graph_csr=t[1] - t[0], fa2=t[2] - t[1], fa2_stages=stages,
+                    nnz=nnz)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        step()
+    st0 = B.bgv_fa2_read_stats(ws_fa, s)
+    launches0 = B.bgv_launch_count()
+    clocks = ClockSampler([dist.local] if dist.world == 1 else None)
+    clocks.start()
+    results = []
+    for _ in range(args.steps):
+        flush.zero_()
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        results.append(step())
+        torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = B.bgv_launch_count() - launches0
+    st1 = B.bgv_fa2_read_stats(ws_fa, s)
+    ms = dist.max(float(np.mean([r["total"] for r in results])))
+    fa2_ms = float(np.mean([r["fa2"] for r in results]))
+    stage = {nm: float(np.mean([r["fa2_stages"][i] for r in results])) for i, nm in enumerate(B.FA2_STAGE_NAMES)}
+    inter = (st1.interactions_total - st0.interactions_total) / max(st1.steps_total - st0.steps_total, 1)
+    rep_ms = stage["repulsion"] / iters
+    ach = inter * FLOPS_PER_INTERACTION / (rep_ms * 1e-3) / 1e12
+    out = {
+        "metric": METRIC, "value": round(m * dist.world / (ms * 1e-3), 1), "unit": "edges/s",
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m, "fa2_iterations": iters,
+                   "theta": 1.2, "kr": 2.0, "kg": 1.0, "mass": "degree + 1",
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "fa2_iters_per_s": round(iters / (fa2_ms * 1e-3), 2),
+        "stage_ms": {k: round(float(np.mean([r[k] for r in results])), 4)
+                     for k in ("communities", "graph_csr", "fa2")},
+        "fa2_stage_ms": {k: round(v, 4) for k, v in stage.items()},
+        "roofline": {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(ach, 3),
+                     "peak": round(fp32_peak_tflops(), 2), "unit": "TFLOP/s",
+                     "frac": round(ach / fp32_peak_tflops(), 4), "traffic": None,
+                     "interactions_per_launch": int(inter), "launch_ms": round(rep_ms, 4)},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if args.precision_sample:
+        import oracle
+        # per-step error of the FP32 forces against the FP64 oracle on a
+        # sample of nodes, same tree and theta
+        off_h, adj_h = off.cpu().numpy(), adj.cpu().numpy()
+        cw_h, mass_h = cw.cpu().numpy().view(np.uint32), mass.cpu().numpy().view(np.uint32)
+        nnz = results[-1]["nnz"]
+        adj_h, cw_h = adj_h[:nnz], cw_h[:nnz]
+        which = np.random.default_rng(4).choice(n, size=min(args.precision_sample, n), replace=False)
+        p = oracle.FA2Params()
+        Fr, Fa, Fg = (torch.zeros_like(pos) for _ in range(3))
+        ws_f = B.alloc_ws(B.bgv_fa2_ws_size(n, nnz), dev)
+        B.bgv_fa2_init(n, fp, pos, Fprev, speed, stream=s)
+        log = {}
+        done = 0
+        for t in sorted({0, iters // 4, iters // 2, iters}):
+            if t > done:
+                B.bgv_fa2_run(n, nnz, off, adj, cw, mass, fp, t - done, 1, pos, F, Fprev, speed, ws_fa, stream=s)
+                done = t
+            B.bgv_fa2_forces(n, nnz, off, adj, cw, mass, fp, pos, Fr, Fa, Fg, ws_f, stream=s)
+            s.synchronize()
+            ph = pos.cpu().numpy()
+            F32 = (Fr + Fa + Fg).cpu().numpy().astype(np.float64)[which]
+            F64 = (oracle.bh_repulsion(ph, mass_h, p, which=which)[0]
+                   + oracle.attraction(off_h, adj_h, cw_h, ph)[which]
+                   + oracle.gravity(mass_h, ph, p.kg, p.strong_gravity)[which])
+            nrm = np.linalg.norm(F64, axis=1)
+            rel = np.linalg.norm(F32 - F64, axis=1) / np.maximum(nrm, 1e-3 * np.sqrt(np.mean(nrm ** 2)))
+            log[str(t)] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
+                           "median": float(np.median(rel))}
+        out["precision"] = {"sample": int(which.shape[0]), "reference": "FP64 oracle, same tree and theta",
+                            "rel_err_by_step": log}
+    return out
+
+
 def reference_arm(args, dist: Dist):
     """The oracle as the reference implementation, on the host cores."""
     if dist.rank != 0:
@@ -414,12 +573,19 @@ def main():
                     help="override the workload's FA2 iteration count (short profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--precision-sample", type=int, default=0,
+                    help="whole-graph workloads: nodes sampled for the FP64 force-error report")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     dist = Dist()
     try:
-        out = reference_arm(args, dist) if args.impl == "reference" else gpu_arm(args, dist)
+        if args.impl == "reference":
+            out = reference_arm(args, dist)
+        elif WORKLOADS[args.workload].get("whole"):
+            out = gpu_arm_whole(args, dist)
+        else:
+            out = gpu_arm(args, dist)
     finally:
         dist.close()
     if out is not None and dist.rank == 0:

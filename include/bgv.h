@@ -171,6 +171,29 @@ int bgv_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
                    uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
                    void *ws, size_t ws_bytes, void *stream);
 
+/* Whole-graph CSR for ForceAtlas2 on the graph itself (Section 4.1: a layout
+ * of the whole graph, coloured by the detected communities).  Row v lists
+ * the distinct neighbours of v in ascending order; csr_w is the number of
+ * edges joining the pair (1 for a simple graph); self-loops are ignored;
+ * mass[v] = (number of distinct neighbours) + 1 (FA2's deg + 1).
+ *   csr_off [n+1] int32, csr_adj [2m] int32, csr_w [2m] uint32, mass [n]
+ *   uint32; *nnz_dev (device int64) receives csr_off[n]. */
+size_t bgv_graph_csr_ws_size(int64_t m, int32_t n);
+int bgv_graph_csr(const int32_t *edges, int64_t m, int32_t n, int32_t *csr_off, int32_t *csr_adj, uint32_t *csr_w,
+                  uint32_t *mass, int64_t *nnz_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Supernode colour groups (Section 4.3).  Communities are ordered by size
+ * ascending (ties by index); group 0 (drawn brown) is the longest prefix of
+ * that order whose sizes sum to at most half of the total; the remaining R
+ * communities get group 1 + floor(10 * rank / R), small to big (the paper's
+ * ten named colours).  sizes [K] uint32 (in, e.g. supernode masses),
+ * group [K] uint8 (out).  Optionally (node_colour != NULL) every node v of a
+ * whole-graph drawing takes its supernode's colour:
+ * node_colour[v] = group[node_map[v]] for node_map [n] int32. */
+size_t bgv_colour_groups_ws_size(int64_t K);
+int bgv_colour_groups(int64_t K, const uint32_t *sizes, uint8_t *group, int32_t n, const int32_t *node_map,
+                      uint8_t *node_colour, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * 4. ForceAtlas2 (Section 3.1; Algorithm 1; the force model and adaptive
  *    speed of Jacomy et al. 2014 that the paper's implementation follows).

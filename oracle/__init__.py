@@ -85,6 +85,8 @@ def lib():
         L.orc_attraction.argtypes = [i64, P, P, P, P, P]
         L.orc_gravity.restype = C.c_int
         L.orc_gravity.argtypes = [i64, P, P, f64, i32, P]
+        L.orc_colour_groups.restype = C.c_int
+        L.orc_colour_groups.argtypes = [i64, P, P]
         L.orc_fa2_step.restype = C.c_int
         L.orc_fa2_step.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P]
         _lib = L
@@ -186,6 +188,14 @@ def supergraph(edges, n: int, labels, dhat, rows: int, width: int, seed: int):
     return dict(node_map=node_map[:n], K=k, src=src[:es], dst=dst[:es], w=w[:es], Es=es, mass=mass[:k],
                 vol=vol[:k], count=cnt[:k], comm_label=cl[:k], csr_off=off[:k + 1], csr_adj=adj[:2 * es],
                 csr_w=cw[:2 * es])
+
+
+def colour_groups(sizes) -> np.ndarray:
+    """Section 4.3 colour group (0 = the small half, 1..10 by size) per community."""
+    sz = np.ascontiguousarray(sizes, dtype=np.uint32)
+    g = np.zeros(max(sz.shape[0], 1), np.uint8)
+    _chk(lib().orc_colour_groups(sz.shape[0], _p(sz), _p(g)))
+    return g[:sz.shape[0]]
 
 
 def modularity(edges, n: int, labels) -> float:

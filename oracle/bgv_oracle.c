@@ -819,3 +819,50 @@ int orc_fa2_step(int64_t K, const int32_t *csr_off, const int32_t *csr_adj, cons
     free(Fr); free(Fa); free(Fg);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Supernode colours (Section 4.3).                                           */
+/* ------------------------------------------------------------------------ */
+
+static const uint32_t *g_sizes;
+static int cmp_by_size(const void *x, const void *y)
+{
+    int64_t i = *(const int64_t *)x, j = *(const int64_t *)y;
+    if (g_sizes[i] != g_sizes[j]) return g_sizes[i] < g_sizes[j] ? -1 : 1;
+    return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+/* Section 4.3: with alpha the sum of all community sizes, the smallest
+ * communities that together take half of alpha are drawn brown (group 0);
+ * the rest are split into ten groups from small to big (groups 1..10).
+ * Reading: order by size ascending (ties by id); group 0 holds the longest
+ * prefix whose sizes sum to at most alpha / 2; the remaining R communities,
+ * in the same order, get group 1 + floor(10 * rank / R). */
+int orc_colour_groups(int64_t K, const uint32_t *size, uint8_t *group)
+{
+    if (K < 0) return ORC_EINVAL;
+    if (K == 0) return ORC_OK;
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    if (!order) return ORC_ENOMEM;
+    uint64_t total = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        order[k] = k;
+        total += size[k];
+    }
+    g_sizes = size;
+    qsort(order, (size_t)K, sizeof(int64_t), cmp_by_size);
+    uint64_t cum = 0;
+    int64_t half = 0;
+    while (half < K && 2 * (cum + size[order[half]]) <= total) {
+        cum += size[order[half]];
+        ++half;
+    }
+    int64_t rest = K - half;
+    for (int64_t r = 0; r < K; ++r) {
+        int64_t k = order[r];
+        if (r < half) group[k] = 0;
+        else group[k] = (uint8_t)(1 + (10 * (r - half)) / rest);
+    }
+    free(order);
+    return ORC_OK;
+}

@@ -60,6 +60,10 @@ _sig("bgv_communities_ws_size", sz, [i64, i32])
 _sig("bgv_communities", C.c_int, [P, i64, i32, P, i32, u32, u32, i32, P, P, P, sz, P])
 _sig("bgv_supergraph_ws_size", sz, [i64, i32, i32, i32])
 _sig("bgv_supergraph", C.c_int, [P, i64, i32, P, P, i32, i32, u64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, sz, P])
+_sig("bgv_graph_csr_ws_size", sz, [i64, i32])
+_sig("bgv_graph_csr", C.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P])
+_sig("bgv_colour_groups_ws_size", sz, [i64])
+_sig("bgv_colour_groups", C.c_int, [i64, P, P, i32, P, P, P, sz, P])
 _sig("bgv_fa2_default_params", None, [C.POINTER(bgv_fa2_params)])
 _sig("bgv_fa2_init", C.c_int, [i64, C.POINTER(bgv_fa2_params), P, P, P, P])
 _sig("bgv_fa2_ws_size", sz, [i64, i64])
@@ -81,6 +85,7 @@ _sig("bgv_layout_host", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, 
 #: every symbol this binding resolves from the library
 EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees", "bgv_sketch_degrees_noalloc",
            "bgv_communities_ws_size", "bgv_communities", "bgv_supergraph_ws_size", "bgv_supergraph",
+           "bgv_graph_csr_ws_size", "bgv_graph_csr", "bgv_colour_groups_ws_size", "bgv_colour_groups",
            "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
            "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
            "bgv_layout_host_ws_size", "bgv_layout_host"]
@@ -183,6 +188,24 @@ def bgv_supergraph(edges, m, n, labels, deg_est, rows, width, seed, node_map, K_
                              _p(ssrc), _p(sdst), _p(sw), _p(Es_dev), _p(mass), _p(csr_off), _p(csr_adj), _p(csr_w),
                              _p(vol), _p(count), _p(comm_label), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
          "bgv_supergraph")
+
+
+def bgv_graph_csr_ws_size(m: int, n: int) -> int:
+    return _lib.bgv_graph_csr_ws_size(m, n)
+
+
+def bgv_graph_csr(edges, m, n, csr_off, csr_adj, csr_w, mass, nnz_dev, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_graph_csr(_p(edges), m, n, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), _p(nnz_dev), _p(ws),
+                            _nbytes(ws, ws_bytes), _s(stream)), "bgv_graph_csr")
+
+
+def bgv_colour_groups_ws_size(K: int) -> int:
+    return _lib.bgv_colour_groups_ws_size(K)
+
+
+def bgv_colour_groups(K, sizes, group, ws, n=0, node_map=None, node_colour=None, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_colour_groups(K, _p(sizes), _p(group), n, _p(node_map), _p(node_colour), _p(ws),
+                                _nbytes(ws, ws_bytes), _s(stream)), "bgv_colour_groups")
 
 
 def bgv_fa2_default_params() -> bgv_fa2_params:

@@ -162,6 +162,45 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
     return rc;
 }
 
+// Whole-graph CSR (ForceAtlas2 on the graph itself): the supergraph of the
+// identity labelling is the graph with duplicate edges merged.
+struct GraphCsrBuffers {
+    int32_t *labels, *node_map;
+    uint32_t *zero, *mass_tmp, *sw;
+    int64_t *K_dev, *Es_dev;
+    int32_t *ssrc, *sdst;
+    SuperScratch super;
+};
+
+void carve_graph_csr(Carver &c, int64_t m, int32_t n, GraphCsrBuffers &b) {
+    const size_t nn = size_t(n), mm = size_t(m > 0 ? m : 1);
+    b.labels = c.take<int32_t>(nn);
+    b.node_map = c.take<int32_t>(nn);
+    b.zero = c.take<uint32_t>(nn);
+    b.mass_tmp = c.take<uint32_t>(nn);
+    b.K_dev = c.take<int64_t>(1);
+    b.Es_dev = c.take<int64_t>(1);
+    b.ssrc = c.take<int32_t>(mm);
+    b.sdst = c.take<int32_t>(mm);
+    b.sw = c.take<uint32_t>(mm);
+    carve_super(c, m, n, 1, 1, b.super);
+}
+
+__global__ void k_identity_labels(int32_t n, int32_t *labels, uint32_t *zero) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        labels[v] = int32_t(v);
+        zero[v] = 0u;
+    }
+}
+
+// FA2 mass of a node of the whole graph: its degree (distinct neighbours)
+// plus one.  Thread 0 also publishes nnz = csr_off[n].
+__global__ void k_mass_from_degree(int32_t n, const int32_t *csr_off, uint32_t *mass, int64_t *nnz_dev) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        mass[v] = uint32_t(csr_off[v + 1] - csr_off[v]) + 1u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nnz_dev = csr_off[n];
+}
+
 __global__ void k_radius(const uint32_t *mass, const int64_t *K_dev, float *radius) {
     const int64_t K = *K_dev;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < K; k += int64_t(gridDim.x) * blockDim.x)
@@ -304,6 +343,31 @@ int bgv_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
     const HashFamily h = make_hash_family(seed, rows, uint32_t(width));
     return run_supergraph(edges, m, n, labels, deg_est, h, node_map, K_dev, ssrc, sdst, sw, Es_dev, mass, csr_off,
                           csr_adj, csr_w, vol, count, comm_label, s, status_ptr(ws), as_stream(stream));
+}
+
+size_t bgv_graph_csr_ws_size(int64_t m, int32_t n) {
+    Carver c(nullptr, kHeaderBytes);
+    GraphCsrBuffers b;
+    carve_graph_csr(c, m, n, b);
+    return c.used();
+}
+
+int bgv_graph_csr(const int32_t *edges, int64_t m, int32_t n, int32_t *csr_off, int32_t *csr_adj, uint32_t *csr_w,
+                  uint32_t *mass, int64_t *nnz_dev, void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    if (!csr_off || !csr_adj || !csr_w || !mass || !nnz_dev) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_graph_csr_ws_size(m, n)));
+    Carver c(ws, kHeaderBytes);
+    GraphCsrBuffers b;
+    carve_graph_csr(c, m, n, b);
+    cudaStream_t st = as_stream(stream);
+    note_launch(), k_identity_labels<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, b.labels, b.zero);
+    BGV_TRY(launch_status());
+    const HashFamily h = make_hash_family(1, 1, 1);
+    BGV_TRY(run_supergraph(edges, m, n, b.labels, b.zero, h, b.node_map, b.K_dev, b.ssrc, b.sdst, b.sw, b.Es_dev,
+                           b.mass_tmp, csr_off, csr_adj, csr_w, nullptr, nullptr, nullptr, b.super, status_ptr(ws), st));
+    note_launch(), k_mass_from_degree<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, csr_off, mass, nnz_dev);
+    return launch_status();
 }
 
 void bgv_fa2_default_params(bgv_fa2_params *p) {

@@ -162,8 +162,8 @@ struct SuperScratch {
     uint32_t *flags;        // [n] label present / CSR counts
     uint32_t *rank;         // [n+1]
     int32_t *label_of;      // [n]
-    uint32_t *incnt;        // [n]
-    uint32_t *first;        // [n]
+    uint32_t *src_first, *src_end;  // [n] runs of each supernode in (src, dst) order
+    uint32_t *dst_first, *dst_end;  // [n] runs in (dst, src) order
     int64_t *m_cut;         // device scalar
     unsigned long long *sketch;  // [rows * width]
     uint32_t *heads;        // [m]

@@ -35,7 +35,7 @@ namespace bgv {
 namespace {
 constexpr int kThreads = 256;
 constexpr int kFrameBlocks = 304;      // 2 x 152 SMs
-constexpr int kNodeBlocks = 152 * 4;
+constexpr int kNodeBlocks = 152 * 8;  // node-kernel grid (rows are grid-strided)
 constexpr int kStack = 96;             // >= 3 * (24 + 1) + 1
 constexpr int kNone = INT32_MIN;       // empty child slot
 
@@ -415,57 +415,90 @@ __device__ __forceinline__ void add_body(float xi, float yi, float kmi, float4 b
     }
 }
 
-// Barnes-Hut traversal without a stack.  A warp serves 32 Morton-consecutive
-// bodies; every lane holds the pre-order index where its own traversal
-// resumes.  Each step the warp takes the smallest resume index (one redux),
-// loads that element once for all lanes, and only the lanes waiting at it
-// act: a body is summed directly (not self) and passed; a cell holding the
-// lane's body is entered; any other cell is accepted (summed, resume after
-// its subtree) or entered, by the FP32 opening test of the definition.  Each
-// body therefore sees exactly its own interaction set, in depth-first order.
+// Barnes-Hut traversal without a stack.  A warp serves 32 * kBodiesPerLane
+// Morton-consecutive bodies; each body keeps the pre-order index where its
+// own traversal resumes.  Each step the warp takes the smallest resume index
+// (one redux), loads that element once for all lanes, and only the bodies
+// waiting at it act: a body is summed directly (not self) and passed; a cell
+// holding the body is entered; any other cell is accepted (summed, resume
+// after its subtree) or entered, by the FP32 opening test of the definition.
+// Each body therefore sees exactly its own interaction set, in depth-first
+// order.
+constexpr int kBodiesPerLane = 1;
+
+struct Walker {
+    float xi, yi, kmi;
+    uint32_t self, resume;
+    float fx, fy;
+    unsigned inter;
+};
+
+__device__ __forceinline__ void walker_step(Walker &b, uint32_t cur, float4 e, uint32_t sk, float theta2) {
+    if (b.resume != cur) return;
+    b.resume = cur + 1;
+    if (e.w < 0.0f) {  // a body
+        if (cur != b.self) {
+            add_body(b.xi, b.yi, b.kmi, e, b.fx, b.fy);
+            ++b.inter;
+        }
+    } else if (!(b.self > cur && b.self < sk)) {  // a cell not holding this body
+        const float dx = __fsub_rn(b.xi, e.x), dy = __fsub_rn(b.yi, e.y);
+        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        if (e.w < __fmul_rn(theta2, d2)) {
+            const float f = __fdividef(b.kmi * e.z, d2);
+            b.fx += f * dx;
+            b.fy += f * dy;
+            ++b.inter;
+            b.resume = sk;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
                                                       const uint32_t *__restrict__ T,
                                                       const float4 *__restrict__ body, int64_t K, float kr,
                                                       float theta2, float2 *__restrict__ Frep,
                                                       unsigned long long *inter_step,
                                                       unsigned long long *inter_total) {
+    constexpr int kWarpBodies = 32 * kBodiesPerLane;
     const int lane = threadIdx.x & 31;
-    const int64_t s0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31);
+    const int64_t s0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kWarpBodies;
     if (s0 >= K) return;  // whole warp leaves together
-    const int64_t s = s0 + lane;
-    const bool active = s < K;
-    const float4 bi = active ? body[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float xi = bi.x, yi = bi.y, kmi = kr * bi.z;
     const uint32_t total = uint32_t(K + T[K]);
-    const uint32_t self = active ? uint32_t(s + T[s + 1]) : 0xFFFFFFFFu;
-    uint32_t resume = active ? 0u : 0xFFFFFFFFu;
-    float fx = 0.0f, fy = 0.0f;
-    unsigned inter = 0;
+    Walker w[kBodiesPerLane];
+#pragma unroll
+    for (int q = 0; q < kBodiesPerLane; ++q) {
+        const int64_t s = s0 + q * 32 + lane;
+        const bool active = s < K;
+        const float4 bi = active ? body[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        w[q].xi = bi.x;
+        w[q].yi = bi.y;
+        w[q].kmi = kr * bi.z;
+        w[q].self = active ? uint32_t(s + T[s + 1]) : 0xFFFFFFFFu;
+        w[q].resume = active ? 0u : 0xFFFFFFFFu;
+        w[q].fx = 0.0f;
+        w[q].fy = 0.0f;
+        w[q].inter = 0;
+    }
     while (true) {
-        const uint32_t cur = __reduce_min_sync(0xFFFFFFFFu, resume);
+        uint32_t mine = w[0].resume;
+#pragma unroll
+        for (int q = 1; q < kBodiesPerLane; ++q) mine = min(mine, w[q].resume);
+        const uint32_t cur = __reduce_min_sync(0xFFFFFFFFu, mine);
         if (cur >= total) break;
+        if (mine != cur) continue;
         const float4 e = geo[cur];
         const uint32_t sk = uint32_t(skip[cur]);
-        if (resume != cur) continue;
-        resume = cur + 1;
-        if (e.w < 0.0f) {  // a body
-            if (cur != self) {
-                add_body(xi, yi, kmi, e, fx, fy);
-                ++inter;
-            }
-        } else if (!(self > cur && self < sk)) {  // a cell not holding this body
-            const float dx = __fsub_rn(xi, e.x), dy = __fsub_rn(yi, e.y);
-            const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            if (e.w < __fmul_rn(theta2, d2)) {
-                const float f = __fdividef(kmi * e.z, d2);
-                fx += f * dx;
-                fy += f * dy;
-                ++inter;
-                resume = sk;
-            }
-        }
+#pragma unroll
+        for (int q = 0; q < kBodiesPerLane; ++q) walker_step(w[q], cur, e, sk, theta2);
     }
-    if (active) Frep[__float_as_int(bi.w)] = make_float2(fx, fy);
+    unsigned inter = 0;
+#pragma unroll
+    for (int q = 0; q < kBodiesPerLane; ++q) {
+        const int64_t s = s0 + q * 32 + lane;
+        if (s < K) Frep[__float_as_int(body[s].w)] = make_float2(w[q].fx, w[q].fy);
+        inter += w[q].inter;
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) inter += __shfl_xor_sync(0xFFFFFFFFu, inter, d);
     if (lane == 0 && inter) {
@@ -523,13 +556,43 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
                                                       float2 *__restrict__ tail) {
     const int64_t chunks = (nnz + kChunk - 1) / kChunk;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(adj) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
         const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
+        const int n = int(e1 - e0);
+        // All loads of the chunk first: 8 neighbour ids and weights (two
+        // 16-byte loads each when aligned), then the 8 position gathers, so
+        // they are in flight together.
+        int32_t jj[kChunk];
+        uint32_t ww[kChunk];
+        if (vec && n == kChunk) {
+            const int4 a0 = __ldcs(reinterpret_cast<const int4 *>(adj + e0));
+            const int4 a1 = __ldcs(reinterpret_cast<const int4 *>(adj + e0) + 1);
+            const uint4 w0 = __ldcs(reinterpret_cast<const uint4 *>(w + e0));
+            const uint4 w1 = __ldcs(reinterpret_cast<const uint4 *>(w + e0) + 1);
+            jj[0] = a0.x; jj[1] = a0.y; jj[2] = a0.z; jj[3] = a0.w;
+            jj[4] = a1.x; jj[5] = a1.y; jj[6] = a1.z; jj[7] = a1.w;
+            ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
+            ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                jj[k] = k < n ? adj[e0 + k] : -1;
+                ww[k] = k < n ? w[e0 + k] : 0u;
+            }
+        }
+        float2 pj[kChunk];
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k)
+            pj[k] = static_cast<uint64_t>(jj[k]) < static_cast<uint64_t>(K) ? pos[jj[k]] : make_float2(0.f, 0.f);
         int64_t r = chunk_row[g];
         int64_t rs = off[r], re = off[r + 1];
         float2 pi = pos[r];
         float ax = 0.0f, ay = 0.0f;
-        for (int64_t e = e0; e < e1; ++e) {
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+            if (k >= n) break;
+            const int64_t e = e0 + k;
             while (e >= re && r + 1 < K) {  // row r ends before e: hand it over
                 if (rs >= e0) full[r] = make_float2(ax, ay);  // started here: complete
                 else head[g] = make_float2(ax, ay);
@@ -540,12 +603,10 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
                 ax = 0.0f;
                 ay = 0.0f;
             }
-            const int32_t j = adj[e];
-            if (static_cast<uint64_t>(j) >= static_cast<uint64_t>(K)) continue;  // invalid CSR entry
-            const float2 pj = pos[j];
-            const float wt = __uint2float_rn(w[e]);
-            ax += wt * (pj.x - pi.x);
-            ay += wt * (pj.y - pi.y);
+            if (static_cast<uint64_t>(jj[k]) >= static_cast<uint64_t>(K)) continue;  // invalid CSR entry
+            const float wt = __uint2float_rn(ww[k]);
+            ax += wt * (pj[k].x - pi.x);
+            ay += wt * (pj[k].y - pi.y);
         }
         if (rs >= e0 && re <= e1) full[r] = make_float2(ax, ay);
         else if (rs < e0) head[g] = make_float2(ax, ay);
@@ -598,6 +659,30 @@ __device__ __forceinline__ void block_merge(Comp &S, Comp &T) {
     __syncthreads();
 }
 
+// Block sum of one (S, T) pair per thread in plain FP64 (fixed tree);
+// thread 0 receives it.  Compensation is applied where the block sums meet.
+__device__ __forceinline__ void block_sum_plain(double &S, double &T) {
+    __shared__ double sS[kThreads / 32], sT[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        S += __shfl_down_sync(0xFFFFFFFFu, S, d);
+        T += __shfl_down_sync(0xFFFFFFFFu, T, d);
+    }
+    if (lane == 0) {
+        sS[warp] = S;
+        sT[warp] = T;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kThreads / 32; ++k) {
+            S += sS[k];
+            T += sT[k];
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const int32_t *__restrict__ off,
                                                    const float2 *__restrict__ full, const float2 *__restrict__ head,
                                                    const float2 *__restrict__ tail,
@@ -615,8 +700,15 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
         const bool valid = i < K;
         int64_t g1 = 0, g2 = -1;
         float ax = 0.0f, ay = 0.0f;
+        // independent per-node loads first, so they overlap the piece sums
+        float2 pi = make_float2(0.f, 0.f), fr = pi, fp = pi;
+        uint32_t mi = 0;
         if (valid) {
             const int64_t b = off[i], e = off[i + 1];
+            pi = pos[i];
+            mi = mass[i];
+            fr = Frep[i];
+            if (mode != 0) fp = Fprev[i];
             if (e > b) {
                 g1 = b / kChunk;
                 g2 = (e - 1) / kChunk;
@@ -664,8 +756,7 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
             }
         }
         if (!valid) continue;
-        const float2 pi = pos[i];
-        const float m = __uint2float_rn(mass[i]);
+        const float m = __uint2float_rn(mi);
         float gx, gy;
         if (strong) {
             gx = -kg * m * pi.x;
@@ -675,7 +766,6 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
             gx = rr > 0.0f ? -kg * m * pi.x / rr : 0.0f;
             gy = rr > 0.0f ? -kg * m * pi.y / rr : 0.0f;
         }
-        const float2 fr = Frep[i];
         if (mode == 0) {
             if (Fr_out) Fr_out[i] = fr;
             if (Fa_out) Fa_out[i] = make_float2(ax, ay);
@@ -683,19 +773,18 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
         } else {
             const float fx = fr.x + ax + gx, fy = fr.y + ay + gy;
             F[i] = make_float2(fx, fy);
-            const float2 fp = Fprev[i];
             const float sx = fx - fp.x, sy = fy - fp.y, tx = fx + fp.x, ty = fy + fp.y;
-            const double md = double(mass[i]);
-            S = comp_add(S, md * double(sqrtf(sx * sx + sy * sy)));
-            T = comp_add(T, md * 0.5 * double(sqrtf(tx * tx + ty * ty)));
+            // per-node products in FP32; the sums over nodes are FP64
+            S.s += double(m * sqrtf(sx * sx + sy * sy));
+            T.s += double(0.5f * m * sqrtf(tx * tx + ty * ty));
         }
     }
     if (mode == 0) return;
     __shared__ bool last;
-    block_merge(S, T);
+    block_sum_plain(S.s, T.s);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = make_double2(S.s, S.c);
-        part[2 * blockIdx.x + 1] = make_double2(T.s, T.c);
+        part[2 * blockIdx.x] = make_double2(S.s, 0.0);
+        part[2 * blockIdx.x + 1] = make_double2(T.s, 0.0);
         __threadfence();
         last = atomicAdd(&hdr->node_ticket, 1u) == gridDim.x - 1;
     }
@@ -920,7 +1009,9 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         BGV_TRY(launch_status());
         BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;
-        note_launch(), k_repulse<<<gt, kThreads, 0, st>>>(s.geo, s.skip, s.T, s.body, K, p.kr, theta2, s.Frep,
+        const int64_t rwarps = (K + 32 * kBodiesPerLane - 1) / (32 * kBodiesPerLane);
+        const unsigned gr = unsigned((rwarps * 32 + kThreads - 1) / kThreads);
+        note_launch(), k_repulse<<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, s.body, K, p.kr, theta2, s.Frep,
                                                           &hdr->interactions, &hdr->interactions_total);
         BGV_TRY(launch_status());
     } else {
@@ -935,11 +1026,12 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
                                                                                              s.chunk_row);
             BGV_TRY(launch_status());
         }
-        note_launch(), k_attract<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0, st>>>(
+        const int64_t nchunks = (nnz + kChunk - 1) / kChunk;
+        note_launch(), k_attract<<<grid_for(nchunks, kThreads, (nchunks + kThreads - 1) / kThreads), kThreads, 0, st>>>(
             K, nnz, csr_off, s.chunk_row, csr_adj, csr_w, pos, s.full, s.head, s.tail);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_node<<<kNodeBlocks, kThreads, 0, st>>>(mode, K, csr_off, s.full, s.head, s.tail, mass, pos,
+    note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(mode, K, csr_off, s.full, s.head, s.tail, mass, pos,
                                                             s.Frep, p.kg, p.strong_gravity, F, Fprev,
                                                             reinterpret_cast<float2 *>(Fr),
                                                             reinterpret_cast<float2 *>(Fa),

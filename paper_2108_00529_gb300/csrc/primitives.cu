@@ -182,8 +182,13 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
 namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+// Keys per thread: 16 for big inputs; 8 below kSmallSort keys, so that a
+// million keys still make ~500 tiles (enough blocks for 152 SMs).
+constexpr int kSortItemsBig = 16, kSortItemsSmall = 8;
+constexpr int64_t kSmallSort = int64_t(1) << 22;
+constexpr int kSortItems = 16;  // the counting kernel's items per thread
+constexpr int kSortTile = kSortThreads * kSortItems;
+inline int sort_items(int64_t cap) { return cap <= kSmallSort ? kSortItemsSmall : kSortItemsBig; }
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
 constexpr uint32_t kInvalidDigit = 0xFFFFu;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_offsets(uint32_t *counts,
     }
 }
 
-template <bool kVals>
+template <bool kVals, int kItems>
 __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned long long *__restrict__ kin,
                                                                 unsigned long long *__restrict__ kout,
                                                                 const uint32_t *__restrict__ vin,
@@ -239,25 +244,23 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
     __syncthreads();
     const int64_t tile = tile_sh;
     const int64_t n = load_count(d_count, cap);
-    if (tile * kSortTile >= n) return;
+    if (tile * (kSortThreads * kItems) >= n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const int64_t base = tile * kSortTile + int64_t(warp) * (32 * kSortItems);
-    unsigned long long key[kSortItems];
-    uint32_t val[kSortItems];
-    uint32_t digit[kSortItems];
-    uint32_t rank[kSortItems];
+    const int64_t base = tile * (kSortThreads * kItems) + int64_t(warp) * (32 * kItems);
+    // Registers hold the keys and ranks only; digits are recomputed from the
+    // keys and the values are loaded just before the scatter.
+    unsigned long long key[kItems];
+    uint32_t rank[kItems];
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < kItems; ++k) {
         const int64_t i = base + int64_t(k) * 32 + lane;
-        const bool ok = i < n;
-        key[k] = ok ? kin[i] : 0ull;
-        if (kVals) val[k] = ok ? vin[i] : 0u;
-        digit[k] = ok ? (static_cast<uint32_t>(key[k] >> shift) & 0xFFu) : kInvalidDigit;
+        key[k] = i < n ? kin[i] : 0ull;
     }
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const uint32_t d = digit[k];
+    for (int k = 0; k < kItems; ++k) {
+        const int64_t i = base + int64_t(k) * 32 + lane;
+        const uint32_t d = i < n ? (static_cast<uint32_t>(key[k] >> shift) & 0xFFu) : kInvalidDigit;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         uint32_t before = 0;
         if (d != kInvalidDigit) before = cnt[warp][d];
@@ -306,18 +309,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-        const uint32_t d = digit[k];
-        if (d == kInvalidDigit) continue;
+    for (int k = 0; k < kItems; ++k) {
+        const int64_t i = base + int64_t(k) * 32 + lane;
+        if (i >= n) continue;
+        const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
         const uint32_t pos = tile_base[d] + cnt[warp][d] + rank[k];
         kout[pos] = key[k];
-        if (kVals) vout[pos] = val[k];
+        if (kVals) vout[pos] = vin[i];
     }
 }
 }  // namespace
 
 int64_t sort_tiles(int64_t cap) {
-    int64_t t = (cap + kSortTile - 1) / kSortTile;
+    const int64_t tile = int64_t(kSortThreads) * sort_items(cap);
+    int64_t t = (cap + tile - 1) / tile;
     return t < 1 ? 1 : t;
 }
 
@@ -333,26 +338,34 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out) {
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
                int *result_buffer, uint32_t *dev_status) {
     const int64_t tiles = sort_tiles(cap);
+    const int items = sort_items(cap);
     const int passes = (end_bit + 7) / 8;
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
-    note_launch(), k_sort_count<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(b.keys[0], cap, d_count,
-                                                                                    passes, b.counts);
+    const int64_t count_blocks = (cap + kSortTile - 1) / kSortTile;
+    note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
+        b.keys[0], cap, d_count, passes, b.counts);
     note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
     BGV_TRY(launch_status());
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
-        if (b.vals[0]) {
-            note_launch(), k_sort_onesweep<true><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-                b.keys[cur], b.keys[cur ^ 1], b.vals[cur], b.vals[cur ^ 1], cap, d_count, 8 * p, b.counts + p * kBins,
-                tile_counters + p, b.status, dev_status);
-        } else {
-            note_launch(), k_sort_onesweep<false><<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-                b.keys[cur], b.keys[cur ^ 1], nullptr, nullptr, cap, d_count, 8 * p, b.counts + p * kBins,
-                tile_counters + p, b.status, dev_status);
-        }
+        const unsigned g = static_cast<unsigned>(tiles);
+        unsigned long long *ki = b.keys[cur], *ko = b.keys[cur ^ 1];
+        uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1], *base = b.counts + p * kBins;
+        if (b.vals[0] && items == kSortItemsSmall)
+            note_launch(), k_sort_onesweep<true, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
+                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+        else if (b.vals[0])
+            note_launch(), k_sort_onesweep<true, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
+                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+        else if (items == kSortItemsSmall)
+            note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
+                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+        else
+            note_launch(), k_sort_onesweep<false, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
+                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
         BGV_TRY(launch_status());
         cur ^= 1;
     }

@@ -10,9 +10,10 @@
 // 4. Reduce by key: run heads -> scan -> superedge endpoints and run lengths.
 // 5. Community-size sketch: every node adds its sketched degree at the
 //    hash of its label (u64 counters); mass = 1 + the row minimum.
-// 6. Symmetric CSR with ascending neighbours: the source side of superedge
-//    (a, b) lands after a's in-neighbours; the destination side comes from a
-//    stable sort of the superedges by b, which orders them by (b, a).
+// 6. Symmetric CSR with ascending neighbours: a stable sort of the
+//    superedges by b orders them by (b, a); run boundaries in the two
+//    orders give each row's in- and out-degree (no atomics), and every
+//    entry's slot follows from its rank inside its run.
 #include "bgv_internal.cuh"
 
 namespace bgv {
@@ -56,15 +57,15 @@ __device__ __forceinline__ void emit_cut(bool valid, unsigned long long key, uns
     if (valid) keys[base + __popc(mask & ((1u << lane) - 1u))] = key;
 }
 
-__device__ __forceinline__ bool cut_key(int32_t u, int32_t v, int32_t n, const int32_t *labels,
-                                        const int32_t *node_map, int shift, unsigned long long *key,
-                                        uint32_t *status) {
+__device__ __forceinline__ bool cut_key(int32_t u, int32_t v, int32_t n, const int32_t *node_map, int shift,
+                                        unsigned long long *key, uint32_t *status) {
     if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(n) || static_cast<uint32_t>(v) >= static_cast<uint32_t>(n)) {
         raise_status(status, BGV_DEV_BADEDGE);
         return false;
     }
-    if (labels[u] == labels[v]) return false;
+    // node_map is one-to-one on labels, so equal supernodes = equal labels
     const uint32_t a = uint32_t(node_map[u]), b = uint32_t(node_map[v]);
+    if (a == b) return false;
     const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
     *key = (static_cast<unsigned long long>(lo) << shift) | hi;
     return true;
@@ -74,7 +75,6 @@ __device__ __forceinline__ bool cut_key(int32_t u, int32_t v, int32_t n, const i
 // test uses the warp's first index) so the ballot in emit_cut always sees all
 // 32 lanes.
 __global__ void __launch_bounds__(kThreads) k_cut_keys(const int32_t *__restrict__ edges, int64_t m, int32_t n,
-                                                       const int32_t *__restrict__ labels,
                                                        const int32_t *__restrict__ node_map, int shift,
                                                        unsigned long long *__restrict__ keys, int64_t *m_cut,
                                                        uint32_t *status) {
@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(kThreads) k_cut_keys(const int32_t *__restrict
         bool v0 = false, v1 = false;
         if (p < full) {
             const int4 e = __ldcs(e2 + p);
-            v0 = cut_key(e.x, e.y, n, labels, node_map, shift, &k0, status);
-            v1 = cut_key(e.z, e.w, n, labels, node_map, shift, &k1, status);
+            v0 = cut_key(e.x, e.y, n, node_map, shift, &k0, status);
+            v1 = cut_key(e.z, e.w, n, node_map, shift, &k1, status);
         } else if (p < pairs) {  // odd tail edge
-            v0 = cut_key(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], n, labels, node_map, shift, &k0, status);
+            v0 = cut_key(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], n, node_map, shift, &k0, status);
         }
         emit_cut(v0, k0, keys, m_cut);
         emit_cut(v1, k1, keys, m_cut);
@@ -176,39 +176,70 @@ __global__ void __launch_bounds__(kThreads) k_mass(const int32_t *__restrict__ l
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_csr_count(const int32_t *__restrict__ ssrc,
-                                                        const int32_t *__restrict__ sdst, const int64_t *Es_dev,
-                                                        uint32_t *__restrict__ cnt, uint32_t *__restrict__ incnt,
-                                                        uint32_t *__restrict__ first_src) {
+// Run boundaries of a sorted id sequence: first[id] and end[id] (both left
+// at 0 for ids that do not occur), so the run length is end - first.
+__global__ void __launch_bounds__(kThreads) k_runs_i32(const int32_t *__restrict__ ids, const int64_t *Es_dev,
+                                                       uint32_t *__restrict__ first, uint32_t *__restrict__ end) {
     const int64_t Es = *Es_dev;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < Es; s += stride) {
-        const int32_t a = ssrc[s], b = sdst[s];
-        atomicAdd(&cnt[a], 1u);
-        atomicAdd(&cnt[b], 1u);
-        atomicAdd(&incnt[b], 1u);
-        if (s == 0 || ssrc[s - 1] != a) first_src[a] = uint32_t(s);
+        const int32_t a = ids[s];
+        if (s == 0 || ids[s - 1] != a) first[a] = uint32_t(s);
+        if (s == Es - 1 || ids[s + 1] != a) end[a] = uint32_t(s + 1);
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_runs_u64(const unsigned long long *__restrict__ ids,
+                                                       const int64_t *Es_dev, uint32_t *__restrict__ first,
+                                                       uint32_t *__restrict__ end) {
+    const int64_t Es = *Es_dev;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < Es; s += stride) {
+        const uint32_t a = uint32_t(ids[s]);
+        if (s == 0 || uint32_t(ids[s - 1]) != a) first[a] = uint32_t(s);
+        if (s == Es - 1 || uint32_t(ids[s + 1]) != a) end[a] = uint32_t(s + 1);
+    }
+}
+
+// CSR row length = out-degree (run in the (src, dst) order) + in-degree (run
+// in the (dst, src) order).
+__global__ void __launch_bounds__(kThreads) k_row_lengths(int32_t n, const uint32_t *__restrict__ sf,
+                                                          const uint32_t *__restrict__ se,
+                                                          const uint32_t *__restrict__ df,
+                                                          const uint32_t *__restrict__ de, uint32_t *__restrict__ cnt) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride)
+        cnt[k] = (se[k] - sf[k]) + (de[k] - df[k]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_dst_keys(const int32_t *__restrict__ sdst, const int64_t *Es_dev,
+                                                       unsigned long long *__restrict__ keys,
+                                                       uint32_t *__restrict__ vals) {
+    const int64_t Es = *Es_dev;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < Es; s += stride) {
+        keys[s] = static_cast<unsigned long long>(uint32_t(sdst[s]));
+        vals[s] = uint32_t(s);
+    }
+}
+
+// Row a lists its in-neighbours (smaller ids, from the (dst, src) order)
+// first, then its out-neighbours (larger ids, from the (src, dst) order).
 __global__ void __launch_bounds__(kThreads) k_csr_fill_src(const int32_t *__restrict__ ssrc,
                                                            const int32_t *__restrict__ sdst,
                                                            const uint32_t *__restrict__ sw, const int64_t *Es_dev,
                                                            const int32_t *__restrict__ csr_off,
-                                                           const uint32_t *__restrict__ incnt,
-                                                           const uint32_t *__restrict__ first_src,
-                                                           int32_t *__restrict__ csr_adj, uint32_t *__restrict__ csr_w,
-                                                           unsigned long long *__restrict__ dst_keys,
-                                                           uint32_t *__restrict__ dst_vals) {
+                                                           const uint32_t *__restrict__ sf,
+                                                           const uint32_t *__restrict__ df,
+                                                           const uint32_t *__restrict__ de,
+                                                           int32_t *__restrict__ csr_adj, uint32_t *__restrict__ csr_w) {
     const int64_t Es = *Es_dev;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < Es; s += stride) {
         const int32_t a = ssrc[s];
-        const int64_t pos = int64_t(csr_off[a]) + incnt[a] + (s - int64_t(first_src[a]));
+        const int64_t pos = int64_t(csr_off[a]) + (de[a] - df[a]) + (s - int64_t(sf[a]));
         csr_adj[pos] = sdst[s];
         csr_w[pos] = sw[s];
-        dst_keys[s] = static_cast<unsigned long long>(uint32_t(sdst[s]));
-        dst_vals[s] = uint32_t(s);
     }
 }
 
@@ -217,19 +248,14 @@ __global__ void __launch_bounds__(kThreads) k_csr_fill_dst(const unsigned long l
                                                            const int32_t *__restrict__ ssrc,
                                                            const uint32_t *__restrict__ sw,
                                                            const int32_t *__restrict__ csr_off,
+                                                           const uint32_t *__restrict__ df,
                                                            int32_t *__restrict__ csr_adj, uint32_t *__restrict__ csr_w) {
     const int64_t Es = *Es_dev;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < Es; t += stride) {
         const uint32_t b = uint32_t(bkeys[t]);
-        // first position of b in the (b, a) order: binary search on the keys
-        int64_t lo = 0, hi = t;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (uint32_t(bkeys[mid]) < b) lo = mid + 1; else hi = mid;
-        }
         const uint32_t s = bvals[t];
-        const int64_t pos = int64_t(csr_off[b]) + (t - lo);
+        const int64_t pos = int64_t(csr_off[b]) + (t - int64_t(df[b]));
         csr_adj[pos] = ssrc[s];
         csr_w[pos] = sw[s];
     }
@@ -240,8 +266,10 @@ void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, S
     s.flags = c.take<uint32_t>(size_t(n) + 1);
     s.rank = c.take<uint32_t>(size_t(n) + 1);
     s.label_of = c.take<int32_t>(size_t(n));
-    s.incnt = c.take<uint32_t>(size_t(n));
-    s.first = c.take<uint32_t>(size_t(n));
+    s.src_first = c.take<uint32_t>(size_t(n));
+    s.src_end = c.take<uint32_t>(size_t(n));
+    s.dst_first = c.take<uint32_t>(size_t(n));
+    s.dst_end = c.take<uint32_t>(size_t(n));
     s.m_cut = c.take<int64_t>(1);
     s.sketch = c.take<unsigned long long>(size_t(rows) * size_t(width));
     s.heads = c.take<uint32_t>(size_t(m));
@@ -275,7 +303,7 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
     BGV_CUDA(cudaMemsetAsync(s.m_cut, 0, sizeof(int64_t), st));
     SortBuffers cut = s.sort_cut;
     if (m > 0) {
-        note_launch(), k_cut_keys<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, labels, node_map,
+        note_launch(), k_cut_keys<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, node_map,
                                                                                  shift, cut.keys[0], s.m_cut, status);
         BGV_TRY(launch_status());
     }
@@ -302,21 +330,28 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
     note_launch(), k_mass<<<gn, kThreads, 0, st>>>(s.label_of, K_dev, h, s.sketch, mass, comm_label);
     BGV_TRY(launch_status());
 
-    // 6. symmetric CSR
-    BGV_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(uint32_t) * (size_t(n) + 1), st));
-    BGV_CUDA(cudaMemsetAsync(s.incnt, 0, sizeof(uint32_t) * size_t(n), st));
-    note_launch(), k_csr_count<<<gm, kThreads, 0, st>>>(ssrc, sdst, Es_dev, s.flags, s.incnt, s.first);
-    BGV_TRY(launch_status());
-    BGV_TRY(scan_exclusive(s.flags, reinterpret_cast<uint32_t *>(csr_off), n, nullptr, nullptr, true, s.scan_tmp,
-                           st));
+    // 6. symmetric CSR: the superedges in (src, dst) order and, from a stable
+    //    sort by dst, in (dst, src) order; run boundaries give the degrees.
     SortBuffers dsort = s.sort_dst;
-    note_launch(), k_csr_fill_src<<<gm, kThreads, 0, st>>>(ssrc, sdst, sw, Es_dev, csr_off, s.incnt, s.first, csr_adj, csr_w,
-                                            dsort.keys[0], dsort.vals[0]);
+    note_launch(), k_dst_keys<<<gm, kThreads, 0, st>>>(sdst, Es_dev, dsort.keys[0], dsort.vals[0]);
     BGV_TRY(launch_status());
     int dres = 0;
     BGV_TRY(radix_sort(dsort, m > 0 ? m : 1, Es_dev, shift, st, &dres, status));
-    note_launch(), k_csr_fill_dst<<<gm, kThreads, 0, st>>>(dsort.keys[dres], dsort.vals[dres], Es_dev, ssrc, sw, csr_off, csr_adj,
-                                            csr_w);
+    BGV_CUDA(cudaMemsetAsync(s.src_first, 0, sizeof(uint32_t) * size_t(n), st));
+    BGV_CUDA(cudaMemsetAsync(s.src_end, 0, sizeof(uint32_t) * size_t(n), st));
+    BGV_CUDA(cudaMemsetAsync(s.dst_first, 0, sizeof(uint32_t) * size_t(n), st));
+    BGV_CUDA(cudaMemsetAsync(s.dst_end, 0, sizeof(uint32_t) * size_t(n), st));
+    note_launch(), k_runs_i32<<<gm, kThreads, 0, st>>>(ssrc, Es_dev, s.src_first, s.src_end);
+    note_launch(), k_runs_u64<<<gm, kThreads, 0, st>>>(dsort.keys[dres], Es_dev, s.dst_first, s.dst_end);
+    note_launch(), k_row_lengths<<<gn, kThreads, 0, st>>>(n, s.src_first, s.src_end, s.dst_first, s.dst_end,
+                                                          s.flags);
+    BGV_TRY(launch_status());
+    BGV_TRY(scan_exclusive(s.flags, reinterpret_cast<uint32_t *>(csr_off), n, nullptr, nullptr, true, s.scan_tmp,
+                           st));
+    note_launch(), k_csr_fill_src<<<gm, kThreads, 0, st>>>(ssrc, sdst, sw, Es_dev, csr_off, s.src_first,
+                                                           s.dst_first, s.dst_end, csr_adj, csr_w);
+    note_launch(), k_csr_fill_dst<<<gm, kThreads, 0, st>>>(dsort.keys[dres], dsort.vals[dres], Es_dev, ssrc, sw,
+                                                           csr_off, s.dst_first, csr_adj, csr_w);
     return launch_status();
 }
 

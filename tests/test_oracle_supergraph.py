@@ -122,3 +122,30 @@ def test_modularity_matches_double_sum():
     same = lab[:, None] == lab[None, :]
     q = ((A - np.outer(k, k) / m2) * same).sum() / m2
     assert oracle.modularity(e, 25, lab) == pytest.approx(q, abs=1e-12)
+
+
+def test_colour_groups_small_example():
+    # Section 4.3 by hand: sizes 1,1,2,3,5,8,13 (alpha = 33, half 16.5).
+    # Ascending prefix sums 1,2,4,7,12,20 -> the first five (sum 12 <= 16.5)
+    # are brown; the rest (8, 13) are split into ten groups: ranks 0 and 1 of
+    # R = 2 -> groups 1 + 0 and 1 + 5.
+    sizes = np.array([13, 1, 8, 2, 1, 5, 3], np.uint32)
+    g = oracle.colour_groups(sizes)
+    assert g.tolist() == [6, 0, 1, 0, 0, 0, 0]
+
+
+def test_colour_groups_properties():
+    rng = np.random.default_rng(3)
+    sizes = rng.lognormal(3, 1.5, 5000).astype(np.uint32) + 1
+    g = oracle.colour_groups(sizes)
+    total = int(sizes.astype(np.int64).sum())
+    brown = int(sizes[g == 0].astype(np.int64).sum())
+    assert 2 * brown <= total
+    # adding the smallest non-brown community would pass half of alpha
+    assert 2 * (brown + int(sizes[g > 0].min())) > total
+    # groups are monotone in size and the ten upper groups have near-equal counts
+    for a in range(0, 10):
+        if np.any(g == a) and np.any(g == a + 1):
+            assert sizes[g == a].max() <= sizes[g == a + 1].min()
+    counts = np.bincount(g, minlength=11)[1:]
+    assert counts.max() - counts.min() <= 1
