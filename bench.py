@@ -56,6 +56,10 @@ WORKLOADS = {
                         "partition (256 communities of lognormal(8, 1) size), nodes coloured by their streamed "
                         "community", rows=4, width=65536, passes=3, threshold=0, growth=2, iterations=500,
                    whole=True),
+    "batch512": dict(desc="batching form: 512 independent planted-partition graphs, node counts log-uniform in "
+                          "[1,000, 200,000], 4 to 64 communities of lognormal(0, 0.5) size, average degree 10, "
+                          "80% of edges inside communities", rows=4, width=4096, passes=3, threshold=0, growth=2,
+                     iterations=300, batched=True),
 }
 
 
@@ -533,10 +537,158 @@ def gpu_arm_whole(args, dist: Dist):
     return out
 
 
+def gpu_arm_batched(args, dist: Dist):
+    """Batching form: all 512 graphs through one bgv_layout_batched call per
+    step (sketch, rounds, supergraph, 300 FA2 iterations for every graph),
+    compared with the same graphs laid out one bgv_layout call at a time."""
+    import torch
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        from paper_2108_00529_gb300 import build
+        build.build()
+        graphgen.load_batch(args.workload)
+    dist.barrier()
+    from paper_2108_00529_gb300 import load
+    B = load()
+    cfg = WORKLOADS[args.workload]
+    edges_np, eo, no = graphgen.load_batch(args.workload)
+    Gn, m, N = eo.shape[0] - 1, int(eo[-1]), int(no[-1])
+    iters = args.fa2_iterations or cfg["iterations"]
+    p = B.bgv_layout_default_params()
+    p.rows, p.width, p.passes, p.threshold, p.growth = cfg["rows"], cfg["width"], cfg["passes"], 0, cfg["growth"]
+    p.iterations, p.use_graph = iters, 1
+    s = torch.cuda.Stream(device=dev)
+    E = torch.from_numpy(edges_np).to(dev)
+    node_map = torch.zeros(N, dtype=torch.int32, device=dev)
+    xy = torch.zeros((N, 2), dtype=torch.float32, device=dev)
+    rad = torch.zeros(N, dtype=torch.float32, device=dev)
+    ws = B.alloc_ws(B.bgv_layout_batched_ws_size(Gn, eo, no, p), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def batched_step():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            K_off, Es_off = B.bgv_layout_batched(E, Gn, eo, no, p, node_map, xy, rad, ws, stream=s)
+            e1.record(s)
+        s.synchronize()
+        return e0.elapsed_time(e1), K_off, Es_off
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        batched_step()
+    st0 = B.bgv_fa2_read_stats(ws, s)
+    launches0 = B.bgv_launch_count()
+    clocks = ClockSampler([dist.local] if dist.world == 1 else None)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        t, K_off, Es_off = batched_step()
+        times.append(t)
+        torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = B.bgv_launch_count() - launches0
+    st1 = B.bgv_fa2_read_stats(ws, s)
+    ms = dist.max(float(np.mean(times)))
+
+    # the same graphs, one bgv_layout call each (own copy of its edges, so
+    # every list starts 16-byte aligned); one warm-up pass, one timed pass
+    per_graph = None
+    if not args.no_per_graph:
+        Eg = [torch.from_numpy(np.ascontiguousarray(edges_np[eo[g]:eo[g + 1]])).to(dev) for g in range(Gn)]
+        nmax, mmax = int(np.max(np.diff(no))), int(np.max(np.diff(eo)))
+        ws1 = B.alloc_ws(max(B.bgv_layout_ws_size(int(eo[g + 1] - eo[g]), int(no[g + 1] - no[g]), p)
+                             for g in range(Gn)), dev)
+        nm1 = torch.zeros(nmax, dtype=torch.int32, device=dev)
+        xy1 = torch.zeros((nmax, 2), dtype=torch.float32, device=dev)
+        r1 = torch.zeros(nmax, dtype=torch.float32, device=dev)
+        same = True
+        pg_ms = 0.0
+        for rep in range(2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s):
+                e0.record(s)
+                for g in range(Gn):
+                    K, Es = B.bgv_layout(Eg[g], int(eo[g + 1] - eo[g]), int(no[g + 1] - no[g]), p, nm1, xy1, r1,
+                                         ws1, stream=s)
+                    if rep == 1:
+                        same &= (K, Es) == (int(K_off[g + 1] - K_off[g]), int(Es_off[g + 1] - Es_off[g]))
+                e1.record(s)
+            s.synchronize()
+            pg_ms = e0.elapsed_time(e1)
+        per_graph = {"graphs_per_s": round(Gn / (pg_ms * 1e-3), 2), "ms": round(pg_ms, 1),
+                     "entry": "bgv_layout, one call per graph", "counts_equal_batched": bool(same)}
+    inter = (st1.interactions_total - st0.interactions_total) / max(st1.steps_total - st0.steps_total, 1)
+    return {
+        "metric": "graphs/s laid out (sketch, communities, supergraph, FA2)", "value": round(Gn * dist.world /
+                                                                                              (ms * 1e-3), 3),
+        "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32+f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {cfg['desc']}", "graphs": Gn, "n": N, "m": m,
+                   "sketch": f"{cfg['rows']}x{cfg['width']} per graph", "passes": cfg["passes"],
+                   "fa2_iterations": iters, "K": int(K_off[-1]), "Es": int(Es_off[-1]),
+                   "l2": "flushed before every timed step (256 MiB write)", "parallelism": "single GPU"},
+        "edges_per_s": round(m * dist.world / (ms * 1e-3), 1),
+        "interactions_per_iteration": int(inter),
+        "per_graph_launches": per_graph,
+        "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // max(args.steps, 1)), "clocks": clk,
+    }
+
+
+def reference_arm_batched(args, dist: Dist):
+    """The oracle on the batching workload: graphs taken in a fixed strided
+    order (every 32nd, so small and large ones alike) until about 10 s of
+    oracle time; each graph's step time is its edge stages plus the
+    workload's iterations x one timed FA2 iteration."""
+    cfg = WORKLOADS[args.workload]
+    edges_np, eo, no = graphgen.load_batch(args.workload)
+    Gn = eo.shape[0] - 1
+    order = [g for r in range(32) for g in range(r, Gn, 32)]
+    steps = []
+    for i in range(args.warmup + args.steps):
+        spent, total, used = 0.0, 0.0, 0
+        for g in order:
+            if spent > 10.0:
+                break
+            e = edges_np[eo[g]:eo[g + 1]]
+            r = oracle_sample(int(no[g + 1] - no[g]), e, cfg)
+            spent += r["wall_s"]
+            total += r["step_s"]
+            used += 1
+        if i >= args.warmup:
+            steps.append((used, total))
+    used = steps[-1][0]
+    per_graph_s = float(np.mean([t / u for u, t in steps]))
+    model, ncpu = cpu_info()
+    value = round(1.0 / per_graph_s, 4)
+    sample = (f"each step: the first {used} graphs of a stride-32 order over the {Gn}; per graph the three edge "
+              f"stages plus 1 timed FA2 iteration, step time = edge stages + {cfg['iterations']} x FA2 iteration")
+    return {"impl": "reference", "metric": "graphs/s laid out (sketch, communities, supergraph, FA2)",
+            "value": value, "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(per_graph_s * Gn * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {cfg['desc']}", "graphs": Gn,
+                       "fa2_iterations": cfg["iterations"]},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": model, "host_cpus": ncpu},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def reference_arm(args, dist: Dist):
     """The oracle as the reference implementation, on the host cores."""
     if dist.rank != 0:
         return None
+    if WORKLOADS[args.workload].get("batched"):
+        return reference_arm_batched(args, dist)
     cfg = WORKLOADS[args.workload]
     n, edges_np, _ = graphgen.load(args.workload)
     m = edges_np.shape[0]
@@ -573,6 +725,8 @@ def main():
                     help="override the workload's FA2 iteration count (short profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--no-per-graph", action="store_true",
+                    help="batched workload: skip the one-call-per-graph comparison")
     ap.add_argument("--precision-sample", type=int, default=0,
                     help="whole-graph workloads: nodes sampled for the FP64 force-error report")
     args = ap.parse_args()
@@ -584,6 +738,8 @@ def main():
             out = reference_arm(args, dist)
         elif WORKLOADS[args.workload].get("whole"):
             out = gpu_arm_whole(args, dist)
+        elif WORKLOADS[args.workload].get("batched"):
+            out = gpu_arm_batched(args, dist)
         else:
             out = gpu_arm(args, dist)
     finally:

@@ -306,3 +306,25 @@ def load(name: str):
         np.save(fm, memb)
     os.replace(tmp, fe)
     return n, edges, memb
+
+
+def load_batch(name: str = "batch512"):
+    """The 512-graph batching workload (``batch_set()`` with its defaults),
+    joined for the batched entry point: returns ``(edges, edge_off,
+    node_off)`` -- the concatenated int32 edge lists in LOCAL node ids, int64
+    edge offsets and int32 node offsets, each offset array of length G + 1.
+    Cached as one ``.npz`` file."""
+    if name != "batch512":
+        raise KeyError(name)
+    f = _cache_dir() / f"{name}.npz"
+    if f.exists():
+        z = np.load(f)
+        return z["edges"], z["edge_off"], z["node_off"]
+    graphs = batch_set()
+    edges = np.concatenate([e for e, _ in graphs]).astype(np.int32)
+    edge_off = np.concatenate([[0], np.cumsum([e.shape[0] for e, _ in graphs])]).astype(np.int64)
+    node_off = np.concatenate([[0], np.cumsum([mem.shape[0] for _, mem in graphs])]).astype(np.int32)
+    tmp = _cache_dir() / f"{name}.tmp.npz"
+    np.savez(tmp, edges=edges, edge_off=edge_off, node_off=node_off)
+    os.replace(tmp, f)
+    return edges, edge_off, node_off

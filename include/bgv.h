@@ -336,6 +336,53 @@ int bgv_layout_host(const int32_t *h_edges, int64_t m, int32_t n, const bgv_layo
  * and the outputs. */
 size_t bgv_layout_host_ws_size(int64_t m, int32_t n, const bgv_layout_params *p);
 
+/* ------------------------------------------------------------------------
+ * 6. Batched form: G independent graphs laid out in one pass of every
+ *    stage (Algorithm 3 applied to each graph; the paper runs its tables
+ *    graph by graph, so this entry point has no counterpart there).  The
+ *    result for every graph is the one bgv_layout gives for it alone: the
+ *    integer stages (node_map, supernode and superedge counts) exactly, the
+ *    positions up to FP32 summation order, because graph g keeps its own
+ *    sketch matrices (rows x width each, local node ids hashed), its own
+ *    degree threshold (floor(2 m_g / n_g) when p->threshold is 0), its own
+ *    community-size sketch, quadtree frame, initial square, and speed.
+ *
+ * Host arrays: edge_off [G+1] int64 and node_off [G+1] int32, both
+ * starting at 0; graph g has node_off[g+1] - node_off[g] >= 1 nodes and
+ * the edges edges[edge_off[g] .. edge_off[g+1]) as (u, v) int32 pairs of
+ * LOCAL ids 0 .. n_g - 1.  An endpoint outside its graph sets
+ * BGV_DEV_BADEDGE and the call returns BGV_EDEVICE.  Totals must fit the
+ * single-graph limits (N < 2^31 - 1 nodes, m < 2^31 edges).
+ * Outputs (device): node_map [N] int32 -- the LOCAL supernode id of every
+ * node; xy [N][2] float and radius [N] float, graph g's supernodes in rows
+ * K_off[g] .. K_off[g+1] (first K_off[G] rows valid).  Host outputs:
+ * K_off [G+1], Es_off [G+1] int64, the supernode and superedge offsets.
+ * Synchronises `stream` after the supergraph and at the end.
+ * ---------------------------------------------------------------------- */
+size_t bgv_layout_batched_ws_size(int32_t G, const int64_t *edge_off, const int32_t *node_off,
+                                  const bgv_layout_params *p);
+int bgv_layout_batched(const int32_t *edges, int32_t G, const int64_t *edge_off, const int32_t *node_off,
+                       const bgv_layout_params *p, int32_t *node_map, float *xy, float *radius,
+                       int64_t *K_off, int64_t *Es_off, void *ws, size_t ws_bytes, void *stream);
+
+/* Batched ForceAtlas2 on caller supergraphs: bodies of graph g are rows
+ * koff[g] .. koff[g+1] (host int64 [G+1], strictly increasing, koff[0] = 0,
+ * K = koff[G]) and the CSR (K rows, nnz entries, global row ids) must not
+ * link two graphs.  Each graph gets its own frame, initial square (R =
+ * sqrt(K_g), local index in the SplitMix64 state), and speed: speed is
+ * [G] device double.  The offsets are copied into `ws` on every call. */
+size_t bgv_fa2_ws_size_batched(int32_t G, int64_t K, int64_t nnz);
+int bgv_fa2_init_batched(int32_t G, const int64_t *koff, const bgv_fa2_params *p, float *pos, float *Fprev,
+                         double *speed, void *ws, size_t ws_bytes, void *stream);
+int bgv_fa2_forces_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32_t *csr_off,
+                           const int32_t *csr_adj, const uint32_t *csr_w, const uint32_t *mass,
+                           const bgv_fa2_params *p, const float *pos, float *Fr, float *Fa, float *Fg,
+                           void *ws, size_t ws_bytes, void *stream);
+int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32_t *csr_off,
+                        const int32_t *csr_adj, const uint32_t *csr_w, const uint32_t *mass,
+                        const bgv_fa2_params *p, int32_t iterations, int32_t use_graph, float *pos, float *F,
+                        float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes as C
 import pathlib
 
+import numpy as np
 import torch
 
 _LIB_PATH = pathlib.Path(__file__).resolve().parent / "libbgv.so"
@@ -81,6 +82,14 @@ _sig("bgv_layout", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, P, P,
 _sig("bgv_layout_host_ws_size", sz, [i64, i32, C.POINTER(bgv_layout_params)])
 _sig("bgv_layout_host", C.c_int, [P, i64, i32, C.POINTER(bgv_layout_params), P, P, P, C.POINTER(i64),
                                   C.POINTER(i64), P, sz, P])
+_sig("bgv_layout_batched_ws_size", sz, [i32, P, P, C.POINTER(bgv_layout_params)])
+_sig("bgv_layout_batched", C.c_int, [P, i32, P, P, C.POINTER(bgv_layout_params), P, P, P, P, P, P, sz, P])
+_sig("bgv_fa2_ws_size_batched", sz, [i32, i64, i64])
+_sig("bgv_fa2_init_batched", C.c_int, [i32, P, C.POINTER(bgv_fa2_params), P, P, P, P, sz, P])
+_sig("bgv_fa2_forces_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_fa2_params), P, P, P, P, P, sz,
+                                         P])
+_sig("bgv_fa2_run_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P,
+                                      sz, P])
 
 #: every symbol this binding resolves from the library
 EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees", "bgv_sketch_degrees_noalloc",
@@ -88,7 +97,8 @@ EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sket
            "bgv_graph_csr_ws_size", "bgv_graph_csr", "bgv_colour_groups_ws_size", "bgv_colour_groups",
            "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
            "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
-           "bgv_layout_host_ws_size", "bgv_layout_host"]
+           "bgv_layout_host_ws_size", "bgv_layout_host", "bgv_layout_batched_ws_size", "bgv_layout_batched",
+           "bgv_fa2_ws_size_batched", "bgv_fa2_init_batched", "bgv_fa2_forces_batched", "bgv_fa2_run_batched"]
 
 
 class BgvError(RuntimeError):
@@ -291,3 +301,54 @@ def bgv_layout_host(h_edges, m, n, params, h_node_map, h_xy, h_radius, ws, ws_by
     _chk(_lib.bgv_layout_host(_p(h_edges), m, n, C.byref(params), _p(h_node_map), _p(h_xy), _p(h_radius),
                               C.byref(K), C.byref(Es), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_layout_host")
     return K.value, Es.value
+
+
+def _host(a, dtype):
+    """A contiguous host array of ``dtype`` and its address."""
+    a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return a, a.ctypes.data
+
+
+def bgv_layout_batched_ws_size(G: int, edge_off, node_off, params) -> int:
+    eo, pe = _host(edge_off, np.int64)
+    no, pn = _host(node_off, np.int32)
+    return _lib.bgv_layout_batched_ws_size(G, pe, pn, C.byref(params))
+
+
+def bgv_layout_batched(edges, G, edge_off, node_off, params, node_map, xy, radius, ws, ws_bytes=None, stream=None):
+    """``edge_off`` [G+1] int64 and ``node_off`` [G+1] int32 on the host;
+    returns the host offsets ``(K_off, Es_off)``, each int64 [G+1]."""
+    eo, pe = _host(edge_off, np.int64)
+    no, pn = _host(node_off, np.int32)
+    K_off = np.zeros(G + 1, np.int64)
+    Es_off = np.zeros(G + 1, np.int64)
+    _chk(_lib.bgv_layout_batched(_p(edges), G, pe, pn, C.byref(params), _p(node_map), _p(xy), _p(radius),
+                                 K_off.ctypes.data, Es_off.ctypes.data, _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_layout_batched")
+    return K_off, Es_off
+
+
+def bgv_fa2_ws_size_batched(G: int, K: int, nnz: int) -> int:
+    return _lib.bgv_fa2_ws_size_batched(G, K, nnz)
+
+
+def bgv_fa2_init_batched(G, koff, params, pos, Fprev, speed, ws, ws_bytes=None, stream=None):
+    ko, pk = _host(koff, np.int64)
+    _chk(_lib.bgv_fa2_init_batched(G, pk, C.byref(params), _p(pos), _p(Fprev), _p(speed), _p(ws),
+                                   _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_init_batched")
+
+
+def bgv_fa2_forces_batched(G, koff, nnz, csr_off, csr_adj, csr_w, mass, params, pos, Fr, Fa, Fg, ws, ws_bytes=None,
+                           stream=None):
+    ko, pk = _host(koff, np.int64)
+    _chk(_lib.bgv_fa2_forces_batched(G, pk, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params),
+                                     _p(pos), _p(Fr), _p(Fa), _p(Fg), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_fa2_forces_batched")
+
+
+def bgv_fa2_run_batched(G, koff, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, use_graph, pos, F, Fprev,
+                        speed, ws, ws_bytes=None, stream=None):
+    ko, pk = _host(koff, np.int64)
+    _chk(_lib.bgv_fa2_run_batched(G, pk, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params),
+                                  iterations, use_graph, _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws),
+                                  _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_run_batched")

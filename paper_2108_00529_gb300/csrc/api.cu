@@ -69,7 +69,7 @@ struct LayoutBuffers {
     char *scratch;  // shared by the stages, which run one after another
 };
 
-size_t stage_scratch_bytes(int64_t m, int32_t n, const bgv_layout_params *p) {
+size_t stage_scratch_bytes(int64_t m, int32_t n, const bgv_layout_params *p, int32_t G = 1) {
     size_t need = 0;
     {
         Carver c(nullptr, 0);
@@ -80,22 +80,22 @@ size_t stage_scratch_bytes(int64_t m, int32_t n, const bgv_layout_params *p) {
     {
         Carver c(nullptr, 0);
         CommScratch s;
-        carve_comm(c, m, n, s);
+        carve_comm(c, m, n, s, G > 1);
         need = c.used() > need ? c.used() : need;
     }
     {
         Carver c(nullptr, 0);
         SuperScratch s;
-        carve_super(c, m, n, p->rows, p->width, s);
+        carve_super(c, m, n, p->rows, p->width, s, G);
         need = c.used() > need ? c.used() : need;
     }
-    size_t f = fa2_scratch_bytes(n, 2 * m);
+    size_t f = fa2_scratch_bytes(n, 2 * m, G);
     return f > need ? f : need;
 }
 
-void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, LayoutBuffers &b) {
-    const size_t nn = size_t(n), mm = size_t(m > 0 ? m : 1);
-    b.sketch = c.take<uint32_t>(size_t(p->rows) * size_t(p->width));
+void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, LayoutBuffers &b, int32_t G = 1) {
+    const size_t nn = size_t(n), mm = size_t(m > 0 ? m : 1), gg = size_t(G > 1 ? G : 1);
+    b.sketch = c.take<uint32_t>(size_t(p->rows) * size_t(p->width) * gg);
     b.deg_est = c.take<uint32_t>(nn);
     b.labels = c.take<int32_t>(nn);
     b.K_dev = c.take<int64_t>(1);
@@ -109,8 +109,8 @@ void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, L
     b.csr_w = c.take<uint32_t>(2 * mm);
     b.F = c.take<float>(2 * nn);
     b.Fprev = c.take<float>(2 * nn);
-    b.speed = c.take<double>(1);
-    b.scratch = c.take<char>(stage_scratch_bytes(m, n, p));
+    b.speed = c.take<double>(gg);
+    b.scratch = c.take<char>(stage_scratch_bytes(m, n, p, G));
 }
 
 int check_layout_params(const bgv_layout_params *p) {
@@ -123,25 +123,26 @@ int check_layout_params(const bgv_layout_params *p) {
 
 int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w, const uint32_t *mass,
              const bgv_fa2_params &p, int32_t iterations, int32_t use_graph, float *pos, float *F, float *Fprev,
-             double *speed, WsHeader *hdr, void *scratch, cudaStream_t st) {
+             double *speed, WsHeader *hdr, void *scratch, cudaStream_t st, int32_t G = 1,
+             const int64_t *koff = nullptr) {
     if (iterations <= 0 || K <= 0) return BGV_OK;
     if (!use_graph || st == nullptr || iterations < 2) {
         for (int32_t t = 0; t < iterations; ++t)
             BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
-                            scratch, st, nullptr, t == 0));
+                            scratch, st, nullptr, t == 0, G, koff));
         return BGV_OK;
     }
     // The first step runs outside the graph and builds the attraction plan;
     // the captured step reuses it.
     BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch,
-                    st, nullptr, true));
+                    st, nullptr, true, G, koff));
     if (iterations == 1) return BGV_OK;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const unsigned long long before = launches_issued();
     int rc = run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st,
-                     nullptr, false);
+                     nullptr, false, G, koff);
     const unsigned long long per_step = launches_issued() - before;  // captured, not yet run
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc != BGV_OK || ce != cudaSuccess) {
@@ -253,6 +254,214 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
         note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
         BGV_TRY(launch_status());
     }
+    return BGV_OK;
+}
+
+// ------------------------------------------------------------- batched form
+// G independent graphs in one pass of every stage.  The caller's edge lists
+// (local node ids, concatenated) are rewritten once into one id space in
+// which graph g owns nodes [node_off[g], node_off[g+1]); every stage then
+// runs over all graphs in the same launches and keeps them apart as
+// BatchView describes.  Supernodes come out graph-major: graph g owns
+// supernodes [K_off[g], K_off[g+1]) and superedges [Es_off[g], Es_off[g+1]).
+struct BatchBuffers {
+    int32_t *edges;        // [2m] global ids
+    int32_t *node_off;     // [G + 1]
+    int64_t *edge_off;     // [G + 1]
+    int32_t *node_graph;   // [N]
+    uint32_t *D0;          // [G]
+    int64_t *koff;         // [G + 1] supernode offsets
+    int64_t *Es_off;       // [G + 1] superedge offsets
+    int32_t *node_map;     // [N] global supernode ids
+};
+
+void carve_batch(Carver &c, int64_t m, int32_t N, int32_t G, BatchBuffers &b) {
+    const size_t gg = size_t(G) + 1;
+    b.edges = c.take<int32_t>(2 * size_t(m > 0 ? m : 1));
+    b.node_off = c.take<int32_t>(gg);
+    b.edge_off = c.take<int64_t>(gg);
+    b.node_graph = c.take<int32_t>(size_t(N));
+    b.D0 = c.take<uint32_t>(gg);
+    b.koff = c.take<int64_t>(gg);
+    b.Es_off = c.take<int64_t>(gg);
+    b.node_map = c.take<int32_t>(size_t(N));
+}
+
+// Largest g with off[g] <= x (off ascending, off[0] = 0 <= x).
+template <class T>
+__device__ __forceinline__ int32_t graph_of(const T *off, int32_t G, T x) {
+    int32_t lo = 0, hi = G;  // off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_nodes(int32_t N, int32_t G, const int32_t *node_off, int32_t *node_graph) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < N; v += int64_t(gridDim.x) * blockDim.x)
+        node_graph[v] = graph_of(node_off, G, int32_t(v));
+}
+
+// Local -> global endpoint ids.  An endpoint outside its own graph becomes
+// -1, which the stages report as BGV_DEV_BADEDGE.
+__global__ void k_batch_edges(const int32_t *__restrict__ in, int64_t m, int32_t G, const int64_t *edge_off,
+                              const int32_t *node_off, int32_t *__restrict__ out) {
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t g = graph_of(edge_off, G, e);
+        const int32_t base = node_off[g], ng = node_off[g + 1] - base;
+        const int2 uv = reinterpret_cast<const int2 *>(in)[e];
+        const int32_t u = static_cast<uint32_t>(uv.x) < static_cast<uint32_t>(ng) ? uv.x + base : -1;
+        const int32_t v = static_cast<uint32_t>(uv.y) < static_cast<uint32_t>(ng) ? uv.y + base : -1;
+        reinterpret_cast<int2 *>(out)[e] = make_int2(u, v);
+    }
+}
+
+// Supernode offsets (the dense rank of a graph's first node id, as labels
+// are node ids of their own graph) and superedge offsets (superedges are
+// sorted by source supernode).
+__global__ void k_batch_offsets(int32_t G, const int32_t *node_off, const uint32_t *rank, const int64_t *K_dev,
+                                const int32_t *ssrc, const int64_t *Es_dev, int64_t *koff, int64_t *Es_off) {
+    const int64_t Es = *Es_dev;
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x) {
+        const int64_t k = g == G ? *K_dev : int64_t(rank[node_off[g]]);
+        koff[g] = k;
+        int64_t lo = 0, hi = Es;  // first superedge with source >= k
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (int64_t(ssrc[mid]) < k) lo = mid + 1; else hi = mid;
+        }
+        Es_off[g] = lo;
+    }
+}
+
+__global__ void k_batch_local_map(int32_t N, const int32_t *node_map, const int32_t *node_graph, const int64_t *koff,
+                                  int32_t *out) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < N; v += int64_t(gridDim.x) * blockDim.x)
+        out[v] = int32_t(node_map[v] - koff[node_graph[v]]);
+}
+
+// Host-side check of the offsets; returns the totals.
+int check_batch(int32_t G, const int64_t *edge_off, const int32_t *node_off, int64_t *m_out, int32_t *N_out) {
+    if (G < 1 || G > (1 << 20) || !edge_off || !node_off) return BGV_EINVAL;
+    if (edge_off[0] != 0 || node_off[0] != 0) return BGV_EINVAL;
+    for (int32_t g = 0; g < G; ++g)
+        if (node_off[g + 1] <= node_off[g] || edge_off[g + 1] < edge_off[g]) return BGV_EINVAL;
+    if (node_off[G] >= 0x7FFFFFFF || edge_off[G] >= (int64_t(1) << 31)) return BGV_EINVAL;
+    *m_out = edge_off[G];
+    *N_out = node_off[G];
+    return BGV_OK;
+}
+
+size_t layout_batched_ws(int64_t m, int32_t N, int32_t G, const bgv_layout_params *p) {
+    Carver c(nullptr, kHeaderBytes);
+    LayoutBuffers b;
+    carve_layout(c, m, N, p, b, G);
+    BatchBuffers bb;
+    carve_batch(c, m, N, G, bb);
+    return c.used();
+}
+
+int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, const int32_t *node_off, int32_t G,
+                          int64_t m, int32_t N, const bgv_layout_params *p, int32_t *node_map, float *xy,
+                          float *radius, int64_t *K_off, int64_t *Es_off, void *ws, cudaStream_t st) {
+    Carver c(ws, kHeaderBytes);
+    LayoutBuffers b;
+    carve_layout(c, m, N, p, b, G);
+    BatchBuffers bb;
+    carve_batch(c, m, N, G, bb);
+    WsHeader *hdr = header(ws);
+    uint32_t *status = &hdr->status;
+    const HashFamily h = make_hash_family(p->seed, p->rows, uint32_t(p->width));
+    // first-round thresholds: the caller's, else floor(2 m_g / n_g) per graph
+    uint32_t *D0 = static_cast<uint32_t *>(malloc(sizeof(uint32_t) * size_t(G)));
+    if (!D0) return BGV_EINVAL;
+    for (int32_t g = 0; g < G; ++g)
+        D0[g] = p->threshold ? p->threshold
+                             : uint32_t((2 * (edge_off[g + 1] - edge_off[g])) / (node_off[g + 1] - node_off[g]));
+    cudaError_t ce = cudaMemcpyAsync(bb.D0, D0, sizeof(uint32_t) * size_t(G), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // D0 is freed next
+    free(D0);
+    BGV_CUDA(ce);
+    BGV_CUDA(cudaMemcpyAsync(bb.node_off, node_off, sizeof(int32_t) * (size_t(G) + 1), cudaMemcpyHostToDevice, st));
+    BGV_CUDA(cudaMemcpyAsync(bb.edge_off, edge_off, sizeof(int64_t) * (size_t(G) + 1), cudaMemcpyHostToDevice, st));
+    BGV_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
+    note_launch(), k_batch_nodes<<<grid_for(N, 256, 152 * 8), 256, 0, st>>>(N, G, bb.node_off, bb.node_graph);
+    BGV_TRY(launch_status());
+    if (m > 0) {
+        note_launch(), k_batch_edges<<<grid_for(m, 256, 152 * 16), 256, 0, st>>>(edges_local, m, G, bb.edge_off,
+                                                                                  bb.node_off, bb.edges);
+        BGV_TRY(launch_status());
+    }
+    const BatchView view{G, bb.node_off, bb.node_graph, bb.D0};
+    {
+        Carver sc(b.scratch, 0);
+        SketchScratch s;
+        carve_sketch(sc, m, N, p->rows, p->width, s);
+        BGV_TRY(run_sketch(bb.edges, m, N, h, b.sketch, b.deg_est, s, status, st, &view));
+    }
+    {
+        Carver sc(b.scratch, 0);
+        CommScratch s;
+        carve_comm(sc, m, N, s, true);
+        BGV_TRY(run_communities(bb.edges, m, N, b.deg_est, p->passes, 0, p->growth, p->tie_mode, b.labels, nullptr, s,
+                                status, st, &view));
+    }
+    {
+        Carver sc(b.scratch, 0);
+        SuperScratch s;
+        carve_super(sc, m, N, p->rows, p->width, s, G);
+        BGV_TRY(run_supergraph(bb.edges, m, N, b.labels, b.deg_est, h, bb.node_map, b.K_dev, b.ssrc, b.sdst, b.sw,
+                               b.Es_dev, b.mass, b.csr_off, b.csr_adj, b.csr_w, nullptr, nullptr, nullptr, s, status,
+                               st, &view));
+        note_launch(), k_batch_offsets<<<grid_for(int64_t(G) + 1, 256, 152), 256, 0, st>>>(
+            G, bb.node_off, s.rank, b.K_dev, b.ssrc, b.Es_dev, bb.koff, bb.Es_off);
+        BGV_TRY(launch_status());
+    }
+    note_launch(), k_batch_local_map<<<grid_for(N, 256, 152 * 8), 256, 0, st>>>(N, bb.node_map, bb.node_graph,
+                                                                                  bb.koff, node_map);
+    BGV_TRY(launch_status());
+    uint32_t dev_status = 0;
+    BGV_CUDA(cudaMemcpyAsync(K_off, bb.koff, sizeof(int64_t) * (size_t(G) + 1), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaMemcpyAsync(Es_off, bb.Es_off, sizeof(int64_t) * (size_t(G) + 1), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaMemcpyAsync(&dev_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    if (dev_status) return BGV_EDEVICE;
+    const int64_t K = K_off[G], Es = Es_off[G];
+    BGV_TRY(run_fa2_init(K, p->fa2, xy, b.Fprev, b.speed, st, G, bb.koff));
+    BGV_TRY(fa2_loop(K, 2 * Es, b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
+                     b.Fprev, b.speed, hdr, b.scratch, st, G, bb.koff));
+    if (radius) {
+        note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
+        BGV_TRY(launch_status());
+    }
+    return BGV_OK;
+}
+
+// Batched FA2 on caller supergraphs: the graph offsets are validated on the
+// host and copied into the workspace, right after the header.
+size_t fa2_batched_ws(int64_t K, int64_t nnz, int32_t G) {
+    Carver c(nullptr, kHeaderBytes);
+    c.take<int64_t>(size_t(G) + 1);
+    c.take<char>(fa2_scratch_bytes(K, nnz, G));
+    return c.used();
+}
+
+int check_koff(int32_t G, const int64_t *koff, int64_t K, int max_depth) {
+    if (G < 1 || G > (1 << 20) || !koff || koff[0] != 0 || koff[G] != K) return BGV_EINVAL;
+    if (!fa2_batch_fits(G, max_depth)) return BGV_EINVAL;
+    for (int32_t g = 0; g < G; ++g)
+        if (koff[g + 1] <= koff[g]) return BGV_EINVAL;
+    return BGV_OK;
+}
+
+int fa2_batched_setup(int32_t G, const int64_t *koff, int64_t K, int max_depth, void *ws, cudaStream_t st,
+                      int64_t **dkoff, char **scratch) {
+    BGV_TRY(check_koff(G, koff, K, max_depth));
+    Carver c(ws, kHeaderBytes);
+    *dkoff = c.take<int64_t>(size_t(G) + 1);
+    *scratch = c.take<char>(0);
+    BGV_CUDA(cudaMemcpyAsync(*dkoff, koff, sizeof(int64_t) * (size_t(G) + 1), cudaMemcpyHostToDevice, st));
     return BGV_OK;
 }
 
@@ -393,13 +602,20 @@ int bgv_fa2_init(int64_t K, const bgv_fa2_params *p, float *pos, float *Fprev, d
 
 size_t bgv_fa2_ws_size(int64_t K, int64_t nnz) { return kHeaderBytes + fa2_scratch_bytes(K, nnz); }
 
-static int check_fa2_args(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w,
-                          const uint32_t *mass, const bgv_fa2_params *p, const float *pos, void *ws,
-                          size_t ws_bytes) {
+static int check_fa2_inputs(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w,
+                            const uint32_t *mass, const bgv_fa2_params *p, const float *pos) {
     if (K < 0 || K >= 0x7FFFFFFF || nnz < 0 || nnz >= (int64_t(1) << 31)) return BGV_EINVAL;
     BGV_TRY(fa2_check_params(p));
     if (K == 0) return BGV_OK;
     if (!off || !adj || !w || !mass || !pos || !aligned(pos, 8)) return BGV_EINVAL;
+    return BGV_OK;
+}
+
+static int check_fa2_args(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, const uint32_t *w,
+                          const uint32_t *mass, const bgv_fa2_params *p, const float *pos, void *ws,
+                          size_t ws_bytes) {
+    BGV_TRY(check_fa2_inputs(K, nnz, off, adj, w, mass, p, pos));
+    if (K == 0) return BGV_OK;
     return check_ws(ws, ws_bytes, bgv_fa2_ws_size(K, nnz));
 }
 
@@ -570,6 +786,85 @@ int bgv_layout_host(const int32_t *h_edges, int64_t m, int32_t n, const bgv_layo
     if (K_out) *K_out = K;
     if (Es_out) *Es_out = Es;
     return dev_status ? BGV_EDEVICE : BGV_OK;
+}
+
+size_t bgv_layout_batched_ws_size(int32_t G, const int64_t *edge_off, const int32_t *node_off,
+                                  const bgv_layout_params *p) {
+    int64_t m = 0;
+    int32_t N = 0;
+    if (check_layout_params(p) != BGV_OK || check_batch(G, edge_off, node_off, &m, &N) != BGV_OK) return 0;
+    return layout_batched_ws(m, N, G, p);
+}
+
+int bgv_layout_batched(const int32_t *edges, int32_t G, const int64_t *edge_off, const int32_t *node_off,
+                       const bgv_layout_params *p, int32_t *node_map, float *xy, float *radius, int64_t *K_off,
+                       int64_t *Es_off, void *ws, size_t ws_bytes, void *stream) {
+    int64_t m = 0;
+    int32_t N = 0;
+    BGV_TRY(check_batch(G, edge_off, node_off, &m, &N));
+    BGV_TRY(check_layout_params(p));
+    if (!fa2_batch_fits(G, p->fa2.max_depth)) return BGV_EINVAL;
+    if ((m > 0 && (!edges || !aligned(edges, 8))) || !node_map || !xy || !aligned(xy, 8) || !K_off || !Es_off)
+        return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, layout_batched_ws(m, N, G, p)));
+    cudaStream_t st = as_stream(stream);
+    BGV_TRY(layout_batched_device(edges, edge_off, node_off, G, m, N, p, node_map, xy, radius, K_off, Es_off, ws, st));
+    uint32_t dev_status = 0;
+    BGV_CUDA(cudaMemcpyAsync(&dev_status, status_ptr(ws), sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    return dev_status ? BGV_EDEVICE : BGV_OK;
+}
+
+size_t bgv_fa2_ws_size_batched(int32_t G, int64_t K, int64_t nnz) {
+    if (G < 1 || G > (1 << 20)) return 0;
+    return fa2_batched_ws(K, nnz, G);
+}
+
+int bgv_fa2_init_batched(int32_t G, const int64_t *koff, const bgv_fa2_params *p, float *pos, float *Fprev,
+                         double *speed, void *ws, size_t ws_bytes, void *stream) {
+    if (!koff || G < 1 || G > (1 << 20)) return BGV_EINVAL;
+    const int64_t K = koff[G];
+    if (K >= 0x7FFFFFFF || !pos || !Fprev || !speed || !aligned(pos, 8)) return BGV_EINVAL;
+    BGV_TRY(fa2_check_params(p));
+    BGV_TRY(check_ws(ws, ws_bytes, fa2_batched_ws(K, 0, G)));
+    cudaStream_t st = as_stream(stream);
+    int64_t *dkoff = nullptr;
+    char *scratch = nullptr;
+    BGV_TRY(fa2_batched_setup(G, koff, K, p->max_depth, ws, st, &dkoff, &scratch));
+    return run_fa2_init(K, *p, pos, Fprev, speed, st, G, dkoff);
+}
+
+int bgv_fa2_forces_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32_t *csr_off,
+                           const int32_t *csr_adj, const uint32_t *csr_w, const uint32_t *mass,
+                           const bgv_fa2_params *p, const float *pos, float *Fr, float *Fa, float *Fg, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (!koff || G < 1 || G > (1 << 20)) return BGV_EINVAL;
+    const int64_t K = koff[G];
+    BGV_TRY(check_fa2_inputs(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos));
+    BGV_TRY(check_ws(ws, ws_bytes, fa2_batched_ws(K, nnz, G)));
+    cudaStream_t st = as_stream(stream);
+    int64_t *dkoff = nullptr;
+    char *scratch = nullptr;
+    BGV_TRY(fa2_batched_setup(G, koff, K, p->max_depth, ws, st, &dkoff, &scratch));
+    return run_fa2(0, K, nnz, csr_off, csr_adj, csr_w, mass, *p, const_cast<float *>(pos), nullptr, nullptr, nullptr,
+                   Fr, Fa, Fg, header(ws), scratch, st, nullptr, true, G, dkoff);
+}
+
+int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj,
+                        const uint32_t *csr_w, const uint32_t *mass, const bgv_fa2_params *p, int32_t iterations,
+                        int32_t use_graph, float *pos, float *F, float *Fprev, double *speed, void *ws,
+                        size_t ws_bytes, void *stream) {
+    if (!koff || G < 1 || G > (1 << 20) || iterations < 0) return BGV_EINVAL;
+    const int64_t K = koff[G];
+    BGV_TRY(check_fa2_inputs(K, nnz, csr_off, csr_adj, csr_w, mass, p, pos));
+    if (!F || !Fprev || !speed) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, fa2_batched_ws(K, nnz, G)));
+    cudaStream_t st = as_stream(stream);
+    int64_t *dkoff = nullptr;
+    char *scratch = nullptr;
+    BGV_TRY(fa2_batched_setup(G, koff, K, p->max_depth, ws, st, &dkoff, &scratch));
+    return fa2_loop(K, nnz, csr_off, csr_adj, csr_w, mass, *p, iterations, use_graph, pos, F, Fprev, speed,
+                    header(ws), scratch, st, G, dkoff);
 }
 
 }  // extern "C"

@@ -142,21 +142,38 @@ inline int bits_for(int64_t n) {
 // --------------------------------------------------------- stage internals
 // Enqueue-only stage bodies used by the public entry points and the
 // pipeline; `status` points at the device status word.
+
+// Batched form: G independent graphs laid side by side in one id space.
+// Graph g owns nodes [node_off[g], node_off[g+1]); every stage keeps the
+// graphs apart exactly as G separate calls would (own sketch matrices,
+// hashing of local ids, own degree thresholds).  All arrays on the device.
+struct BatchView {
+    int32_t G;
+    const int32_t *node_off;    // [G + 1]
+    const int32_t *node_graph;  // [N] graph of each node
+    const uint32_t *D0;         // [G] first-round degree threshold
+};
 struct SketchScratch {
     uint32_t *deg;
 };
 void carve_sketch(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SketchScratch &s);
+// With `batch`, `sketch` holds G matrices of rows x width, one per graph.
 int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, uint32_t *sketch,
-               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st);
+               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st,
+               const BatchView *batch = nullptr);
 
 struct CommScratch {
     uint2 *state;                   // (degree, label) per node
+    uint4 *bstate;                  // batched form: (degree, label, threshold, 0)
     unsigned long long *best;       // packed (edge index, label) proposals
 };
-void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s);
+void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched = false);
+// With `batch`, the threshold of every node starts at its graph's D0 and
+// `threshold` is ignored.
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels,
-                    uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st);
+                    uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st,
+                    const BatchView *batch = nullptr);
 
 struct SuperScratch {
     uint32_t *flags;        // [n] label present / CSR counts
@@ -165,7 +182,7 @@ struct SuperScratch {
     uint32_t *src_first, *src_end;  // [n] runs of each supernode in (src, dst) order
     uint32_t *dst_first, *dst_end;  // [n] runs in (dst, src) order
     int64_t *m_cut;         // device scalar
-    unsigned long long *sketch;  // [rows * width]
+    unsigned long long *sketch;  // [rows * width], batched form: one per graph
     uint32_t *heads;        // [m]
     uint32_t *segidx;       // [m + 1]
     uint32_t *segstart;     // [m]
@@ -173,17 +190,26 @@ struct SuperScratch {
     SortBuffers sort_cut;   // m keys
     SortBuffers sort_dst;   // m keys + values
 };
-void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s);
+void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s, int32_t G = 1);
+// With `batch`, community labels are node ids of their own graph, so the
+// supernodes come out graph-major; the community-size sketch of graph g
+// hashes local labels into its own matrix.
 int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *labels, const uint32_t *deg_est,
                    const HashFamily &h, int32_t *node_map, int64_t *K_dev, int32_t *ssrc, int32_t *sdst,
                    uint32_t *sw, int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
                    uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
-                   const SuperScratch &s, uint32_t *status, cudaStream_t st);
+                   const SuperScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch = nullptr);
 
-// Scratch for one FA2 step, carved from `scratch` (not counting a header).
-size_t fa2_scratch_bytes(int64_t K, int64_t nnz);
+// Scratch for one FA2 step over G graphs (G = 1: a single layout), carved
+// from `scratch` (not counting a header).
+size_t fa2_scratch_bytes(int64_t K, int64_t nnz, int32_t G = 1);
 int fa2_check_params(const bgv_fa2_params *p);
-int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st);
+// Batched form (G > 1): graph g owns bodies [koff[g], koff[g+1]) (koff on the
+// device); speed then holds G values.  The sort keys put the graph id above
+// the 2 max_depth Morton bits, so both must fit in 64 bits.
+inline bool fa2_batch_fits(int32_t G, int max_depth) { return G <= 1 || 2 * max_depth + bits_for(G) <= 64; }
+int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st,
+                 int32_t G = 1, const int64_t *koff = nullptr);
 // mode 0: forces only (Fr/Fa/Fg outputs, any may be null); mode 1: full step.
 // `marks` (optional) receives kFa2Stages + 1 event records at the stage
 // boundaries: frame+keys, sort, gather, tree, quad, repulsion, node, update.
@@ -193,6 +219,6 @@ constexpr int kFa2Stages = 8;
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
-            cudaEvent_t *marks = nullptr, bool build_plan = true);
+            cudaEvent_t *marks = nullptr, bool build_plan = true, int32_t G = 1, const int64_t *koff = nullptr);
 
 }  // namespace bgv

@@ -9,6 +9,12 @@
 // apply kernel then updates every node that received a proposal and resets
 // the proposal slot for the next round.  No state is written during a
 // propose pass, so every edge reads the snapshot of the round.
+//
+// Batched form: each node also carries its graph's threshold, (degree,
+// label, threshold) in one 16-byte word, so a propose still gathers one
+// 32-byte sector per endpoint and graphs with different thresholds share a
+// launch.  Edge indices and labels are global but ordered as inside each
+// graph, so the winners are those of G separate runs.
 #include "bgv_internal.cuh"
 
 namespace bgv {
@@ -26,33 +32,115 @@ __global__ void __launch_bounds__(kThreads) k_comm_init(const uint32_t *__restri
     }
 }
 
-__device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, int32_t n, const uint2 *state,
-                                             unsigned long long *best, uint32_t D, int tie_mode,
-                                             uint32_t *status) {
+// The rule of one edge on the round's snapshot: returns the joining node w
+// and the label it is offered, or -1 when the edge moves nothing.
+__device__ __forceinline__ int32_t edge_rule(int32_t u, int32_t v, uint32_t du, uint32_t lu, uint32_t dv, uint32_t lv,
+                                             uint32_t D, int tie_mode, uint32_t *lab) {
+    if (du > D || dv > D) return -1;
+    if (lu == lv) return -1;
+    if (du > dv) {
+        *lab = lu;
+        return v;
+    }
+    if (dv > du) {
+        *lab = lv;
+        return u;
+    }
+    if (!tie_mode) return -1;
+    *lab = u < v ? lv : lu;
+    return u < v ? u : v;
+}
+
+__device__ __forceinline__ bool endpoints_ok(int32_t u, int32_t v, int32_t n, uint32_t *status) {
     if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(n) || static_cast<uint32_t>(v) >= static_cast<uint32_t>(n)) {
         raise_status(status, BGV_DEV_BADEDGE);
-        return;
+        return false;
     }
-    if (u == v) return;
-    const uint2 su = state[u], sv = state[v];  // (degree, label)
-    if (su.x > D || sv.x > D) return;
-    if (su.y == sv.y) return;
-    int32_t w;
-    uint32_t lab;
-    if (su.x > sv.x) {
-        w = v; lab = su.y;
-    } else if (sv.x > su.x) {
-        w = u; lab = sv.y;
-    } else if (tie_mode) {
-        w = u < v ? u : v;
-        lab = u < v ? sv.y : su.y;
-    } else {
-        return;
-    }
+    return u != v;
+}
+
+__device__ __forceinline__ void offer(unsigned long long *best, int32_t w, uint32_t e, uint32_t lab) {
     const unsigned long long cand = (static_cast<unsigned long long>(e) << 32) | lab;
     // The slot only decreases, so a stale read can only be larger than the
     // current value: skipping when cand is not below it is always safe.
     if (cand < best[w]) atomicMin(&best[w], cand);
+}
+
+__device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, int32_t n, const uint2 *state,
+                                             unsigned long long *best, uint32_t D, int tie_mode,
+                                             uint32_t *status) {
+    if (!endpoints_ok(u, v, n, status)) return;
+    const uint2 su = state[u], sv = state[v];  // (degree, label)
+    uint32_t lab;
+    const int32_t w = edge_rule(u, v, su.x, su.y, sv.x, sv.y, D, tie_mode, &lab);
+    if (w >= 0) offer(best, w, e, lab);
+}
+
+// Batched form: both endpoints belong to one graph, so the threshold
+// carried by u is the graph's.
+__device__ __forceinline__ void propose_edge_b(int32_t u, int32_t v, uint32_t e, int32_t n, const uint4 *state,
+                                               unsigned long long *best, int tie_mode, uint32_t *status) {
+    if (!endpoints_ok(u, v, n, status)) return;
+    const uint4 su = state[u], sv = state[v];  // (degree, label, threshold, 0)
+    uint32_t lab;
+    const int32_t w = edge_rule(u, v, su.x, su.y, sv.x, sv.y, su.z, tie_mode, &lab);
+    if (w >= 0) offer(best, w, e, lab);
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_init_b(const uint32_t *__restrict__ deg_est, int32_t n,
+                                                          const int32_t *__restrict__ node_graph,
+                                                          const uint32_t *__restrict__ D0, uint4 *__restrict__ state,
+                                                          unsigned long long *__restrict__ best) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        state[v] = make_uint4(deg_est[v], uint32_t(v), D0[node_graph[v]], 0u);
+        best[v] = kNone;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_propose_b(const int32_t *__restrict__ edges, int64_t m, int32_t n,
+                                                             const uint4 *__restrict__ state,
+                                                             unsigned long long *best, int tie_mode,
+                                                             uint32_t *status) {
+    const int4 *e2 = reinterpret_cast<const int4 *>(edges);
+    const int64_t pairs = m >> 1;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
+        const int4 e = __ldcs(e2 + p);
+        propose_edge_b(e.x, e.y, uint32_t(2 * p), n, state, best, tie_mode, status);
+        propose_edge_b(e.z, e.w, uint32_t(2 * p + 1), n, state, best, tie_mode, status);
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        propose_edge_b(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, state, best, tie_mode, status);
+}
+
+// Applies the winning proposals and moves every node's threshold to the
+// next round's (times growth, saturating at 2^32 - 1).
+__global__ void __launch_bounds__(kThreads) k_comm_apply_b(int32_t n, uint4 *__restrict__ state,
+                                                           unsigned long long *__restrict__ best, uint32_t growth) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long b = best[v];
+        uint4 s = state[v];
+        if (b != kNone) {
+            s.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
+            if (s.x != 0xFFFFFFFFu) s.x += 1;
+            best[v] = kNone;
+        }
+        const unsigned long long D = static_cast<unsigned long long>(s.z) * growth;
+        s.z = D > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(D);
+        state[v] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_comm_out_b(int32_t n, const uint4 *__restrict__ state,
+                                                         int32_t *__restrict__ labels, uint32_t *__restrict__ deg_out) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint4 s = state[v];
+        labels[v] = int32_t(s.y);
+        if (deg_out) deg_out[v] = s.x;
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_comm_propose(const int32_t *__restrict__ edges, int64_t m, int32_t n,
@@ -98,16 +186,34 @@ __global__ void __launch_bounds__(kThreads) k_comm_out(int32_t n, const uint2 *_
 }
 }  // namespace
 
-void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s) {
+void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched) {
     (void)m;
-    s.state = c.take<uint2>(size_t(n));
+    s.state = batched ? nullptr : c.take<uint2>(size_t(n));
+    s.bstate = batched ? c.take<uint4>(size_t(n)) : nullptr;
     s.best = c.take<unsigned long long>(size_t(n));
 }
 
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
-                    const CommScratch &s, uint32_t *status, cudaStream_t st) {
+                    const CommScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch) {
     const int gn = grid_for(n, kThreads, 152 * 8);
+    if (batch) {
+        const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
+        note_launch(), k_comm_init_b<<<gn, kThreads, 0, st>>>(deg_est, n, batch->node_graph, batch->D0, s.bstate,
+                                                              s.best);
+        BGV_TRY(launch_status());
+        for (int32_t p = 0; p < passes; ++p) {
+            if (m > 0) {
+                note_launch(), k_comm_propose_b<<<ge, kThreads, 0, st>>>(edges, m, n, s.bstate, s.best, tie_mode,
+                                                                         status);
+                BGV_TRY(launch_status());
+            }
+            note_launch(), k_comm_apply_b<<<gn, kThreads, 0, st>>>(n, s.bstate, s.best, growth);
+            BGV_TRY(launch_status());
+        }
+        note_launch(), k_comm_out_b<<<gn, kThreads, 0, st>>>(n, s.bstate, labels, deg_out);
+        return launch_status();
+    }
     note_launch(), k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
     BGV_TRY(launch_status());
     unsigned long long D = threshold;

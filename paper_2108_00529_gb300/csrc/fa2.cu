@@ -103,21 +103,62 @@ __global__ void __launch_bounds__(kThreads) k_frame(const float2 *__restrict__ p
     *ticket = 0u;
 }
 
+// Batched form: one block per graph; graph g owns bodies [koff[g], koff[g+1]).
+__global__ void __launch_bounds__(kThreads) k_frame_seg(const float2 *__restrict__ pos,
+                                                        const int64_t *__restrict__ koff, float4 *__restrict__ frames,
+                                                        int32_t *__restrict__ bgraph) {
+    const int g = blockIdx.x;
+    const int64_t a = koff[g], b = koff[g + 1];
+    float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const float2 p = pos[i];
+        lx = fminf(lx, p.x); ly = fminf(ly, p.y);
+        hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y);
+        bgraph[i] = g;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xFFFFFFFFu, lx, d));
+        ly = fminf(ly, __shfl_xor_sync(0xFFFFFFFFu, ly, d));
+        hx = fmaxf(hx, __shfl_xor_sync(0xFFFFFFFFu, hx, d));
+        hy = fmaxf(hy, __shfl_xor_sync(0xFFFFFFFFu, hy, d));
+    }
+    __shared__ float4 wpart[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = make_float4(lx, ly, hx, hy);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    float4 r = wpart[0];
+    for (int w = 1; w < kThreads / 32; ++w) {
+        r.x = fminf(r.x, wpart[w].x); r.y = fminf(r.y, wpart[w].y);
+        r.z = fmaxf(r.z, wpart[w].z); r.w = fmaxf(r.w, wpart[w].w);
+    }
+    const float ex = __fsub_rn(r.z, r.x), ey = __fsub_rn(r.w, r.y);
+    const float ext = ex > ey ? ex : ey;
+    float side = __fmul_rn(ext, 1.00000095367431640625f);  // 1 + 2^-20
+    if (!(ext > 0.0f)) side = 1.0f;
+    frames[g] = make_float4(r.x, r.y, side, 0.0f);
+}
+
 // ------------------------------------------------------------------ keys
+// Morton key of the body's fixed-point position in its graph's frame; in the
+// batched form the graph id sits above the 2L Morton bits, so each graph's
+// bodies stay together and form their own subtree.
 __global__ void __launch_bounds__(kThreads) k_keys(const float2 *__restrict__ pos, int64_t K,
-                                                   const float4 *__restrict__ frame, int L,
+                                                   const float4 *__restrict__ frames,
+                                                   const int32_t *__restrict__ bgraph, int L,
                                                    unsigned long long *__restrict__ keys,
                                                    uint32_t *__restrict__ vals, uint2 *__restrict__ U) {
-    const float4 fr = *frame;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const int g = bgraph ? bgraph[i] : 0;
+        const float4 fr = frames[g];
         const float2 p = pos[i];
         const float ux = __fdiv_rn(__fsub_rn(p.x, fr.x), fr.z);
         const float uy = __fdiv_rn(__fsub_rn(p.y, fr.y), fr.z);
         const uint32_t Ux = __float2uint_rz(__fmul_rn(ux, 4294967296.0f));
         const uint32_t Uy = __float2uint_rz(__fmul_rn(uy, 4294967296.0f));
         const uint32_t qx = Ux >> (32 - L), qy = Uy >> (32 - L);
-        keys[i] = (spread_bits(qx) << 1) | spread_bits(qy);
+        keys[i] = (static_cast<unsigned long long>(g) << (2 * L)) | (spread_bits(qx) << 1) | spread_bits(qy);
         vals[i] = uint32_t(i);
         U[i] = make_uint2(Ux, Uy);
     }
@@ -154,13 +195,13 @@ __device__ __forceinline__ int key_delta(const unsigned long long *__restrict__ 
 }
 
 __global__ void __launch_bounds__(kThreads) k_radix_tree(const unsigned long long *__restrict__ keys, int64_t K,
-                                                         int L, int32_t *__restrict__ left,
+                                                         int L, int gbits, int32_t *__restrict__ left,
                                                          int32_t *__restrict__ right, int32_t *__restrict__ parent,
                                                          int2 *__restrict__ range, int8_t *__restrict__ level,
                                                          int32_t *__restrict__ root) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= K - 1) return;
-    const int kb = 2 * L;
+    const int kb = 2 * L + gbits;
     const unsigned long long ki = __ldg(&keys[i]);
     const int d = key_delta(keys, K, kb, i, ki, i + 1) > key_delta(keys, K, kb, i, ki, i - 1) ? 1 : -1;
     const int dmin = key_delta(keys, K, kb, i, ki, i - d);
@@ -190,7 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_tree(const unsigned long lon
         *root = 0;
     }
     range[i] = make_int2(int32_t(first), int32_t(last));
-    level[i] = static_cast<int8_t>(dnode >= kb ? L : (dnode >> 1));
+    // 2-bit quadtree level below the graph bits; -1 above a graph's root
+    level[i] = static_cast<int8_t>(dnode >= kb ? L : (dnode < gbits ? -1 : ((dnode - gbits) >> 1)));
 }
 
 // Exact moment prefix sums over the Morton order: P[s] = sum over bodies
@@ -328,7 +370,8 @@ __global__ void __launch_bounds__(kThreads) k_mom_down(const uint2 *__restrict__
 // from the exact moments, mass, and the squared side used by the opening
 // test (+inf for a leaf that is never accepted).  Cells are counted by their
 // first body for the pre-order layout.
-__global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_cap, const float4 *__restrict__ frame,
+__global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_cap, const float4 *__restrict__ frames,
+                                                    const int32_t *__restrict__ bgraph,
                                                     const int32_t *__restrict__ parent,
                                                     const int2 *__restrict__ range, const int8_t *__restrict__ level,
                                                     const unsigned long long *__restrict__ PM,
@@ -353,7 +396,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_c
             // bodies between its parent's level and L; the deepest of them,
             // at level L - 1, takes the opening test for the whole chain.
             const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
-            const float4 fr = *frame;
+            // positions of graph g in Morton order are its index range too
+            const float4 fr = frames[bgraph ? bgraph[rg.x] : 0];
             const Mom hi = mom_load(PM, PX, PY, rg.y + 1), lo = mom_load(PM, PX, PY, rg.x);
             const unsigned long long M = hi.M - lo.M;
             const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
@@ -428,7 +472,7 @@ constexpr int kBodiesPerLane = 1;
 
 struct Walker {
     float xi, yi, kmi;
-    uint32_t self, resume;
+    uint32_t self, resume, end;
     float fx, fy;
     unsigned inter;
 };
@@ -452,10 +496,13 @@ __device__ __forceinline__ void walker_step(Walker &b, uint32_t cur, float4 e, u
             b.resume = sk;
         }
     }
+    if (b.resume >= b.end) b.resume = 0xFFFFFFFFu;  // left its graph's subtree: done
 }
 
 __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
                                                       const uint32_t *__restrict__ T,
+                                                      const int64_t *__restrict__ koff,
+                                                      const int32_t *__restrict__ bgraph,
                                                       const float4 *__restrict__ body, int64_t K, float kr,
                                                       float theta2, float2 *__restrict__ Frep,
                                                       unsigned long long *inter_step,
@@ -475,7 +522,16 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
         w[q].yi = bi.y;
         w[q].kmi = kr * bi.z;
         w[q].self = active ? uint32_t(s + T[s + 1]) : 0xFFFFFFFFu;
-        w[q].resume = active ? 0u : 0xFFFFFFFFu;
+        // the body's own graph: its subtree spans [start, end) in pre-order
+        uint32_t start = 0, end = total;
+        if (active && bgraph) {
+            const int g = bgraph[s];
+            const int64_t a = koff[g], b = koff[g + 1];
+            start = uint32_t(a + T[a]);
+            end = uint32_t(b + T[b]);
+        }
+        w[q].end = end;
+        w[q].resume = active ? start : 0xFFFFFFFFu;
         w[q].fx = 0.0f;
         w[q].fy = 0.0f;
         w[q].inter = 0;
@@ -691,7 +747,7 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
                                                    float2 *__restrict__ F, const float2 *__restrict__ Fprev,
                                                    float2 *__restrict__ Fr_out, float2 *__restrict__ Fa_out,
                                                    float2 *__restrict__ Fg_out, double2 *part, double *speed,
-                                                   float tau, WsHeader *hdr) {
+                                                   float tau, WsHeader *hdr, float2 *__restrict__ rowst) {
     Comp S{0.0, 0.0}, T{0.0, 0.0};
     const int lane = threadIdx.x & 31;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -775,11 +831,16 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
             F[i] = make_float2(fx, fy);
             const float sx = fx - fp.x, sy = fy - fp.y, tx = fx + fp.x, ty = fy + fp.y;
             // per-node products in FP32; the sums over nodes are FP64
-            S.s += double(m * sqrtf(sx * sx + sy * sy));
-            T.s += double(0.5f * m * sqrtf(tx * tx + ty * ty));
+            const float msw = m * sqrtf(sx * sx + sy * sy), mtr = 0.5f * m * sqrtf(tx * tx + ty * ty);
+            if (rowst) {
+                rowst[i] = make_float2(msw, mtr);  // batched: summed per graph
+            } else {
+                S.s += double(msw);
+                T.s += double(mtr);
+            }
         }
     }
-    if (mode == 0) return;
+    if (mode == 0 || rowst) return;
     __shared__ bool last;
     block_sum_plain(S.s, T.s);
     if (threadIdx.x == 0) {
@@ -815,12 +876,42 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
     hdr->node_ticket = 0u;
 }
 
+// Batched form: one block per graph sums its rows' swing and traction (FP64,
+// compensated, fixed order) and updates that graph's speed.
+__global__ void __launch_bounds__(kThreads) k_speed_seg(const float2 *__restrict__ rowst,
+                                                        const int64_t *__restrict__ koff, double *speed, float tau,
+                                                        WsHeader *hdr) {
+    const int g = blockIdx.x;
+    const int64_t a = koff[g], b = koff[g + 1];
+    Comp S{0.0, 0.0}, T{0.0, 0.0};
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const float2 v = rowst[i];
+        S = comp_add(S, double(v.x));
+        T = comp_add(T, double(v.y));
+    }
+    block_merge(S, T);
+    if (threadIdx.x != 0) return;
+    const double Ssum = S.s + S.c, Tsum = T.s + T.c;
+    double sp = speed[g];
+    if (Ssum > 0.0) {
+        const double target = double(tau) * Tsum / Ssum;
+        const double rise = target - sp, cap = 0.5 * sp;
+        sp += rise < cap ? rise : cap;
+    }
+    speed[g] = sp;
+    if (g == 0) {
+        hdr->S = Ssum;
+        hdr->T = Tsum;
+        hdr->steps_total += 1;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_update(int64_t K, const float2 *__restrict__ F, float2 *__restrict__ Fprev,
                                                      float2 *__restrict__ pos, const double *__restrict__ speed,
-                                                     float ks, float ksmax) {
-    const float sp = float(*speed);
+                                                     const int32_t *__restrict__ bgraph, float ks, float ksmax) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const float sp = float(speed[bgraph ? bgraph[i] : 0]);
         const float2 f = F[i], fp = Fprev[i];
         const float sx = f.x - fp.x, sy = f.y - fp.y;
         const float swing = sqrtf(sx * sx + sy * sy);
@@ -858,12 +949,41 @@ __global__ void __launch_bounds__(kThreads) k_init(int64_t K, unsigned long long
 }
 
 __global__ void k_set_speed(double *speed) { *speed = 1.0; }
+
+// Batched form: graph g starts exactly as it would alone (local index, its
+// own square of side 2 sqrt(K_g)) with speed 1.
+__global__ void __launch_bounds__(kThreads) k_init_seg(const int64_t *__restrict__ koff, unsigned long long seed,
+                                                       float2 *pos, float2 *Fprev, double *speed) {
+    const int g = blockIdx.x;
+    const int64_t a = koff[g], b = koff[g + 1];
+    const float R = sqrtf(float(b - a));
+    const float R2 = __fmul_rn(R, 2.0f);
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const int64_t local = i - a;
+        float c[2];
+#pragma unroll
+        for (int axis = 0; axis < 2; ++axis) {
+            unsigned long long z = seed + 2ull * static_cast<unsigned long long>(local) + unsigned(axis);
+            z += 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            const float U = __fmul_rn(__uint2float_rn(uint32_t(z >> 40)), 5.9604644775390625e-08f);  // 2^-24
+            c[axis] = __fsub_rn(__fmul_rn(U, R2), R);
+        }
+        pos[i] = make_float2(c[0], c[1]);
+        Fprev[i] = make_float2(0.0f, 0.0f);
+    }
+    if (threadIdx.x == 0) speed[g] = 1.0;
+}
 }  // namespace
 
 // ------------------------------------------------------------- scratch
 struct Fa2Scratch {
-    float4 *frame;
+    float4 *frame;         // frames: one per graph
     float4 *frame_part;
+    int32_t *bgraph;       // batched form: graph of each body
+    float2 *rowst;         // batched form: per-row swing, traction
     SortBuffers sort;
     uint2 *U;
     float4 *body;
@@ -887,11 +1007,14 @@ struct Fa2Scratch {
     double2 *part;  // two per block: (S, comp), (T, comp)
 };
 
-static void carve_fa2(Carver &c, int64_t K, int64_t nnz, Fa2Scratch &s) {
+static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
     const size_t k = size_t(K > 0 ? K : 1);
     const size_t chunks = size_t((nnz > 0 ? nnz : 1) + kChunk - 1) / kChunk;
-    s.frame = c.take<float4>(1);
+    const bool batched = G > 1;
+    s.frame = c.take<float4>(size_t(G > 1 ? G : 1));
     s.frame_part = c.take<float4>(kFrameBlocks);
+    s.bgraph = batched ? c.take<int32_t>(k) : nullptr;
+    s.rowst = batched ? c.take<float2>(k) : nullptr;
     carve_sort(c, int64_t(k), true, s.sort);
     s.U = c.take<uint2>(k);
     s.body = c.take<float4>(k);
@@ -925,10 +1048,10 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, Fa2Scratch &s) {
     s.part = c.take<double2>(2 * kNodeBlocks);
 }
 
-size_t fa2_scratch_bytes(int64_t K, int64_t nnz) {
+size_t fa2_scratch_bytes(int64_t K, int64_t nnz, int32_t G) {
     Carver c(nullptr, 0);
     Fa2Scratch s;
-    carve_fa2(c, K, nnz, s);
+    carve_fa2(c, K, nnz, G, s);
     return c.used();
 }
 
@@ -942,11 +1065,17 @@ int fa2_check_params(const bgv_fa2_params *p) {
     return BGV_OK;
 }
 
-int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st) {
+int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, double *speed, cudaStream_t st,
+                 int32_t G, const int64_t *koff) {
+    if (G > 1) {
+        note_launch(), k_init_seg<<<G, kThreads, 0, st>>>(koff, p.seed, reinterpret_cast<float2 *>(pos),
+                                                          reinterpret_cast<float2 *>(Fprev), speed);
+        return launch_status();
+    }
     if (K > 0) {
         const float R = __builtin_sqrtf(float(K));
-        note_launch(), k_init<<<grid_for(K, kThreads, 152 * 8), kThreads, 0, st>>>(K, p.seed, R, reinterpret_cast<float2 *>(pos),
-                                                                   reinterpret_cast<float2 *>(Fprev));
+        note_launch(), k_init<<<grid_for(K, kThreads, 152 * 8), kThreads, 0, st>>>(
+            K, p.seed, R, reinterpret_cast<float2 *>(pos), reinterpret_cast<float2 *>(Fprev));
         BGV_TRY(launch_status());
     }
     note_launch(), k_set_speed<<<1, 1, 0, st>>>(speed);
@@ -956,15 +1085,18 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
-            bool build_plan) {
+            bool build_plan, int32_t G, const int64_t *koff) {
     if (K <= 0) return BGV_OK;
+    const bool batched = G > 1;
+    if (!fa2_batch_fits(G, p.max_depth)) return BGV_EINVAL;
     Carver c(scratch, 0);
     Fa2Scratch s;
-    carve_fa2(c, K, nnz, s);
+    carve_fa2(c, K, nnz, G, s);
     float2 *pos = reinterpret_cast<float2 *>(pos_f);
     float2 *F = reinterpret_cast<float2 *>(F_f);
     float2 *Fprev = reinterpret_cast<float2 *>(Fprev_f);
     const int L = p.max_depth;
+    const int gbits = batched ? bits_for(G) : 0;
     auto mark = [&](int i) -> int {
         if (marks && cudaEventRecord(marks[i], st) != cudaSuccess) return BGV_ECUDA;
         return BGV_OK;
@@ -974,14 +1106,18 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     BGV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(hdr) + offsetof(WsHeader, interactions), 0,
                              offsetof(WsHeader, reserved) - offsetof(WsHeader, interactions), st));
     BGV_TRY(mark(0));
-    note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
+    if (batched)
+        note_launch(), k_frame_seg<<<G, kThreads, 0, st>>>(pos, koff, s.frame, s.bgraph);
+    else
+        note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
     const int gk = grid_for(K, kThreads, 152 * 16);
-    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, L, s.sort.keys[0], s.sort.vals[0], s.U);
+    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
+                                                   s.U);
     BGV_TRY(launch_status());
     BGV_TRY(mark(1));
     int res = 0;
-    BGV_TRY(radix_sort(s.sort, K, nullptr, 2 * L, st, &res, &hdr->status));
+    BGV_TRY(radix_sort(s.sort, K, nullptr, 2 * L + gbits, st, &res, &hdr->status));
     BGV_TRY(mark(2));
     note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass);
     BGV_TRY(launch_status());
@@ -990,8 +1126,8 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         const unsigned gi = unsigned((K - 1 + kThreads - 1) / kThreads);
         const unsigned tiles = unsigned((K + kMomTile - 1) / kMomTile);
-        note_launch(), k_radix_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, s.left, s.right, s.parent,
-                                                             s.range, s.level, s.root);
+        note_launch(), k_radix_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, s.left, s.right,
+                                                             s.parent, s.range, s.level, s.root);
         BGV_TRY(launch_status());
         note_launch(), k_mom_reduce<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY);
         note_launch(), k_mom_tiles<<<1, kThreads, 0, st>>>(s.TM, s.TX, s.TY, tiles);
@@ -999,8 +1135,8 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         BGV_TRY(launch_status());
         BGV_TRY(mark(4));
         BGV_CUDA(cudaMemsetAsync(s.start_count, 0, sizeof(uint32_t) * size_t(K), st));
-        note_launch(), k_cells<<<gi, kThreads, 0, st>>>(K, L, p.leaf_cap, s.frame, s.parent, s.range, s.level, s.PM,
-                                                        s.PX, s.PY, s.cell, s.topflag, s.start_count,
+        note_launch(), k_cells<<<gi, kThreads, 0, st>>>(K, L, p.leaf_cap, s.frame, s.bgraph, s.parent, s.range,
+                                                        s.level, s.PM, s.PX, s.PY, s.cell, s.topflag, s.start_count,
                                                         &hdr->tree_nodes);
         BGV_TRY(launch_status());
         BGV_TRY(scan_exclusive(s.start_count, s.T, K, nullptr, nullptr, true, s.scan_tmp, st));
@@ -1011,8 +1147,9 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         const float theta2 = p.theta * p.theta;
         const int64_t rwarps = (K + 32 * kBodiesPerLane - 1) / (32 * kBodiesPerLane);
         const unsigned gr = unsigned((rwarps * 32 + kThreads - 1) / kThreads);
-        note_launch(), k_repulse<<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, s.body, K, p.kr, theta2, s.Frep,
-                                                          &hdr->interactions, &hdr->interactions_total);
+        note_launch(), k_repulse<<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, koff, s.bgraph, s.body, K, p.kr,
+                                                          theta2, s.Frep, &hdr->interactions,
+                                                          &hdr->interactions_total);
         BGV_TRY(launch_status());
     } else {
         BGV_CUDA(cudaMemsetAsync(s.Frep, 0, sizeof(float2), st));
@@ -1027,19 +1164,22 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
             BGV_TRY(launch_status());
         }
         const int64_t nchunks = (nnz + kChunk - 1) / kChunk;
-        note_launch(), k_attract<<<grid_for(nchunks, kThreads, (nchunks + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-            K, nnz, csr_off, s.chunk_row, csr_adj, csr_w, pos, s.full, s.head, s.tail);
+        note_launch(), k_attract<<<grid_for(nchunks, kThreads, (nchunks + kThreads - 1) / kThreads), kThreads, 0,
+                                   st>>>(K, nnz, csr_off, s.chunk_row, csr_adj, csr_w, pos, s.full, s.head, s.tail);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(mode, K, csr_off, s.full, s.head, s.tail, mass, pos,
-                                                            s.Frep, p.kg, p.strong_gravity, F, Fprev,
-                                                            reinterpret_cast<float2 *>(Fr),
-                                                            reinterpret_cast<float2 *>(Fa),
-                                                            reinterpret_cast<float2 *>(Fg), s.part, speed, p.tau, hdr);
+    note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(
+        mode, K, csr_off, s.full, s.head, s.tail, mass, pos, s.Frep, p.kg, p.strong_gravity, F, Fprev,
+        reinterpret_cast<float2 *>(Fr), reinterpret_cast<float2 *>(Fa), reinterpret_cast<float2 *>(Fg), s.part, speed,
+        p.tau, hdr, (batched && mode == 1) ? s.rowst : nullptr);
     BGV_TRY(launch_status());
+    if (batched && mode == 1) {
+        note_launch(), k_speed_seg<<<G, kThreads, 0, st>>>(s.rowst, koff, speed, p.tau, hdr);
+        BGV_TRY(launch_status());
+    }
     BGV_TRY(mark(7));
     if (mode == 1) {
-        note_launch(), k_update<<<gk, kThreads, 0, st>>>(K, F, Fprev, pos, speed, p.ks, p.ksmax);
+        note_launch(), k_update<<<gk, kThreads, 0, st>>>(K, F, Fprev, pos, speed, s.bgraph, p.ks, p.ksmax);
         BGV_TRY(launch_status());
     }
     BGV_TRY(mark(8));

@@ -63,26 +63,46 @@ __global__ void __launch_bounds__(kThreads) k_degree_count(const int32_t *__rest
     }
 }
 
+// Batched form: node v of graph g = node_graph[v] hashes its local id
+// v - node_off[g] into graph g's own rows x width matrix.
+__device__ __forceinline__ uint32_t *sketch_of(uint32_t *sketch, const HashFamily &h, int64_t v,
+                                               const int32_t *node_graph, const int32_t *node_off, uint32_t *x) {
+    if (!node_graph) {
+        *x = uint32_t(v);
+        return sketch;
+    }
+    const int32_t g = node_graph[v];
+    *x = uint32_t(v - node_off[g]);
+    return sketch + size_t(g) * size_t(h.rows) * h.width;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sketch_fill(const uint32_t *__restrict__ deg, int32_t n,
                                                           const __grid_constant__ HashFamily h,
-                                                          uint32_t *__restrict__ sketch) {
+                                                          uint32_t *__restrict__ sketch,
+                                                          const int32_t *__restrict__ node_graph,
+                                                          const int32_t *__restrict__ node_off) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint32_t d = deg[v];
         if (d == 0) continue;
-        for (int i = 0; i < h.rows; ++i)
-            atomicAdd(&sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], uint32_t(v), h.width)], d);
+        uint32_t x;
+        uint32_t *M = sketch_of(sketch, h, v, node_graph, node_off, &x);
+        for (int i = 0; i < h.rows; ++i) atomicAdd(&M[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], x, h.width)], d);
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_sketch_query(const uint32_t *__restrict__ sketch, int32_t n,
                                                            const __grid_constant__ HashFamily h,
-                                                           uint32_t *__restrict__ deg_est) {
+                                                           uint32_t *__restrict__ deg_est,
+                                                           const int32_t *__restrict__ node_graph,
+                                                           const int32_t *__restrict__ node_off) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t x;
+        const uint32_t *M = sketch_of(const_cast<uint32_t *>(sketch), h, v, node_graph, node_off, &x);
         uint32_t best = 0xFFFFFFFFu;
         for (int i = 0; i < h.rows; ++i) {
-            uint32_t c = sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], uint32_t(v), h.width)];
+            uint32_t c = M[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], x, h.width)];
             best = c < best ? c : best;
         }
         deg_est[v] = best;
@@ -96,16 +116,21 @@ void carve_sketch(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, 
 }
 
 int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, uint32_t *sketch,
-               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st) {
+               uint32_t *deg_est, const SketchScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch) {
+    const int32_t *node_graph = batch ? batch->node_graph : nullptr;
+    const int32_t *node_off = batch ? batch->node_off : nullptr;
+    const size_t mats = batch ? size_t(batch->G) : 1;
     BGV_CUDA(cudaMemsetAsync(s.deg, 0, sizeof(uint32_t) * size_t(n), st));
-    BGV_CUDA(cudaMemsetAsync(sketch, 0, sizeof(uint32_t) * size_t(h.rows) * h.width, st));
+    BGV_CUDA(cudaMemsetAsync(sketch, 0, sizeof(uint32_t) * size_t(h.rows) * h.width * mats, st));
     if (m > 0) {
         note_launch(), k_degree_count<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch);
+    note_launch(), k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch, node_graph,
+                                                                                       node_off);
     BGV_TRY(launch_status());
-    note_launch(), k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est);
+    note_launch(), k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est, node_graph,
+                                                                                        node_off);
     return launch_status();
 }
 

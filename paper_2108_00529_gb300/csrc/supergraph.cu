@@ -137,21 +137,38 @@ __global__ void __launch_bounds__(kThreads) k_weights(const uint32_t *__restrict
     }
 }
 
+// Batched form: a label is a node id of its own graph g, hashed as its local
+// id into graph g's matrix.
+__device__ __forceinline__ size_t label_matrix(const HashFamily &h, int32_t l, const int32_t *node_graph,
+                                               const int32_t *node_off, uint32_t *x) {
+    if (!node_graph) {
+        *x = uint32_t(l);
+        return 0;
+    }
+    const int32_t g = node_graph[l];
+    *x = uint32_t(l - node_off[g]);
+    return size_t(g) * size_t(h.rows) * h.width;
+}
+
 __global__ void __launch_bounds__(kThreads) k_size_sketch(const int32_t *__restrict__ labels,
                                                           const uint32_t *__restrict__ deg_est,
                                                           const int32_t *__restrict__ node_map, int32_t n,
                                                           const __grid_constant__ HashFamily h,
                                                           unsigned long long *__restrict__ sketch,
                                                           unsigned long long *__restrict__ vol,
-                                                          uint32_t *__restrict__ count) {
+                                                          uint32_t *__restrict__ count,
+                                                          const int32_t *__restrict__ node_graph,
+                                                          const int32_t *__restrict__ node_off) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int32_t l = labels[v];
         if (static_cast<uint32_t>(l) >= static_cast<uint32_t>(n)) continue;
         const unsigned long long d = deg_est[v];
-        if (d)
-            for (int i = 0; i < h.rows; ++i)
-                atomicAdd(&sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], uint32_t(l), h.width)], d);
+        if (d) {
+            uint32_t x;
+            unsigned long long *M = sketch + label_matrix(h, l, node_graph, node_off, &x);
+            for (int i = 0; i < h.rows; ++i) atomicAdd(&M[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], x, h.width)], d);
+        }
         if (vol && d) atomicAdd(&vol[node_map[v]], d);
         if (count) atomicAdd(&count[node_map[v]], 1u);
     }
@@ -160,14 +177,18 @@ __global__ void __launch_bounds__(kThreads) k_size_sketch(const int32_t *__restr
 __global__ void __launch_bounds__(kThreads) k_mass(const int32_t *__restrict__ label_of, const int64_t *K_dev,
                                                    const __grid_constant__ HashFamily h,
                                                    const unsigned long long *__restrict__ sketch,
-                                                   uint32_t *__restrict__ mass, int32_t *__restrict__ comm_label) {
+                                                   uint32_t *__restrict__ mass, int32_t *__restrict__ comm_label,
+                                                   const int32_t *__restrict__ node_graph,
+                                                   const int32_t *__restrict__ node_off) {
     const int64_t K = *K_dev;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < K; k += stride) {
         const uint32_t l = uint32_t(label_of[k]);
+        uint32_t x;
+        const unsigned long long *M = sketch + label_matrix(h, int32_t(l), node_graph, node_off, &x);
         unsigned long long best = ~0ull;
         for (int i = 0; i < h.rows; ++i) {
-            const unsigned long long c = sketch[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], l, h.width)];
+            const unsigned long long c = M[size_t(i) * h.width + hash_eval(h.a[i], h.b[i], x, h.width)];
             best = c < best ? c : best;
         }
         const unsigned long long ms = best + 1;
@@ -262,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_csr_fill_dst(const unsigned long l
 }
 }  // namespace
 
-void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s) {
+void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s, int32_t G) {
     s.flags = c.take<uint32_t>(size_t(n) + 1);
     s.rank = c.take<uint32_t>(size_t(n) + 1);
     s.label_of = c.take<int32_t>(size_t(n));
@@ -271,7 +292,7 @@ void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, S
     s.dst_first = c.take<uint32_t>(size_t(n));
     s.dst_end = c.take<uint32_t>(size_t(n));
     s.m_cut = c.take<int64_t>(1);
-    s.sketch = c.take<unsigned long long>(size_t(rows) * size_t(width));
+    s.sketch = c.take<unsigned long long>(size_t(rows) * size_t(width) * size_t(G > 1 ? G : 1));
     s.heads = c.take<uint32_t>(size_t(m));
     s.segidx = c.take<uint32_t>(size_t(m) + 1);
     s.segstart = c.take<uint32_t>(size_t(m));
@@ -285,7 +306,10 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
                    const HashFamily &h, int32_t *node_map, int64_t *K_dev, int32_t *ssrc, int32_t *sdst,
                    uint32_t *sw, int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
                    uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
-                   const SuperScratch &s, uint32_t *status, cudaStream_t st) {
+                   const SuperScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch) {
+    const int32_t *node_graph = batch ? batch->node_graph : nullptr;
+    const int32_t *node_off = batch ? batch->node_off : nullptr;
+    const size_t mats = batch ? size_t(batch->G) : 1;
     const int gn = grid_for(n, kThreads, 152 * 8);
     const int gm = grid_for(m > 0 ? m : 1, kThreads, 152 * 8);
     const int shift = bits_for(n);  // supernode ids < K <= n fit in `shift` bits
@@ -321,13 +345,15 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
     BGV_TRY(launch_status());
 
     // 5. community sizes
-    BGV_CUDA(cudaMemsetAsync(s.sketch, 0, sizeof(unsigned long long) * size_t(h.rows) * h.width, st));
+    BGV_CUDA(cudaMemsetAsync(s.sketch, 0, sizeof(unsigned long long) * size_t(h.rows) * h.width * mats, st));
     if (vol) BGV_CUDA(cudaMemsetAsync(vol, 0, sizeof(uint64_t) * size_t(n), st));
     if (count) BGV_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t) * size_t(n), st));
     note_launch(), k_size_sketch<<<gn, kThreads, 0, st>>>(labels, deg_est, node_map, n, h, s.sketch,
-                                          reinterpret_cast<unsigned long long *>(vol), count);
+                                                          reinterpret_cast<unsigned long long *>(vol), count,
+                                                          node_graph, node_off);
     BGV_TRY(launch_status());
-    note_launch(), k_mass<<<gn, kThreads, 0, st>>>(s.label_of, K_dev, h, s.sketch, mass, comm_label);
+    note_launch(), k_mass<<<gn, kThreads, 0, st>>>(s.label_of, K_dev, h, s.sketch, mass, comm_label, node_graph,
+                                                   node_off);
     BGV_TRY(launch_status());
 
     // 6. symmetric CSR: the superedges in (src, dst) order and, from a stable

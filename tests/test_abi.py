@@ -82,3 +82,30 @@ def test_host_validation_rejects_bad_arguments(lib):
                           C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), fake_ws, 1 << 30,
                           None) == bgv.BGV_EINVAL
     assert bgv.bgv_strerror(bgv.BGV_ENOSPC) == "workspace too small"
+
+
+def test_batched_host_validation(lib):
+    # Offsets are checked on the host before any CUDA call.
+    import numpy as np
+    from paper_2108_00529_gb300 import bgv
+    L = bgv._lib
+    p = bgv.bgv_layout_default_params()
+    eo = np.array([0, 10, 25], np.int64)
+    no = np.array([0, 5, 9], np.int32)
+    assert bgv.bgv_layout_batched_ws_size(2, eo, no, p) > bgv.bgv_layout_ws_size(25, 9, p)
+    for bad_e, bad_n in [([1, 10, 25], [0, 5, 9]),      # offsets must start at 0
+                         ([0, 10, 25], [0, 5, 5]),      # empty graph
+                         ([0, 30, 25], [0, 5, 9])]:     # edge offsets decrease
+        assert bgv.bgv_layout_batched_ws_size(2, bad_e, bad_n, p) == 0
+        e, pe = bgv._host(bad_e, np.int64)
+        n, pn = bgv._host(bad_n, np.int32)
+        K = np.zeros(3, np.int64)
+        assert L.bgv_layout_batched(C.c_void_p(16), 2, pe, pn, C.byref(p), C.c_void_p(16), C.c_void_p(16), None,
+                                    K.ctypes.data, K.ctypes.data, C.c_void_p(256), 1 << 30, None) == bgv.BGV_EINVAL
+    fp = bgv.bgv_fa2_default_params()
+    ko, pk = bgv._host([0, 3, 3, 7], np.int64)  # graph 1 has no bodies
+    assert L.bgv_fa2_run_batched(3, pk, 0, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16),
+                                 C.byref(fp), 1, 0, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16),
+                                 C.c_void_p(256), 1 << 30, None) == bgv.BGV_EINVAL
+    # more graphs need more workspace (frames, speeds, per-body graph ids)
+    assert bgv.bgv_fa2_ws_size_batched(1, 1000, 10) <= bgv.bgv_fa2_ws_size_batched(100, 1000, 10)
