@@ -42,6 +42,10 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FLOPS_PER_INTERACTION = 12     # dx, dy, d2 (3), division, k*m*M (2), two FMAs (4)
+# DRAM bytes (read + write) of one k_repulse launch on the rmat20 supergraph,
+# from the ncu capture summarised in profiles/k_repulse_rmat20.md; valid only
+# while k_repulse is unchanged since that capture.
+REPULSE_TRAFFIC = {"rmat20": 51_629_312}
 
 WORKLOADS = {
     "rmat20": dict(desc="R-MAT scale 20 (1,048,576 node ids), 10,000,000 unique edges, a,b,c,d=.57,.19,.19,.05, "
@@ -307,7 +311,7 @@ def gpu_arm(args, dist: Dist):
     peak_tf = fp32_peak_tflops()
     roofline = {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(achieved_tf, 3),
                 "peak": round(peak_tf, 2), "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
-                "traffic": None, "interactions_per_launch": int(inter_per_launch),
+                "traffic": REPULSE_TRAFFIC.get(args.workload), "interactions_per_launch": int(inter_per_launch),
                 "launch_ms": round(rep_launch_ms, 4),
                 "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe unit counts, max clock)"}
 

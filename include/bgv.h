@@ -68,7 +68,7 @@ extern "C" {
 /* Bits of the device status word. */
 #define BGV_DEV_BADEDGE 1u     /* an edge endpoint outside [0, n) */
 #define BGV_DEV_BADLABEL 2u    /* a label outside [0, n) */
-#define BGV_DEV_STACK 4u       /* Barnes-Hut traversal stack exhausted */
+/* bit 4u is unused: the Barnes-Hut traversal keeps no stack */
 #define BGV_DEV_TIMEOUT 8u     /* a bounded device-side wait gave up */
 
 /* Library version, (major << 16) | minor. */

@@ -20,7 +20,7 @@ if not _LIB_PATH.exists():
 _lib = C.CDLL(str(_LIB_PATH))
 
 BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA, BGV_ELIMIT = 0, 1, 2, 3, 4, 5
-BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_STACK, BGV_DEV_TIMEOUT = 1, 2, 4, 8
+BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_TIMEOUT = 1, 2, 8
 
 P = C.c_void_p
 i32, i64, u32, u64, sz = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t

@@ -36,8 +36,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFrameBlocks = 304;      // 2 x 152 SMs
 constexpr int kNodeBlocks = 152 * 8;  // node-kernel grid (rows are grid-strided)
-constexpr int kStack = 96;             // >= 3 * (24 + 1) + 1
-constexpr int kNone = INT32_MIN;       // empty child slot
 
 typedef unsigned __int128 u128;
 
@@ -87,13 +85,31 @@ __global__ void __launch_bounds__(kThreads) k_frame(const float2 *__restrict__ p
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
+    // the last block reduces the block partials, all threads at once
+    // (min and max do not depend on the order)
     __threadfence();
-    float4 r = __ldcg(&part[0]);
-    for (unsigned b = 1; b < gridDim.x; ++b) {
+    float4 r = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
         const float4 q = __ldcg(&part[b]);
         r.x = fminf(r.x, q.x); r.y = fminf(r.y, q.y);
         r.z = fmaxf(r.z, q.z); r.w = fmaxf(r.w, q.w);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        r.x = fminf(r.x, __shfl_xor_sync(0xFFFFFFFFu, r.x, d));
+        r.y = fminf(r.y, __shfl_xor_sync(0xFFFFFFFFu, r.y, d));
+        r.z = fmaxf(r.z, __shfl_xor_sync(0xFFFFFFFFu, r.z, d));
+        r.w = fmaxf(r.w, __shfl_xor_sync(0xFFFFFFFFu, r.w, d));
+    }
+    __syncthreads();  // wpart is reused
+    if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    r = wpart[0];
+    for (int w = 1; w < kThreads / 32; ++w) {
+        r.x = fminf(r.x, wpart[w].x); r.y = fminf(r.y, wpart[w].y);
+        r.z = fmaxf(r.z, wpart[w].z); r.w = fmaxf(r.w, wpart[w].w);
     }
     const float ex = __fsub_rn(r.z, r.x), ey = __fsub_rn(r.w, r.y);
     const float ext = ex > ey ? ex : ey;
@@ -574,23 +590,37 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
 // k_node adds a row's pieces in chunk order, so the sum order is fixed.
 constexpr int kChunk = 8;
 
-// The row of each chunk's first entry, written once per CSR (the plan): the
-// thread of row r writes r into every chunk that starts inside the row; a
-// warp shares the writes of rows that cover many chunks.
+// The plan, written once per CSR:
+//   chunk_row[g]   row of chunk g's first entry (the thread of row r writes r
+//                  into every chunk that starts inside the row; a warp shares
+//                  the writes of rows that cover many chunks);
+//   chunk_meta[g]  byte k (1..7): row of entry k minus chunk_row[g]; byte 0:
+//                  kMetaHead (the first row began in an earlier chunk),
+//                  kMetaTail (the last row goes on into the next chunk),
+//                  kMetaWalk (a row gap above 255: the chunk walks the
+//                  offsets instead);
+//   long_rows      the rows spread over more than kLongRowChunks chunks.
+// With the rows of all 8 entries known up front, every load of a chunk is
+// issued at once; no dependent walk over the row offsets.
 constexpr int kLongRowChunks = 32;
+constexpr unsigned kMetaHead = 1u, kMetaTail = 2u, kMetaWalk = 4u;
 
 __global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
-                                                         int32_t *__restrict__ chunk_row) {
+                                                         int32_t *__restrict__ chunk_row, int32_t *__restrict__ long_rows,
+                                                         int32_t *long_count) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); base < K; base += stride) {
         const int64_t r = base + lane;
         int64_t g0 = 0, g1 = 0;
+        bool spread = false;
         if (r < K) {
             const int64_t b = off[r], e = off[r + 1] < nnz ? off[r + 1] : nnz;
             g0 = (b + kChunk - 1) / kChunk;
             g1 = (e + kChunk - 1) / kChunk;
+            spread = e > b && (e - 1) / kChunk - b / kChunk > kLongRowChunks;
         }
+        if (spread) long_rows[atomicAdd(long_count, 1)] = int32_t(r);
         const bool longrow = g1 - g0 > kLongRowChunks;
         if (!longrow)
             for (int64_t g = g0; g < g1; ++g) chunk_row[g] = int32_t(r);
@@ -604,8 +634,41 @@ __global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz,
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads) k_chunk_meta(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+                                                         const int32_t *__restrict__ chunk_row,
+                                                         unsigned long long *__restrict__ chunk_meta) {
+    const int64_t chunks = (nnz + kChunk - 1) / kChunk;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
+        const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
+        const int64_t r0 = chunk_row[g];
+        unsigned long long meta = off[r0] < e0 ? kMetaHead : 0u;
+        int64_t r = r0;
+        for (int64_t e = e0 + 1; e < e1; ++e) {
+            while (r + 1 < K && e >= off[r + 1]) ++r;
+            const int64_t d = r - r0;
+            if (d > 255) meta |= kMetaWalk;
+            meta |= static_cast<unsigned long long>(d > 255 ? 255 : d) << (8 * (e - e0));
+        }
+        if (off[r + 1] > e1) meta |= kMetaTail;
+        chunk_meta[g] = meta;
+    }
+}
+
+// A row segment of a chunk goes to head[g] if it continues a row from an
+// earlier chunk, to tail[g] if its row goes on past the chunk, else it is
+// the whole row.
+__device__ __forceinline__ void put_piece(bool first, bool last, unsigned flags, int64_t g, int64_t row, float ax,
+                                          float ay, float2 *full, float2 *head, float2 *tail) {
+    const float2 v = make_float2(ax, ay);
+    if (first && (flags & kMetaHead)) head[g] = v;
+    else if (last && (flags & kMetaTail)) tail[g] = v;
+    else full[row] = v;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ chunk_row,
+                                                      const unsigned long long *__restrict__ chunk_meta,
                                                       const int32_t *__restrict__ adj,
                                                       const uint32_t *__restrict__ w, const float2 *__restrict__ pos,
                                                       float2 *__restrict__ full, float2 *__restrict__ head,
@@ -616,9 +679,12 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
         const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
         const int n = int(e1 - e0);
+        const int64_t r0 = chunk_row[g];
+        const unsigned long long meta = chunk_meta[g];
+        const unsigned flags = unsigned(meta & 0xFFu);
         // All loads of the chunk first: 8 neighbour ids and weights (two
-        // 16-byte loads each when aligned), then the 8 position gathers, so
-        // they are in flight together.
+        // 16-byte loads each when aligned), then the 8 neighbour and 8 row
+        // position gathers, so they are in flight together.
         int32_t jj[kChunk];
         uint32_t ww[kChunk];
         if (vec && n == kChunk) {
@@ -641,7 +707,39 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
 #pragma unroll
         for (int k = 0; k < kChunk; ++k)
             pj[k] = static_cast<uint64_t>(jj[k]) < static_cast<uint64_t>(K) ? pos[jj[k]] : make_float2(0.f, 0.f);
-        int64_t r = chunk_row[g];
+        if (!(flags & kMetaWalk)) {
+            int32_t rk[kChunk];
+            float2 pr[kChunk];
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                rk[k] = int32_t(r0) + int32_t(k ? unsigned(meta >> (8 * k)) & 0xFFu : 0u);
+                pr[k] = k < n ? pos[rk[k]] : make_float2(0.f, 0.f);
+            }
+            float ax = 0.0f, ay = 0.0f;
+            bool first = true;
+            int32_t row = rk[0];
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                if (k < n) {
+                    if (rk[k] != row) {
+                        put_piece(first, false, flags, g, row, ax, ay, full, head, tail);
+                        first = false;
+                        row = rk[k];
+                        ax = 0.0f;
+                        ay = 0.0f;
+                    }
+                    if (static_cast<uint64_t>(jj[k]) < static_cast<uint64_t>(K)) {  // else an invalid CSR entry
+                        const float wt = __uint2float_rn(ww[k]);
+                        ax += wt * (pj[k].x - pr[k].x);
+                        ay += wt * (pj[k].y - pr[k].y);
+                    }
+                }
+            }
+            put_piece(first, true, flags, g, row, ax, ay, full, head, tail);
+            continue;
+        }
+        // Rows far apart (long runs of empty rows): walk the offsets.
+        int64_t r = r0;
         int64_t rs = off[r], re = off[r + 1];
         float2 pi = pos[r];
         float ax = 0.0f, ay = 0.0f;
@@ -667,6 +765,40 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
         if (rs >= e0 && re <= e1) full[r] = make_float2(ax, ay);
         else if (rs < e0) head[g] = make_float2(ax, ay);
         else tail[g] = make_float2(ax, ay);
+    }
+}
+
+// Rows spread over more than kLongRowChunks chunks, one warp each: the
+// lanes add strided subsets of the row's middle pieces in chunk order, then
+// a fixed butterfly, then the row's first piece.  k_node reads the result
+// from full[].
+__global__ void __launch_bounds__(kThreads) k_long_rows(const int32_t *__restrict__ off,
+                                                        const int32_t *__restrict__ long_rows,
+                                                        const int32_t *__restrict__ long_count,
+                                                        const float2 *__restrict__ head,
+                                                        const float2 *__restrict__ tail, float2 *__restrict__ full) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int64_t count = *long_count;
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < count; q += warps) {
+        const int32_t r = long_rows[q];
+        const int64_t a = off[r] / kChunk, z = (off[r + 1] - 1) / kChunk;
+        float px = 0.0f, py = 0.0f;
+#pragma unroll 4
+        for (int64_t g = a + 1 + lane; g <= z; g += 32) {
+            const float2 v = head[g];
+            px += v.x;
+            py += v.y;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            px += __shfl_xor_sync(0xFFFFFFFFu, px, d);
+            py += __shfl_xor_sync(0xFFFFFFFFu, py, d);
+        }
+        if (lane == 0) {
+            const float2 t = tail[a];
+            full[r] = make_float2(t.x + px, t.y + py);
+        }
     }
 }
 
@@ -770,9 +902,9 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
                 g2 = (e - 1) / kChunk;
             }
         }
-        const bool longrow = g2 - g1 > kLongRowChunks;
-        if (valid && g2 >= g1 && !longrow) {
-            if (g1 == g2) {
+        // rows over many chunks were summed by k_long_rows into full[]
+        if (valid && g2 >= g1) {
+            if (g1 == g2 || g2 - g1 > kLongRowChunks) {
                 const float2 v = full[i];
                 ax = v.x;
                 ay = v.y;
@@ -785,30 +917,6 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
                     ax += v.x;
                     ay += v.y;
                 }
-            }
-        }
-        // Rows spread over many chunks: the warp sums their pieces, each lane
-        // a strided subset, then a fixed butterfly; the order is fixed.
-        unsigned lm = __ballot_sync(0xFFFFFFFFu, longrow);
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int64_t a = __shfl_sync(0xFFFFFFFFu, g1, src), z = __shfl_sync(0xFFFFFFFFu, g2, src);
-            float px = 0.0f, py = 0.0f;
-            for (int64_t g = a + 1 + lane; g <= z; g += 32) {
-                const float2 v = head[g];
-                px += v.x;
-                py += v.y;
-            }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                px += __shfl_xor_sync(0xFFFFFFFFu, px, d);
-                py += __shfl_xor_sync(0xFFFFFFFFu, py, d);
-            }
-            if (lane == src) {
-                const float2 t = tail[a];
-                ax = t.x + px;
-                ay = t.y + py;
             }
         }
         if (!valid) continue;
@@ -1004,6 +1112,9 @@ struct Fa2Scratch {
     float2 *Frep;
     float2 *full, *head, *tail;
     int32_t *chunk_row;   // plan: row of each chunk's first entry
+    unsigned long long *chunk_meta;  // plan: rows of the chunk's entries, flags
+    int32_t *long_rows;   // plan: rows over more than kLongRowChunks chunks
+    int32_t *long_count;
     double2 *part;  // two per block: (S, comp), (T, comp)
 };
 
@@ -1045,6 +1156,9 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.head = c.take<float2>(chunks);
     s.tail = c.take<float2>(chunks);
     s.chunk_row = c.take<int32_t>(chunks);
+    s.chunk_meta = c.take<unsigned long long>(chunks);
+    s.long_rows = c.take<int32_t>(chunks / kLongRowChunks + 1);
+    s.long_count = c.take<int32_t>(1);
     s.part = c.take<double2>(2 * kNodeBlocks);
 }
 
@@ -1159,13 +1273,21 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     BGV_TRY(mark(6));
     if (nnz > 0) {
         if (build_plan) {
-            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, st>>>(K, nnz, csr_off,
-                                                                                             s.chunk_row);
+            BGV_CUDA(cudaMemsetAsync(s.long_count, 0, sizeof(int32_t), st));
+            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, st>>>(
+                K, nnz, csr_off, s.chunk_row, s.long_rows, s.long_count);
+            BGV_TRY(launch_status());
+            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0,
+                                          st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
             BGV_TRY(launch_status());
         }
         const int64_t nchunks = (nnz + kChunk - 1) / kChunk;
         note_launch(), k_attract<<<grid_for(nchunks, kThreads, (nchunks + kThreads - 1) / kThreads), kThreads, 0,
-                                   st>>>(K, nnz, csr_off, s.chunk_row, csr_adj, csr_w, pos, s.full, s.head, s.tail);
+                                   st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
+                                         s.head, s.tail);
+        BGV_TRY(launch_status());
+        note_launch(), k_long_rows<<<152 * 4, kThreads, 0, st>>>(csr_off, s.long_rows, s.long_count, s.head, s.tail,
+                                                                 s.full);
         BGV_TRY(launch_status());
     }
     note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(

@@ -192,8 +192,14 @@ inline int sort_items(int64_t cap) { return cap <= kSmallSort ? kSortItemsSmall 
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
 constexpr uint32_t kInvalidDigit = 0xFFFFu;
-constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kCountMask = (1ull << 62) - 1;
+// Look-back words: 2 flag bits, the pass number (1..8) in bits 40..47 and a
+// 40-bit count.  The words are cleared once per sort; a word written by an
+// earlier pass carries another pass number and reads as "not yet published".
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFlagMask = 3ull << 62;
+constexpr unsigned long long kCountMask = (1ull << 40) - 1;
+constexpr int kTagShift = 40;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookBack = 4;  // predecessors read per look-back round
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long long *__restrict__ keys, int64_t cap,
                                                              const int64_t *d_count, int passes,
@@ -235,7 +241,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
                                                                 const int64_t *d_count, int shift,
                                                                 const uint32_t *__restrict__ digit_base,
                                                                 unsigned int *tile_counter,
-                                                                unsigned long long *status, uint32_t *dev_status) {
+                                                                unsigned long long *status, uint32_t *dev_status,
+                                                                unsigned long long tag) {
     __shared__ uint32_t cnt[kSortWarps][kBins];
     __shared__ uint32_t tile_base[kBins];
     __shared__ unsigned int tile_sh;
@@ -283,27 +290,42 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
         volatile unsigned long long *st = status;
         unsigned long long excl = 0;
         if (tile == 0) {
-            st[d] = kFlagIncl | total;
+            st[d] = kFlagIncl | tag | total;
         } else {
-            st[tile * kBins + d] = kFlagAgg | total;
+            st[tile * kBins + d] = kFlagAgg | tag | total;
+            // Look back kLookBack predecessors per round (independent loads in
+            // flight together): add aggregates up to the nearest inclusive
+            // prefix; stop at a tile that has published nothing yet and
+            // wait for it.
             int64_t j = tile - 1;
             int spins = 0;
-            while (j >= 0) {
-                const unsigned long long v = st[j * kBins + d];
-                const unsigned long long flag = v & ~kCountMask;
-                if (flag == 0) {
+            while (true) {
+                unsigned long long v[kLookBack];
+#pragma unroll
+                for (int q = 0; q < kLookBack; ++q) v[q] = j - q >= 0 ? st[(j - q) * kBins + d] : (kFlagIncl | tag);
+                int q = 0;
+                bool done = false;
+                for (; q < kLookBack; ++q) {
+                    const unsigned long long flag =
+                        (v[q] & ~(kFlagMask | kCountMask)) == tag ? (v[q] & kFlagMask) : 0ull;
+                    if (flag == 0) break;
+                    excl += v[q] & kCountMask;
+                    if (flag == kFlagIncl) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done) break;
+                j -= q;
+                if (q < kLookBack) {
                     if (++spins > kSpinLimit) {
                         raise_status(dev_status, BGV_DEV_TIMEOUT);
                         break;
                     }
                     __nanosleep(32);
-                    continue;
                 }
-                excl += v & kCountMask;
-                if (flag == kFlagIncl) break;
-                --j;
             }
-            st[tile * kBins + d] = kFlagIncl | (excl + total);
+            st[tile * kBins + d] = kFlagIncl | tag | (excl + total);
         }
         tile_base[d] = digit_base[d] + uint32_t(excl);
     }
@@ -349,23 +371,24 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
     BGV_TRY(launch_status());
     int cur = 0;
+    BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
     for (int p = 0; p < passes; ++p) {
-        BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
+        const unsigned long long tag = static_cast<unsigned long long>(p + 1) << kTagShift;
         const unsigned g = static_cast<unsigned>(tiles);
         unsigned long long *ki = b.keys[cur], *ko = b.keys[cur ^ 1];
         uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1], *base = b.counts + p * kBins;
         if (b.vals[0] && items == kSortItemsSmall)
             note_launch(), k_sort_onesweep<true, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
         else if (b.vals[0])
             note_launch(), k_sort_onesweep<true, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
         else if (items == kSortItemsSmall)
             note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
         else
             note_launch(), k_sort_onesweep<false, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status);
+                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
         BGV_TRY(launch_status());
         cur ^= 1;
     }

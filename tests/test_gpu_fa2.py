@@ -198,3 +198,25 @@ def test_layout_invariants_over_many_steps():
     spread = np.mean([np.linalg.norm(pos[memb == c] - cent[c], axis=1).mean() for c in range(5)])
     sep = np.mean([np.linalg.norm(cent[a] - cent[b]) for a in range(5) for b in range(a + 1, 5)])
     assert sep > 2 * spread
+
+
+def test_attraction_over_uneven_rows():
+    # Row shapes the attraction plan treats differently: empty rows in long
+    # runs (row gaps above 255 inside one 8-entry chunk), rows on and around
+    # the 8-entry chunk size, rows just under and over 33 chunks, and hubs
+    # spread over hundreds of chunks.
+    rng = np.random.default_rng(11)
+    lengths = [3, 0, 0, 5] + [0] * 300 + [2, 1] + [0] * 1000 + [4, 8, 9, 7, 1, 16, 17, 263, 264, 265, 272, 273,
+                                                              5000, 0, 12345, 1, 0, 0, 3]
+    lengths += list(rng.integers(0, 40, 3000)) + [0] * 500 + [6]
+    K = len(lengths)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    adj = rng.integers(0, K, off[-1]).astype(np.int32)
+    w = rng.integers(1, 5, off[-1]).astype(np.uint32)
+    pos = (rng.random((K, 2)) * 200 - 100).astype(np.float32)
+    mass = np.ones(K, np.uint32)
+    r = G.fa2_forces(pos, mass, off, adj, w, FA2Params())
+    assert r["status"] == 0
+    assert G.rel_err(r["Fa"], oracle.attraction(off, adj, w, pos)) <= TOL
+    empty = np.diff(off) == 0
+    assert np.all(r["Fa"][empty] == 0.0)
