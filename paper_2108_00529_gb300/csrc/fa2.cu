@@ -13,13 +13,16 @@
 //               parent's; FP32 centre of mass from the exact moments
 //   k_preorder  cells and bodies laid out in depth-first pre-order with skip
 //               indices (positions from a prefix count of cells per body)
-//   k_repulse   Barnes-Hut repulsion: one warp per 32 Morton-consecutive
-//               bodies walks the union of their traversals without a stack;
-//               every lane takes its own opening decisions, so each body's
-//               interaction set is exactly the one the definition gives
-//   k_attract   attraction over fixed 8-entry chunks of the CSR (balanced
-//               whatever the degrees), row pieces kept per chunk
-//   k_node      per node: attraction pieces in chunk order, gravity, total
+//   k_repulse   Barnes-Hut repulsion: one thread per body walks the
+//               pre-order array without a stack (accept -> skip past the
+//               subtree, open -> next element); every body takes its own
+//               opening decisions, so its interaction set is exactly the
+//               one the definition gives
+//   k_attract   attraction over fixed 256-entry ranges of the CSR, one warp
+//               per range (balanced whatever the degrees): segmented scan by
+//               row, row pieces kept per range; k_long_rows sums the rows
+//               spread over many ranges
+//   k_node      per node: attraction pieces in range order, gravity, total
 //               force, swing and traction (FP64, compensated); the last block
 //               merges the block partials and updates the global speed
 //   k_update    local speed, displacement, Fprev = F
@@ -465,56 +468,14 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int32_t 
 }
 
 // -------------------------------------------------------------- repulsion
-__device__ __forceinline__ void add_body(float xi, float yi, float kmi, float4 bj, float &fx, float &fy) {
-    const float dx = xi - bj.x, dy = yi - bj.y;
-    const float d2 = dx * dx + dy * dy;
-    if (d2 > 0.0f) {
-        const float f = __fdividef(kmi * bj.z, d2);
-        fx += f * dx;
-        fy += f * dy;
-    }
-}
-
-// Barnes-Hut traversal without a stack.  A warp serves 32 * kBodiesPerLane
-// Morton-consecutive bodies; each body keeps the pre-order index where its
-// own traversal resumes.  Each step the warp takes the smallest resume index
-// (one redux), loads that element once for all lanes, and only the bodies
-// waiting at it act: a body is summed directly (not self) and passed; a cell
-// holding the body is entered; any other cell is accepted (summed, resume
-// after its subtree) or entered, by the FP32 opening test of the definition.
-// Each body therefore sees exactly its own interaction set, in depth-first
-// order.
-constexpr int kBodiesPerLane = 1;
-
-struct Walker {
-    float xi, yi, kmi;
-    uint32_t self, resume, end;
-    float fx, fy;
-    unsigned inter;
-};
-
-__device__ __forceinline__ void walker_step(Walker &b, uint32_t cur, float4 e, uint32_t sk, float theta2) {
-    if (b.resume != cur) return;
-    b.resume = cur + 1;
-    if (e.w < 0.0f) {  // a body
-        if (cur != b.self) {
-            add_body(b.xi, b.yi, b.kmi, e, b.fx, b.fy);
-            ++b.inter;
-        }
-    } else if (!(b.self > cur && b.self < sk)) {  // a cell not holding this body
-        const float dx = __fsub_rn(b.xi, e.x), dy = __fsub_rn(b.yi, e.y);
-        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        if (e.w < __fmul_rn(theta2, d2)) {
-            const float f = __fdividef(b.kmi * e.z, d2);
-            b.fx += f * dx;
-            b.fy += f * dy;
-            ++b.inter;
-            b.resume = sk;
-        }
-    }
-    if (b.resume >= b.end) b.resume = 0xFFFFFFFFu;  // left its graph's subtree: done
-}
-
+// Barnes-Hut traversal without a stack, one body per thread, over the
+// pre-order array.  At element `cur` (a cell or a body) the thread accepts it
+// -- sums its monopole and moves to skip[cur], past its subtree -- or enters
+// it (cur + 1).  A body is always accepted except the thread's own (its
+// side^2 is -1); a cell holding the thread's body is always entered; any
+// other cell is accepted by the FP32 opening test of the definition.  Each
+// body sees exactly its own interaction set in depth-first order; threads of
+// a warp are Morton neighbours, so they mostly read the same elements.
 __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
                                                       const uint32_t *__restrict__ T,
                                                       const int64_t *__restrict__ koff,
@@ -523,87 +484,75 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
                                                       float theta2, float2 *__restrict__ Frep,
                                                       unsigned long long *inter_step,
                                                       unsigned long long *inter_total) {
-    constexpr int kWarpBodies = 32 * kBodiesPerLane;
-    const int lane = threadIdx.x & 31;
-    const int64_t s0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kWarpBodies;
-    if (s0 >= K) return;  // whole warp leaves together
-    const uint32_t total = uint32_t(K + T[K]);
-    Walker w[kBodiesPerLane];
-#pragma unroll
-    for (int q = 0; q < kBodiesPerLane; ++q) {
-        const int64_t s = s0 + q * 32 + lane;
-        const bool active = s < K;
-        const float4 bi = active ? body[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        w[q].xi = bi.x;
-        w[q].yi = bi.y;
-        w[q].kmi = kr * bi.z;
-        w[q].self = active ? uint32_t(s + T[s + 1]) : 0xFFFFFFFFu;
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    unsigned inter = 0;
+    if (s < K) {
+        const float4 bi = body[s];
+        const float kmi = kr * bi.z;
+        const uint32_t self = uint32_t(s + T[s + 1]);
         // the body's own graph: its subtree spans [start, end) in pre-order
-        uint32_t start = 0, end = total;
-        if (active && bgraph) {
+        uint32_t cur = 0, end = uint32_t(K + T[K]);
+        if (bgraph) {
             const int g = bgraph[s];
             const int64_t a = koff[g], b = koff[g + 1];
-            start = uint32_t(a + T[a]);
+            cur = uint32_t(a + T[a]);
             end = uint32_t(b + T[b]);
         }
-        w[q].end = end;
-        w[q].resume = active ? start : 0xFFFFFFFFu;
-        w[q].fx = 0.0f;
-        w[q].fy = 0.0f;
-        w[q].inter = 0;
-    }
-    while (true) {
-        uint32_t mine = w[0].resume;
-#pragma unroll
-        for (int q = 1; q < kBodiesPerLane; ++q) mine = min(mine, w[q].resume);
-        const uint32_t cur = __reduce_min_sync(0xFFFFFFFFu, mine);
-        if (cur >= total) break;
-        if (mine != cur) continue;
-        const float4 e = geo[cur];
-        const uint32_t sk = uint32_t(skip[cur]);
-#pragma unroll
-        for (int q = 0; q < kBodiesPerLane; ++q) walker_step(w[q], cur, e, sk, theta2);
-    }
-    unsigned inter = 0;
-#pragma unroll
-    for (int q = 0; q < kBodiesPerLane; ++q) {
-        const int64_t s = s0 + q * 32 + lane;
-        if (s < K) Frep[__float_as_int(body[s].w)] = make_float2(w[q].fx, w[q].fy);
-        inter += w[q].inter;
+        float fx = 0.0f, fy = 0.0f;
+        while (cur < end) {
+            const float4 e = geo[cur];
+            const uint32_t sk = uint32_t(skip[cur]);
+            const float dx = __fsub_rn(bi.x, e.x), dy = __fsub_rn(bi.y, e.y);
+            const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            const bool holds = self >= cur && self < sk;
+            if (!holds && e.w < __fmul_rn(theta2, d2)) {
+                if (d2 > 0.0f) {
+                    const float f = __fdividef(kmi * e.z, d2);
+                    fx += f * dx;
+                    fy += f * dy;
+                }
+                ++inter;
+                cur = sk;
+            } else {
+                cur = cur + 1;
+            }
+        }
+        Frep[__float_as_int(bi.w)] = make_float2(fx, fy);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) inter += __shfl_xor_sync(0xFFFFFFFFu, inter, d);
-    if (lane == 0 && inter) {
+    if ((threadIdx.x & 31) == 0 && inter) {
         atomicAdd(inter_step, static_cast<unsigned long long>(inter));
         atomicAdd(inter_total, static_cast<unsigned long long>(inter));
     }
 }
 
 // ------------------------------------------------------------ attraction
-// The CSR entries are cut into fixed chunks of kChunk consecutive entries,
-// one chunk per thread whatever the row lengths (a hub row spreads over many
-// threads, short rows share one).  A thread finds the row of its first entry
-// by binary search on the offsets and walks its entries accumulating
-// w_ij (p_j - p_i).  A row that starts and ends inside the chunk is written
-// to `full`; the piece of a row that continues past the chunk goes to
-// tail[chunk], the piece of a row that began before it to head[chunk].
-// k_node adds a row's pieces in chunk order, so the sum order is fixed.
-constexpr int kChunk = 8;
+// The CSR entries are cut into fixed ranges of kRange consecutive entries,
+// one warp per range whatever the row lengths (a hub row spreads over many
+// warps, short rows share one).  The warp takes its range 32 entries at a
+// time, one entry per lane: coalesced loads of the neighbour and weight,
+// gathers of the two positions, w_ij (p_j - p_i), then a segmented
+// inclusive scan over the lanes by row (rows ascend along the entries), with
+// the partial sum of the row still open at lane 31 carried to the next
+// step.  A row that starts and ends inside the range is written to `full`;
+// the piece of a row that continues past the range goes to tail[range], the
+// piece of a row that began before it to head[range].  k_node adds a row's
+// pieces in range order, so every sum has a fixed order.
+constexpr int kChunk = 8;     // entries per plan record
+constexpr int kRange = 256;   // entries per warp range
 
 // The plan, written once per CSR:
-//   chunk_row[g]   row of chunk g's first entry (the thread of row r writes r
-//                  into every chunk that starts inside the row; a warp shares
-//                  the writes of rows that cover many chunks);
-//   chunk_meta[g]  byte k (1..7): row of entry k minus chunk_row[g]; byte 0:
-//                  kMetaHead (the first row began in an earlier chunk),
-//                  kMetaTail (the last row goes on into the next chunk),
-//                  kMetaWalk (a row gap above 255: the chunk walks the
-//                  offsets instead);
-//   long_rows      the rows spread over more than kLongRowChunks chunks.
-// With the rows of all 8 entries known up front, every load of a chunk is
-// issued at once; no dependent walk over the row offsets.
-constexpr int kLongRowChunks = 32;
-constexpr unsigned kMetaHead = 1u, kMetaTail = 2u, kMetaWalk = 4u;
+//   chunk_row[g]   row of entry 8g (the thread of row r writes r into every
+//                  chunk that starts inside the row; a warp shares the writes
+//                  of rows that cover many chunks);
+//   chunk_meta[g]  byte k (1..7): row of entry 8g + k minus chunk_row[g], or
+//                  kMetaWalk in byte 0 when a gap between rows (empty rows)
+//                  exceeds 255 inside the chunk: those entries find their
+//                  row by binary search on the offsets;
+//   long_rows      the rows spread over more than kLongRowRanges ranges.
+constexpr int kLongRowRanges = 8;
+constexpr unsigned kMetaWalk = 4u;
 
 __global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
                                                          int32_t *__restrict__ chunk_row, int32_t *__restrict__ long_rows,
@@ -618,10 +567,10 @@ __global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz,
             const int64_t b = off[r], e = off[r + 1] < nnz ? off[r + 1] : nnz;
             g0 = (b + kChunk - 1) / kChunk;
             g1 = (e + kChunk - 1) / kChunk;
-            spread = e > b && (e - 1) / kChunk - b / kChunk > kLongRowChunks;
+            spread = e > b && (e - 1) / kRange - b / kRange > kLongRowRanges;
         }
         if (spread) long_rows[atomicAdd(long_count, 1)] = int32_t(r);
-        const bool longrow = g1 - g0 > kLongRowChunks;
+        const bool longrow = g1 - g0 > 32;
         if (!longrow)
             for (int64_t g = g0; g < g1; ++g) chunk_row[g] = int32_t(r);
         unsigned lm = __ballot_sync(0xFFFFFFFFu, longrow);
@@ -642,7 +591,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_meta(int64_t K, int64_t nnz,
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
         const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
         const int64_t r0 = chunk_row[g];
-        unsigned long long meta = off[r0] < e0 ? kMetaHead : 0u;
+        unsigned long long meta = 0;
         int64_t r = r0;
         for (int64_t e = e0 + 1; e < e1; ++e) {
             while (r + 1 < K && e >= off[r + 1]) ++r;
@@ -650,142 +599,123 @@ __global__ void __launch_bounds__(kThreads) k_chunk_meta(int64_t K, int64_t nnz,
             if (d > 255) meta |= kMetaWalk;
             meta |= static_cast<unsigned long long>(d > 255 ? 255 : d) << (8 * (e - e0));
         }
-        if (off[r + 1] > e1) meta |= kMetaTail;
         chunk_meta[g] = meta;
     }
 }
 
-// A row segment of a chunk goes to head[g] if it continues a row from an
-// earlier chunk, to tail[g] if its row goes on past the chunk, else it is
-// the whole row.
-__device__ __forceinline__ void put_piece(bool first, bool last, unsigned flags, int64_t g, int64_t row, float ax,
-                                          float ay, float2 *full, float2 *head, float2 *tail) {
-    const float2 v = make_float2(ax, ay);
-    if (first && (flags & kMetaHead)) head[g] = v;
-    else if (last && (flags & kMetaTail)) tail[g] = v;
+// Row of CSR entry e from the plan (binary search in the rare chunks that
+// span long runs of empty rows).
+__device__ __forceinline__ int32_t entry_row(int64_t e, int64_t K, const int32_t *__restrict__ off,
+                                             const int32_t *__restrict__ chunk_row,
+                                             const unsigned long long *__restrict__ chunk_meta) {
+    const int64_t g = e / kChunk;
+    const int32_t r0 = chunk_row[g];
+    const unsigned long long meta = chunk_meta[g];
+    if (!(meta & kMetaWalk)) {
+        const int k = int(e - g * kChunk);
+        return r0 + int32_t(k ? unsigned(meta >> (8 * k)) & 0xFFu : 0u);
+    }
+    int64_t lo = r0, hi = K - 1;  // the largest r with off[r] <= e
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return int32_t(lo);
+}
+
+__device__ __forceinline__ void put_piece(bool first, bool last, bool began, bool goes_on, int64_t q, int32_t row,
+                                          float x, float y, float2 *full, float2 *head, float2 *tail) {
+    const float2 v = make_float2(x, y);
+    if (first && began) head[q] = v;
+    else if (last && goes_on) tail[q] = v;
     else full[row] = v;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ chunk_row,
                                                       const unsigned long long *__restrict__ chunk_meta,
                                                       const int32_t *__restrict__ adj,
                                                       const uint32_t *__restrict__ w, const float2 *__restrict__ pos,
                                                       float2 *__restrict__ full, float2 *__restrict__ head,
                                                       float2 *__restrict__ tail) {
-    const int64_t chunks = (nnz + kChunk - 1) / kChunk;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(adj) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
-    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
-        const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
-        const int n = int(e1 - e0);
-        const int64_t r0 = chunk_row[g];
-        const unsigned long long meta = chunk_meta[g];
-        const unsigned flags = unsigned(meta & 0xFFu);
-        // All loads of the chunk first: 8 neighbour ids and weights (two
-        // 16-byte loads each when aligned), then the 8 neighbour and 8 row
-        // position gathers, so they are in flight together.
-        int32_t jj[kChunk];
-        uint32_t ww[kChunk];
-        if (vec && n == kChunk) {
-            const int4 a0 = __ldcs(reinterpret_cast<const int4 *>(adj + e0));
-            const int4 a1 = __ldcs(reinterpret_cast<const int4 *>(adj + e0) + 1);
-            const uint4 w0 = __ldcs(reinterpret_cast<const uint4 *>(w + e0));
-            const uint4 w1 = __ldcs(reinterpret_cast<const uint4 *>(w + e0) + 1);
-            jj[0] = a0.x; jj[1] = a0.y; jj[2] = a0.z; jj[3] = a0.w;
-            jj[4] = a1.x; jj[5] = a1.y; jj[6] = a1.z; jj[7] = a1.w;
-            ww[0] = w0.x; ww[1] = w0.y; ww[2] = w0.z; ww[3] = w0.w;
-            ww[4] = w1.x; ww[5] = w1.y; ww[6] = w1.z; ww[7] = w1.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < kChunk; ++k) {
-                jj[k] = k < n ? adj[e0 + k] : -1;
-                ww[k] = k < n ? w[e0 + k] : 0u;
-            }
-        }
-        float2 pj[kChunk];
-#pragma unroll
-        for (int k = 0; k < kChunk; ++k)
-            pj[k] = static_cast<uint64_t>(jj[k]) < static_cast<uint64_t>(K) ? pos[jj[k]] : make_float2(0.f, 0.f);
-        if (!(flags & kMetaWalk)) {
-            int32_t rk[kChunk];
-            float2 pr[kChunk];
-#pragma unroll
-            for (int k = 0; k < kChunk; ++k) {
-                rk[k] = int32_t(r0) + int32_t(k ? unsigned(meta >> (8 * k)) & 0xFFu : 0u);
-                pr[k] = k < n ? pos[rk[k]] : make_float2(0.f, 0.f);
-            }
-            float ax = 0.0f, ay = 0.0f;
-            bool first = true;
-            int32_t row = rk[0];
-#pragma unroll
-            for (int k = 0; k < kChunk; ++k) {
-                if (k < n) {
-                    if (rk[k] != row) {
-                        put_piece(first, false, flags, g, row, ax, ay, full, head, tail);
-                        first = false;
-                        row = rk[k];
-                        ax = 0.0f;
-                        ay = 0.0f;
-                    }
-                    if (static_cast<uint64_t>(jj[k]) < static_cast<uint64_t>(K)) {  // else an invalid CSR entry
-                        const float wt = __uint2float_rn(ww[k]);
-                        ax += wt * (pj[k].x - pr[k].x);
-                        ay += wt * (pj[k].y - pr[k].y);
-                    }
+    const int lane = threadIdx.x & 31;
+    const int64_t ranges = (nnz + kRange - 1) / kRange;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < ranges; q += warps) {
+        const int64_t e0 = q * kRange, e1 = e0 + kRange < nnz ? e0 + kRange : nnz;
+        const int32_t row_first = entry_row(e0, K, off, chunk_row, chunk_meta);
+        const int32_t row_last = entry_row(e1 - 1, K, off, chunk_row, chunk_meta);
+        const bool began = off[row_first] < e0;
+        const bool goes_on = off[row_last + 1] > e1;
+        int32_t crow = -1;  // row open at the end of the previous step, and its sum
+        float cx = 0.0f, cy = 0.0f;
+        for (int64_t b = e0; b < e1; b += 32) {
+            const int64_t e = b + lane;
+            const bool valid = e < e1;
+            const int32_t row = valid ? entry_row(e, K, off, chunk_row, chunk_meta) : INT32_MAX;
+            float vx = 0.0f, vy = 0.0f;
+            if (valid) {
+                const int32_t j = __ldcs(adj + e);
+                const uint32_t wt = __ldcs(w + e);
+                if (static_cast<uint64_t>(j) < static_cast<uint64_t>(K)) {  // else an invalid CSR entry
+                    const float2 pj = pos[j], pi = pos[row];
+                    const float wf = __uint2float_rn(wt);
+                    vx = wf * (pj.x - pi.x);
+                    vy = wf * (pj.y - pi.y);
                 }
             }
-            put_piece(first, true, flags, g, row, ax, ay, full, head, tail);
-            continue;
-        }
-        // Rows far apart (long runs of empty rows): walk the offsets.
-        int64_t r = r0;
-        int64_t rs = off[r], re = off[r + 1];
-        float2 pi = pos[r];
-        float ax = 0.0f, ay = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kChunk; ++k) {
-            if (k >= n) break;
-            const int64_t e = e0 + k;
-            while (e >= re && r + 1 < K) {  // row r ends before e: hand it over
-                if (rs >= e0) full[r] = make_float2(ax, ay);  // started here: complete
-                else head[g] = make_float2(ax, ay);
-                ++r;
-                rs = re;
-                re = off[r + 1];
-                pi = pos[r];
-                ax = 0.0f;
-                ay = 0.0f;
+            // the carried row ended with the previous step: emit it
+            const int32_t row0 = __shfl_sync(0xFFFFFFFFu, row, 0);
+            if (crow >= 0 && row0 != crow) {
+                if (lane == 0) put_piece(crow == row_first, false, began, goes_on, q, crow, cx, cy, full, head, tail);
+                crow = -1;
             }
-            if (static_cast<uint64_t>(jj[k]) >= static_cast<uint64_t>(K)) continue;  // invalid CSR entry
-            const float wt = __uint2float_rn(ww[k]);
-            ax += wt * (pj[k].x - pi.x);
-            ay += wt * (pj[k].y - pi.y);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float ox = __shfl_up_sync(0xFFFFFFFFu, vx, d), oy = __shfl_up_sync(0xFFFFFFFFu, vy, d);
+                const int32_t orow = __shfl_up_sync(0xFFFFFFFFu, row, d);
+                if (lane >= d && orow == row) {
+                    vx += ox;
+                    vy += oy;
+                }
+            }
+            if (row == crow) {  // the leading lanes continue the carried row
+                vx = cx + vx;
+                vy = cy + vy;
+            }
+            const int L = int(e1 - b < 32 ? e1 - b : 32) - 1;  // last valid lane
+            const int32_t nrow = __shfl_down_sync(0xFFFFFFFFu, row, 1);
+            if (lane < L && nrow != row)
+                put_piece(row == row_first, false, began, goes_on, q, row, vx, vy, full, head, tail);
+            crow = __shfl_sync(0xFFFFFFFFu, row, L);
+            cx = __shfl_sync(0xFFFFFFFFu, vx, L);
+            cy = __shfl_sync(0xFFFFFFFFu, vy, L);
         }
-        if (rs >= e0 && re <= e1) full[r] = make_float2(ax, ay);
-        else if (rs < e0) head[g] = make_float2(ax, ay);
-        else tail[g] = make_float2(ax, ay);
+        if (lane == 0) put_piece(crow == row_first, true, began, goes_on, q, crow, cx, cy, full, head, tail);
     }
 }
 
-// Rows spread over more than kLongRowChunks chunks, one warp each: the
-// lanes add strided subsets of the row's middle pieces in chunk order, then
-// a fixed butterfly, then the row's first piece.  k_node reads the result
-// from full[].
-__global__ void __launch_bounds__(kThreads) k_long_rows(const int32_t *__restrict__ off,
-                                                        const int32_t *__restrict__ long_rows,
-                                                        const int32_t *__restrict__ long_count,
-                                                        const float2 *__restrict__ head,
-                                                        const float2 *__restrict__ tail, float2 *__restrict__ full) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+// Rows spread over more than kLongRowRanges ranges, one block of
+// kLongThreads each: the threads add strided subsets of the row's middle
+// pieces in range order, the warps a fixed butterfly, thread 0 the warp sums
+// in order after the row's first piece.  k_node reads the result from
+// full[].
+constexpr int kLongThreads = 128;
+
+__global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__restrict__ off,
+                                                            const int32_t *__restrict__ long_rows,
+                                                            const int32_t *__restrict__ long_count,
+                                                            const float2 *__restrict__ head,
+                                                            const float2 *__restrict__ tail,
+                                                            float2 *__restrict__ full) {
+    __shared__ float2 wsum[kLongThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t count = *long_count;
-    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < count; q += warps) {
+    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int32_t r = long_rows[q];
-        const int64_t a = off[r] / kChunk, z = (off[r + 1] - 1) / kChunk;
+        const int64_t a = off[r] / kRange, z = (off[r + 1] - 1) / kRange;
         float px = 0.0f, py = 0.0f;
-#pragma unroll 4
-        for (int64_t g = a + 1 + lane; g <= z; g += 32) {
+        for (int64_t g = a + 1 + threadIdx.x; g <= z; g += kLongThreads) {
             const float2 v = head[g];
             px += v.x;
             py += v.y;
@@ -795,10 +725,17 @@ __global__ void __launch_bounds__(kThreads) k_long_rows(const int32_t *__restric
             px += __shfl_xor_sync(0xFFFFFFFFu, px, d);
             py += __shfl_xor_sync(0xFFFFFFFFu, py, d);
         }
-        if (lane == 0) {
-            const float2 t = tail[a];
-            full[r] = make_float2(t.x + px, t.y + py);
+        if (lane == 0) wsum[warp] = make_float2(px, py);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float2 t = tail[a];
+            for (int w = 0; w < kLongThreads / 32; ++w) {
+                t.x += wsum[w].x;
+                t.y += wsum[w].y;
+            }
+            full[r] = t;
         }
+        __syncthreads();
     }
 }
 
@@ -898,13 +835,13 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
             fr = Frep[i];
             if (mode != 0) fp = Fprev[i];
             if (e > b) {
-                g1 = b / kChunk;
-                g2 = (e - 1) / kChunk;
+                g1 = b / kRange;
+                g2 = (e - 1) / kRange;
             }
         }
-        // rows over many chunks were summed by k_long_rows into full[]
+        // rows over many ranges were summed by k_long_rows into full[]
         if (valid && g2 >= g1) {
-            if (g1 == g2 || g2 - g1 > kLongRowChunks) {
+            if (g1 == g2 || g2 - g1 > kLongRowRanges) {
                 const float2 v = full[i];
                 ax = v.x;
                 ay = v.y;
@@ -1113,7 +1050,7 @@ struct Fa2Scratch {
     float2 *full, *head, *tail;
     int32_t *chunk_row;   // plan: row of each chunk's first entry
     unsigned long long *chunk_meta;  // plan: rows of the chunk's entries, flags
-    int32_t *long_rows;   // plan: rows over more than kLongRowChunks chunks
+    int32_t *long_rows;   // plan: rows over more than kLongRowRanges ranges
     int32_t *long_count;
     double2 *part;  // two per block: (S, comp), (T, comp)
 };
@@ -1121,6 +1058,7 @@ struct Fa2Scratch {
 static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
     const size_t k = size_t(K > 0 ? K : 1);
     const size_t chunks = size_t((nnz > 0 ? nnz : 1) + kChunk - 1) / kChunk;
+    const size_t ranges = size_t((nnz > 0 ? nnz : 1) + kRange - 1) / kRange;
     const bool batched = G > 1;
     s.frame = c.take<float4>(size_t(G > 1 ? G : 1));
     s.frame_part = c.take<float4>(kFrameBlocks);
@@ -1153,11 +1091,11 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.skip = c.take<int32_t>(2 * k);
     s.Frep = c.take<float2>(k);
     s.full = c.take<float2>(k);
-    s.head = c.take<float2>(chunks);
-    s.tail = c.take<float2>(chunks);
+    s.head = c.take<float2>(ranges);
+    s.tail = c.take<float2>(ranges);
     s.chunk_row = c.take<int32_t>(chunks);
     s.chunk_meta = c.take<unsigned long long>(chunks);
-    s.long_rows = c.take<int32_t>(chunks / kLongRowChunks + 1);
+    s.long_rows = c.take<int32_t>(ranges / kLongRowRanges + 1);
     s.long_count = c.take<int32_t>(1);
     s.part = c.take<double2>(2 * kNodeBlocks);
 }
@@ -1259,8 +1197,7 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         BGV_TRY(launch_status());
         BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;
-        const int64_t rwarps = (K + 32 * kBodiesPerLane - 1) / (32 * kBodiesPerLane);
-        const unsigned gr = unsigned((rwarps * 32 + kThreads - 1) / kThreads);
+        const unsigned gr = unsigned((K + kThreads - 1) / kThreads);
         note_launch(), k_repulse<<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, koff, s.bgraph, s.body, K, p.kr,
                                                           theta2, s.Frep, &hdr->interactions,
                                                           &hdr->interactions_total);
@@ -1281,13 +1218,13 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
                                           st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
             BGV_TRY(launch_status());
         }
-        const int64_t nchunks = (nnz + kChunk - 1) / kChunk;
-        note_launch(), k_attract<<<grid_for(nchunks, kThreads, (nchunks + kThreads - 1) / kThreads), kThreads, 0,
-                                   st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
+        const int64_t nranges = (nnz + kRange - 1) / kRange;
+        note_launch(), k_attract<<<grid_for(nranges * 32, kThreads, (nranges * 32 + kThreads - 1) / kThreads), kThreads,
+                                   0, st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
                                          s.head, s.tail);
         BGV_TRY(launch_status());
-        note_launch(), k_long_rows<<<152 * 4, kThreads, 0, st>>>(csr_off, s.long_rows, s.long_count, s.head, s.tail,
-                                                                 s.full);
+        note_launch(), k_long_rows<<<152 * 16, kLongThreads, 0, st>>>(csr_off, s.long_rows, s.long_count, s.head,
+                                                                       s.tail, s.full);
         BGV_TRY(launch_status());
     }
     note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(
