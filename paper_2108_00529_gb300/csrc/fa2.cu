@@ -530,17 +530,19 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
 // ------------------------------------------------------------ attraction
 // The CSR entries are cut into fixed ranges of kRange consecutive entries,
 // one warp per range whatever the row lengths (a hub row spreads over many
-// warps, short rows share one).  The warp takes its range 32 entries at a
-// time, one entry per lane: coalesced loads of the neighbour and weight,
-// gathers of the two positions, w_ij (p_j - p_i), then a segmented
-// inclusive scan over the lanes by row (rows ascend along the entries), with
-// the partial sum of the row still open at lane 31 carried to the next
-// step.  A row that starts and ends inside the range is written to `full`;
+// warps, short rows share one).  The warp takes its range kStep entries at a
+// time, 4 consecutive entries per lane: 16-byte loads of the neighbours and
+// weights, gathers of the positions, w_ij (p_j - p_i), sums of the row runs
+// inside the lane, then a segmented inclusive scan over the lanes by row
+// (rows ascend along the entries), with the partial sum of the row still
+// open at the last lane carried to the next step.  A row that starts and ends inside the range is written to `full`;
 // the piece of a row that continues past the range goes to tail[range], the
 // piece of a row that began before it to head[range].  k_node adds a row's
 // pieces in range order, so every sum has a fixed order.
 constexpr int kChunk = 8;     // entries per plan record
-constexpr int kRange = 256;   // entries per warp range
+constexpr int kRange = 512;   // entries per warp range
+constexpr int kLaneEntries = 4;                 // consecutive entries per lane and step
+constexpr int kStep = 32 * kLaneEntries;
 
 // The plan, written once per CSR:
 //   chunk_row[g]   row of entry 8g (the thread of row r writes r into every
@@ -641,6 +643,7 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
     const int lane = threadIdx.x & 31;
     const int64_t ranges = (nnz + kRange - 1) / kRange;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const bool vec = ((reinterpret_cast<uintptr_t>(adj) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
     for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < ranges; q += warps) {
         const int64_t e0 = q * kRange, e1 = e0 + kRange < nnz ? e0 + kRange : nnz;
         const int32_t row_first = entry_row(e0, K, off, chunk_row, chunk_meta);
@@ -649,47 +652,120 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
         const bool goes_on = off[row_last + 1] > e1;
         int32_t crow = -1;  // row open at the end of the previous step, and its sum
         float cx = 0.0f, cy = 0.0f;
-        for (int64_t b = e0; b < e1; b += 32) {
-            const int64_t e = b + lane;
-            const bool valid = e < e1;
-            const int32_t row = valid ? entry_row(e, K, off, chunk_row, chunk_meta) : INT32_MAX;
-            float vx = 0.0f, vy = 0.0f;
-            if (valid) {
-                const int32_t j = __ldcs(adj + e);
-                const uint32_t wt = __ldcs(w + e);
-                if (static_cast<uint64_t>(j) < static_cast<uint64_t>(K)) {  // else an invalid CSR entry
-                    const float2 pj = pos[j], pi = pos[row];
-                    const float wf = __uint2float_rn(wt);
-                    vx = wf * (pj.x - pi.x);
-                    vy = wf * (pj.y - pi.y);
+        for (int64_t b = e0; b < e1; b += kStep) {
+            // this lane's kLaneEntries consecutive entries (one plan chunk)
+            const int64_t ea = b + int64_t(lane) * kLaneEntries;
+            const int nv = ea >= e1 ? 0 : (e1 - ea < kLaneEntries ? int(e1 - ea) : kLaneEntries);
+            int32_t j[kLaneEntries], r[kLaneEntries];
+            uint32_t wt[kLaneEntries];
+            if (nv == kLaneEntries && vec) {
+                const int4 a4 = __ldcs(reinterpret_cast<const int4 *>(adj + ea));
+                const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w + ea));
+                j[0] = a4.x; j[1] = a4.y; j[2] = a4.z; j[3] = a4.w;
+                wt[0] = w4.x; wt[1] = w4.y; wt[2] = w4.z; wt[3] = w4.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < kLaneEntries; ++k) {
+                    j[k] = k < nv ? __ldcs(adj + ea + k) : -1;
+                    wt[k] = k < nv ? __ldcs(w + ea + k) : 0u;
                 }
             }
+            if (nv > 0) {
+                const int64_t g = ea / kChunk;
+                const int32_t r0 = chunk_row[g];
+                const unsigned long long meta = chunk_meta[g];
+                const int k0 = int(ea - g * kChunk);
+#pragma unroll
+                for (int k = 0; k < kLaneEntries; ++k) {
+                    const int kk = k0 + k;
+                    r[k] = (meta & kMetaWalk) ? (k < nv ? entry_row(ea + k, K, off, chunk_row, chunk_meta) : r0)
+                                              : r0 + int32_t(kk ? unsigned(meta >> (8 * kk)) & 0xFFu : 0u);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kLaneEntries; ++k) r[k] = INT32_MAX;
+            }
+            float vx[kLaneEntries], vy[kLaneEntries];
+#pragma unroll
+            for (int k = 0; k < kLaneEntries; ++k) {
+                vx[k] = 0.0f;
+                vy[k] = 0.0f;
+                if (k < nv && static_cast<uint64_t>(j[k]) < static_cast<uint64_t>(K)) {  // else an invalid entry
+                    const float2 pj = pos[j[k]], pi = pos[r[k]];
+                    const float wf = __uint2float_rn(wt[k]);
+                    vx[k] = wf * (pj.x - pi.x);
+                    vy[k] = wf * (pj.y - pi.y);
+                }
+            }
+            // In-lane runs: the first row's run (ra, pa), rows complete inside
+            // the lane (written at once), the last row's run (rb, pb).
+            const int32_t ra = r[0], rb = nv > 0 ? r[nv - 1] : INT32_MAX;
+            float pax = 0.0f, pay = 0.0f, pbx = 0.0f, pby = 0.0f;
+            {
+                int32_t cur = ra;
+                float ax = 0.0f, ay = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kLaneEntries; ++k) {
+                    if (k < nv) {
+                        if (r[k] != cur) {
+                            if (cur == ra) {
+                                pax = ax;
+                                pay = ay;
+                            } else {
+                                put_piece(false, false, began, goes_on, q, cur, ax, ay, full, head, tail);
+                            }
+                            cur = r[k];
+                            ax = 0.0f;
+                            ay = 0.0f;
+                        }
+                        ax += vx[k];
+                        ay += vy[k];
+                    }
+                }
+                pbx = ax;
+                pby = ay;
+            }
             // the carried row ended with the previous step: emit it
-            const int32_t row0 = __shfl_sync(0xFFFFFFFFu, row, 0);
-            if (crow >= 0 && row0 != crow) {
+            const int32_t ra0 = __shfl_sync(0xFFFFFFFFu, ra, 0);
+            if (crow >= 0 && ra0 != crow) {
                 if (lane == 0) put_piece(crow == row_first, false, began, goes_on, q, crow, cx, cy, full, head, tail);
                 crow = -1;
             }
+            // segmented inclusive scan of the last runs by row (rows ascend
+            // along the lanes, so equal rows are one segment)
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const float ox = __shfl_up_sync(0xFFFFFFFFu, vx, d), oy = __shfl_up_sync(0xFFFFFFFFu, vy, d);
-                const int32_t orow = __shfl_up_sync(0xFFFFFFFFu, row, d);
-                if (lane >= d && orow == row) {
-                    vx += ox;
-                    vy += oy;
+                const float ox = __shfl_up_sync(0xFFFFFFFFu, pbx, d), oy = __shfl_up_sync(0xFFFFFFFFu, pby, d);
+                const int32_t orow = __shfl_up_sync(0xFFFFFFFFu, rb, d);
+                if (lane >= d && orow == rb) {
+                    pbx += ox;
+                    pby += oy;
                 }
             }
-            if (row == crow) {  // the leading lanes continue the carried row
-                vx = cx + vx;
-                vy = cy + vy;
+            if (rb == crow) {  // the leading lanes continue the carried row
+                pbx = cx + pbx;
+                pby = cy + pby;
             }
-            const int L = int(e1 - b < 32 ? e1 - b : 32) - 1;  // last valid lane
-            const int32_t nrow = __shfl_down_sync(0xFFFFFFFFu, row, 1);
-            if (lane < L && nrow != row)
-                put_piece(row == row_first, false, began, goes_on, q, row, vx, vy, full, head, tail);
-            crow = __shfl_sync(0xFFFFFFFFu, row, L);
-            cx = __shfl_sync(0xFFFFFFFFu, vx, L);
-            cy = __shfl_sync(0xFFFFFFFFu, vy, L);
+            // a lane whose first run closes inside it takes what precedes it
+            int32_t prb = __shfl_up_sync(0xFFFFFFFFu, rb, 1);
+            float ppx = __shfl_up_sync(0xFFFFFFFFu, pbx, 1), ppy = __shfl_up_sync(0xFFFFFFFFu, pby, 1);
+            if (lane == 0) {
+                prb = crow;
+                ppx = cx;
+                ppy = cy;
+            }
+            if (nv > 0 && ra != rb) {
+                const bool cont = prb == ra;
+                put_piece(ra == row_first, false, began, goes_on, q, ra, cont ? ppx + pax : pax,
+                          cont ? ppy + pay : pay, full, head, tail);
+            }
+            const int L = int((e1 - 1 - b) / kLaneEntries < 31 ? (e1 - 1 - b) / kLaneEntries : 31);  // last valid lane
+            const int32_t nra = __shfl_down_sync(0xFFFFFFFFu, ra, 1);
+            if (lane < L && nra != rb)
+                put_piece(rb == row_first, false, began, goes_on, q, rb, pbx, pby, full, head, tail);
+            crow = __shfl_sync(0xFFFFFFFFu, rb, L);
+            cx = __shfl_sync(0xFFFFFFFFu, pbx, L);
+            cy = __shfl_sync(0xFFFFFFFFu, pby, L);
         }
         if (lane == 0) put_piece(crow == row_first, true, began, goes_on, q, crow, cx, cy, full, head, tail);
     }

@@ -191,7 +191,6 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 inline int sort_items(int64_t cap) { return cap <= kSmallSort ? kSortItemsSmall : kSortItemsBig; }
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
-constexpr uint32_t kInvalidDigit = 0xFFFFu;
 // Look-back words: 2 flag bits, the pass number (1..8) in bits 40..47 and a
 // 40-bit count.  The words are cleared once per sort; a word written by an
 // earlier pass carries another pass number and reads as "not yet published".
@@ -255,25 +254,42 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t base = tile * (kSortThreads * kItems) + int64_t(warp) * (32 * kItems);
-    // Registers hold the keys and ranks only; digits are recomputed from the
-    // keys and the values are loaded just before the scatter.
+    // Keys are loaded up front, and with 8 keys per thread the values too
+    // (their latency then overlaps the ranking; with 16 the registers would
+    // halve the resident blocks).  Digits are recomputed from the keys.
+    constexpr bool kEarlyVals = kVals && kItems <= 8;
     unsigned long long key[kItems];
+    uint32_t val[kItems];
     uint32_t rank[kItems];
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int64_t i = base + int64_t(k) * 32 + lane;
         key[k] = i < n ? kin[i] : 0ull;
+        if (kEarlyVals) val[k] = i < n ? vin[i] : 0u;
     }
+    // Rank inside the warp: the lanes holding the same digit are found with
+    // nine ballots (eight digit bits and validity); the lowest of them reads
+    // and advances the warp's counter for that digit.
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int64_t i = base + int64_t(k) * 32 + lane;
-        const uint32_t d = i < n ? (static_cast<uint32_t>(key[k] >> shift) & 0xFFu) : kInvalidDigit;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const bool valid = i < n;
+        const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+        uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? m : ~m;
+        }
+        const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
-        if (d != kInvalidDigit) before = cnt[warp][d];
+        if (valid && lane == leader) {
+            before = cnt[warp][d];
+            cnt[warp][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xFFFFFFFFu, before, leader);
         rank[k] = before + __popc(peers & lt_mask);
-        __syncwarp();
-        if (d != kInvalidDigit && (peers & lt_mask) == 0) cnt[warp][d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -337,7 +353,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
         const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
         const uint32_t pos = tile_base[d] + cnt[warp][d] + rank[k];
         kout[pos] = key[k];
-        if (kVals) vout[pos] = vin[i];
+        if (kVals) vout[pos] = kEarlyVals ? val[k] : vin[i];
     }
 }
 }  // namespace
