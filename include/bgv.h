@@ -278,7 +278,7 @@ int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *c
  * BGV_FA2_STAGES stages of each step; synchronises `stream` and returns in
  * stage_ms[BGV_FA2_STAGES] the summed milliseconds per stage:
  *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order,
- *   3 tree build, 4 quadtree nodes, 5 Barnes-Hut repulsion,
+ *   3 moments, radix tree and quadtree cells, 4 pre-order layout, 5 Barnes-Hut repulsion,
  *   6 attraction + gravity + swing/traction + speed, 7 displacement.
  * Creates and destroys (BGV_FA2_STAGES + 1) * iterations CUDA events. */
 #define BGV_FA2_STAGES 8

@@ -250,7 +250,7 @@ def bgv_fa2_run(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, use_g
 
 
 BGV_FA2_STAGES = 8
-FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "quad", "repulsion", "node_speed", "update"]
+FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "preorder", "repulsion", "node_speed", "update"]
 
 
 def bgv_fa2_run_timed(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, pos, F, Fprev, speed, ws,

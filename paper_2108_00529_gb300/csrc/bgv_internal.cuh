@@ -132,6 +132,8 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
                int *result_buffer, uint32_t *dev_status);
 
+
+
 // Number of bits needed to hold values 0..n-1 (at least 1).
 inline int bits_for(int64_t n) {
     int b = 1;

@@ -213,47 +213,6 @@ __device__ __forceinline__ int key_delta(const unsigned long long *__restrict__ 
     return keybits + __clz(static_cast<int>(uint32_t(i) ^ uint32_t(j)));
 }
 
-__global__ void __launch_bounds__(kThreads) k_radix_tree(const unsigned long long *__restrict__ keys, int64_t K,
-                                                         int L, int gbits, int32_t *__restrict__ left,
-                                                         int32_t *__restrict__ right, int32_t *__restrict__ parent,
-                                                         int2 *__restrict__ range, int8_t *__restrict__ level,
-                                                         int32_t *__restrict__ root) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= K - 1) return;
-    const int kb = 2 * L + gbits;
-    const unsigned long long ki = __ldg(&keys[i]);
-    const int d = key_delta(keys, K, kb, i, ki, i + 1) > key_delta(keys, K, kb, i, ki, i - 1) ? 1 : -1;
-    const int dmin = key_delta(keys, K, kb, i, ki, i - d);
-    int64_t lmax = 2;
-    while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
-    int64_t l = 0;
-    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-        if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
-    const int64_t j = i + l * d;
-    const int dnode = key_delta(keys, K, kb, i, ki, j);
-    int64_t sp = 0;
-    for (int64_t div = 2;; div <<= 1) {
-        const int64_t t = (l + div - 1) / div;
-        if (key_delta(keys, K, kb, i, ki, i + (sp + t) * d) > dnode) sp += t;
-        if (t <= 1) break;
-    }
-    const int64_t gamma = i + sp * d + (d < 0 ? -1 : 0);
-    const int64_t first = i < j ? i : j, last = i < j ? j : i;
-    const int32_t lc = first == gamma ? ~int32_t(gamma) : int32_t(gamma);
-    const int32_t rc = last == gamma + 1 ? ~int32_t(gamma + 1) : int32_t(gamma + 1);
-    left[i] = lc;
-    right[i] = rc;
-    if (lc >= 0) parent[lc] = int32_t(i);
-    if (rc >= 0) parent[rc] = int32_t(i);
-    if (i == 0) {
-        parent[0] = -1;
-        *root = 0;
-    }
-    range[i] = make_int2(int32_t(first), int32_t(last));
-    // 2-bit quadtree level below the graph bits; -1 above a graph's root
-    level[i] = static_cast<int8_t>(dnode >= kb ? L : (dnode < gbits ? -1 : ((dnode - gbits) >> 1)));
-}
-
 // Exact moment prefix sums over the Morton order: P[s] = sum over bodies
 // t < s of (m, m*Ux, m*Uy), in 64/128-bit integers, so every node's moments
 // are P[last+1] - P[first] (exact, order-free).
@@ -383,32 +342,56 @@ __global__ void __launch_bounds__(kThreads) k_mom_down(const uint2 *__restrict__
     }
 }
 
-// Quadtree cells: the binary nodes whose 2-bit level exceeds their parent's
-// (a chain of single-child cells collapses into its deepest cell, which
-// takes the opening test for the whole chain).  For each cell: FP32 centre
-// from the exact moments, mass, and the squared side used by the opening
-// test (+inf for a leaf that is never accepted).  Cells are counted by their
-// first body for the pre-order layout.
-__global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_cap, const float4 *__restrict__ frames,
-                                                    const int32_t *__restrict__ bgraph,
-                                                    const int32_t *__restrict__ parent,
-                                                    const int2 *__restrict__ range, const int8_t *__restrict__ level,
-                                                    const unsigned long long *__restrict__ PM,
-                                                    const ulonglong2 *__restrict__ PX,
-                                                    const ulonglong2 *__restrict__ PY, float4 *__restrict__ cell,
-                                                    int8_t *__restrict__ topflag, uint32_t *__restrict__ start_count,
-                                                    unsigned long long *tree_nodes) {
-    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// 2-bit quadtree level of a binary node with split prefix length delta (the
+// graph bits come first): -1 above a graph's root, L for coincident keys.
+__device__ __forceinline__ int node_level(int delta, int kb, int L, int gbits) {
+    return delta >= kb ? L : (delta < gbits ? -1 : ((delta - gbits) >> 1));
+}
+
+// Binary radix tree and quadtree cells in one pass, one thread per internal
+// node (Karras, HPG 2012): the node's range and split prefix length come
+// from an exponential and a binary search on key prefixes.  Its parent's
+// split is the nearer of the two pairs just outside the range (the far one
+// shares a shorter prefix), so the node knows its parent's level without
+// waiting for anyone.  A node is a quadtree cell when its level exceeds its
+// parent's (a chain of single-child cells collapses into its deepest cell,
+// which takes the opening test for the whole chain).  For each cell: FP32
+// centre from the exact moments, mass, and the squared side used by the
+// opening test (+inf for a leaf that is never accepted); cells are counted
+// per first body, and their levels recorded there, for the pre-order
+// layout.
+__global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__restrict__ keys, int64_t K, int L,
+                                                   int gbits, int leaf_cap, const float4 *__restrict__ frames,
+                                                   const int32_t *__restrict__ bgraph,
+                                                   const unsigned long long *__restrict__ PM,
+                                                   const ulonglong2 *__restrict__ PX,
+                                                   const ulonglong2 *__restrict__ PY, int2 *__restrict__ range,
+                                                   int8_t *__restrict__ cell_level, float4 *__restrict__ cell,
+                                                   uint32_t *__restrict__ start_count,
+                                                   uint32_t *__restrict__ start_levels,
+                                                   unsigned long long *tree_nodes) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     bool top = false;
-    if (p < K - 1) {
-        const int lev = level[p];
-        const int32_t par = parent[p];
-        const int par_lev = (par < 0 || int64_t(par) >= K - 1) ? -1 : int(level[par]);
+    if (i < K - 1) {
+        const int kb = 2 * L + gbits;
+        const unsigned long long ki = __ldg(&keys[i]);
+        const int d = key_delta(keys, K, kb, i, ki, i + 1) > key_delta(keys, K, kb, i, ki, i - 1) ? 1 : -1;
+        const int dmin = key_delta(keys, K, kb, i, ki, i - d);
+        int64_t lmax = 2;
+        while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
+        int64_t l = 0;
+        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+            if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
+        const int64_t j = i + l * d;
+        const int dnode = key_delta(keys, K, kb, i, ki, j);
+        const int64_t first = i < j ? i : j, last = i < j ? j : i;
+        const int lev = node_level(dnode, kb, L, gbits);
+        const int par_lev = node_level(dmin, kb, L, gbits);
         top = par_lev < lev;
-        topflag[p] = top ? 1 : 0;
+        cell_level[i] = static_cast<int8_t>(top ? lev : -1);
         if (top) {
-            const int2 rg = range[p];
-            const int cnt = rg.y - rg.x + 1;
+            range[i] = make_int2(int32_t(first), int32_t(last));
+            const int cnt = int(last - first) + 1;
             const bool leaf = cnt <= leaf_cap || lev >= L;
             // A leaf made by the depth limit (coincident keys, more than
             // leaf_cap bodies) hides a chain of non-leaf cells with the same
@@ -416,8 +399,8 @@ __global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_c
             // at level L - 1, takes the opening test for the whole chain.
             const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
             // positions of graph g in Morton order are its index range too
-            const float4 fr = frames[bgraph ? bgraph[rg.x] : 0];
-            const Mom hi = mom_load(PM, PX, PY, rg.y + 1), lo = mom_load(PM, PX, PY, rg.x);
+            const float4 fr = frames[bgraph ? bgraph[first] : 0];
+            const Mom hi = mom_load(PM, PX, PY, last + 1), lo = mom_load(PM, PX, PY, first);
             const unsigned long long M = hi.M - lo.M;
             const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
             const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
@@ -425,8 +408,9 @@ __global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_c
             const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), 2.3283064365386963e-10f)));
             const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
             const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
-            cell[p] = make_float4(cx, cy, __ull2float_rn(M), side2);
-            atomicAdd(&start_count[rg.x], 1u);
+            cell[i] = make_float4(cx, cy, __ull2float_rn(M), side2);
+            atomicAdd(&start_count[first], 1u);
+            atomicOr(&start_levels[first], 1u << lev);
         }
     }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, top);
@@ -439,10 +423,13 @@ __global__ void __launch_bounds__(kThreads) k_cells(int64_t K, int L, int leaf_c
 //                                          comes first)
 //   cell [a, b]      -> a + T[a] + (its ancestors that also start at a)
 //   skip(cell [a,b]) -> b + 1 + T[b+1]   (the element after its subtree)
-// Elements are float4 (x, y, mass, side^2), side^2 = -1 for a body.
-__global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int32_t *__restrict__ parent,
-                                                       const int2 *__restrict__ range,
-                                                       const int8_t *__restrict__ topflag,
+// The cells starting at body a are nested with strictly increasing levels,
+// so a cell's ancestors among them are those of a lower level in
+// start_levels[a].  Elements are float4 (x, y, mass, side^2), side^2 = -1
+// for a body.
+__global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int2 *__restrict__ range,
+                                                       const int8_t *__restrict__ cell_level,
+                                                       const uint32_t *__restrict__ start_levels,
                                                        const float4 *__restrict__ cell,
                                                        const uint32_t *__restrict__ T,
                                                        const float4 *__restrict__ body, float4 *__restrict__ geo,
@@ -454,16 +441,15 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int32_t 
         geo[pre] = make_float4(b.x, b.y, b.z, -1.0f);
         skip[pre] = int32_t(pre + 1);
     }
-    if (t < K - 1 && topflag[t]) {
-        const int2 rg = range[t];
-        int dep = 0;
-        for (int32_t par = parent[t]; par >= 0 && int64_t(par) < K - 1; par = parent[par]) {
-            if (range[par].x != rg.x) break;
-            dep += topflag[par];
+    if (t < K - 1) {
+        const int lev = cell_level[t];
+        if (lev >= 0) {
+            const int2 rg = range[t];
+            const int dep = __popc(start_levels[rg.x] & ((1u << lev) - 1u));
+            const int64_t pre = rg.x + int64_t(T[rg.x]) + dep;
+            geo[pre] = cell[t];
+            skip[pre] = int32_t(int64_t(rg.y) + 1 + T[rg.y + 1]);
         }
-        const int64_t pre = rg.x + int64_t(T[rg.x]) + dep;
-        geo[pre] = cell[t];
-        skip[pre] = int32_t(int64_t(rg.y) + 1 + T[rg.y + 1]);
     }
 }
 
@@ -1110,14 +1096,13 @@ struct Fa2Scratch {
     float4 *body;
     uint2 *sU;
     uint32_t *smass;
-    int32_t *left, *right, *parent, *root;
-    int2 *range;
-    int8_t *level;
+    int2 *range;           // per binary node that is a cell: its bodies
+    int8_t *cell_level;    // per binary node: its level if a cell, else -1
     unsigned long long *PM, *TM;   // moment prefix sums, per-tile sums
     ulonglong2 *PX, *PY, *TX, *TY;
     float4 *cell;          // per binary node: centre, mass, side^2 (cells only)
-    int8_t *topflag;       // per binary node: is a quadtree cell
     uint32_t *start_count; // cells per first body
+    uint32_t *start_levels;  // levels of the cells per first body (bit mask)
     uint32_t *T;           // exclusive scan of start_count, K + 1 entries
     void *scan_tmp;
     float4 *geo;           // pre-order elements (cells and bodies)
@@ -1146,12 +1131,8 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.sU = c.take<uint2>(k);
     s.smass = c.take<uint32_t>(k);
     const size_t tiles = (k + kMomTile - 1) / kMomTile;
-    s.left = c.take<int32_t>(k);
-    s.right = c.take<int32_t>(k);
-    s.parent = c.take<int32_t>(k);
-    s.root = c.take<int32_t>(1);
     s.range = c.take<int2>(k);
-    s.level = c.take<int8_t>(k);
+    s.cell_level = c.take<int8_t>(k);
     s.PM = c.take<unsigned long long>(k + 1);
     s.PX = c.take<ulonglong2>(k + 1);
     s.PY = c.take<ulonglong2>(k + 1);
@@ -1159,8 +1140,8 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.TX = c.take<ulonglong2>(tiles);
     s.TY = c.take<ulonglong2>(tiles);
     s.cell = c.take<float4>(k);
-    s.topflag = c.take<int8_t>(k);
     s.start_count = c.take<uint32_t>(k + 1);
+    s.start_levels = c.take<uint32_t>(k);
     s.T = c.take<uint32_t>(k + 1);
     s.scan_tmp = c.take<char>(scan_tmp_bytes(int64_t(k) + 1));
     s.geo = c.take<float4>(2 * k);
@@ -1254,22 +1235,20 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         const unsigned gi = unsigned((K - 1 + kThreads - 1) / kThreads);
         const unsigned tiles = unsigned((K + kMomTile - 1) / kMomTile);
-        note_launch(), k_radix_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, s.left, s.right,
-                                                             s.parent, s.range, s.level, s.root);
-        BGV_TRY(launch_status());
         note_launch(), k_mom_reduce<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY);
         note_launch(), k_mom_tiles<<<1, kThreads, 0, st>>>(s.TM, s.TX, s.TY, tiles);
         note_launch(), k_mom_down<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY, s.PM, s.PX, s.PY);
         BGV_TRY(launch_status());
-        BGV_TRY(mark(4));
         BGV_CUDA(cudaMemsetAsync(s.start_count, 0, sizeof(uint32_t) * size_t(K), st));
-        note_launch(), k_cells<<<gi, kThreads, 0, st>>>(K, L, p.leaf_cap, s.frame, s.bgraph, s.parent, s.range,
-                                                        s.level, s.PM, s.PX, s.PY, s.cell, s.topflag, s.start_count,
-                                                        &hdr->tree_nodes);
+        BGV_CUDA(cudaMemsetAsync(s.start_levels, 0, sizeof(uint32_t) * size_t(K), st));
+        note_launch(), k_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph,
+                                                       s.PM, s.PX, s.PY, s.range, s.cell_level, s.cell,
+                                                       s.start_count, s.start_levels, &hdr->tree_nodes);
         BGV_TRY(launch_status());
+        BGV_TRY(mark(4));
         BGV_TRY(scan_exclusive(s.start_count, s.T, K, nullptr, nullptr, true, s.scan_tmp, st));
-        note_launch(), k_preorder<<<gt, kThreads, 0, st>>>(K, s.parent, s.range, s.topflag, s.cell, s.T, s.body,
-                                                           s.geo, s.skip);
+        note_launch(), k_preorder<<<gt, kThreads, 0, st>>>(K, s.range, s.cell_level, s.start_levels, s.cell, s.T,
+                                                           s.body, s.geo, s.skip);
         BGV_TRY(launch_status());
         BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;

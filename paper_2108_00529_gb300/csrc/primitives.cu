@@ -373,10 +373,36 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out) {
     out.counts = c.take<uint32_t>(size_t(kMaxPasses) * kBins + kMaxPasses);
 }
 
+namespace {
+// One onesweep pass on the 8-bit digit at `shift`, from buffer pair `cur` to
+// `cur ^ 1`.
+int onesweep_pass(SortBuffers &b, int64_t cap, const int64_t *d_count, int cur, int shift, const uint32_t *base,
+                  unsigned *tile_counter, unsigned long long tag, cudaStream_t s, uint32_t *dev_status) {
+    const unsigned g = static_cast<unsigned>(sort_tiles(cap));
+    const bool small = sort_items(cap) == kSortItemsSmall;
+    unsigned long long *ki = b.keys[cur], *ko = b.keys[cur ^ 1];
+    uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1];
+    if (b.vals[0] && small)
+        note_launch(), k_sort_onesweep<true, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
+            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+    else if (b.vals[0])
+        note_launch(), k_sort_onesweep<true, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
+            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+    else if (small)
+        note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
+            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+    else
+        note_launch(), k_sort_onesweep<false, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
+            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+    return launch_status();
+}
+
+inline unsigned long long pass_tag(int p) { return static_cast<unsigned long long>(p + 1) << kTagShift; }
+}  // namespace
+
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
                int *result_buffer, uint32_t *dev_status) {
     const int64_t tiles = sort_tiles(cap);
-    const int items = sort_items(cap);
     const int passes = (end_bit + 7) / 8;
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
@@ -389,23 +415,8 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     int cur = 0;
     BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
     for (int p = 0; p < passes; ++p) {
-        const unsigned long long tag = static_cast<unsigned long long>(p + 1) << kTagShift;
-        const unsigned g = static_cast<unsigned>(tiles);
-        unsigned long long *ki = b.keys[cur], *ko = b.keys[cur ^ 1];
-        uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1], *base = b.counts + p * kBins;
-        if (b.vals[0] && items == kSortItemsSmall)
-            note_launch(), k_sort_onesweep<true, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
-        else if (b.vals[0])
-            note_launch(), k_sort_onesweep<true, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-                ki, ko, vi, vo, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
-        else if (items == kSortItemsSmall)
-            note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
-        else
-            note_launch(), k_sort_onesweep<false, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-                ki, ko, nullptr, nullptr, cap, d_count, 8 * p, base, tile_counters + p, b.status, dev_status, tag);
-        BGV_TRY(launch_status());
+        BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p), s,
+                              dev_status));
         cur ^= 1;
     }
     *result_buffer = cur;
