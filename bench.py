@@ -242,6 +242,7 @@ def gpu_arm(args, dist: Dist):
     fp = B.bgv_fa2_default_params()
     K_host = torch.zeros(2, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sampled = min(10, iters)
 
     def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -261,13 +262,17 @@ def gpu_arm(args, dist: Dist):
         nnz = 2 * int(K_host[1].item())
         with torch.cuda.stream(s):
             B.bgv_fa2_init(K, fp, pos, Fprev, speed, stream=s)
-            stages = B.bgv_fa2_run_timed(K, nnz, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa,
+            # the iterations run as replays of one captured step, as in
+            # bgv_layout; the last `sampled` run launch by launch with events
+            # at the stage boundaries, which time the kernels inside the step
+            B.bgv_fa2_run(K, nnz, off, adj, cw, mass, fp, iters - sampled, 1, pos, F, Fprev, speed, ws_fa, stream=s)
+            stages = B.bgv_fa2_run_timed(K, nnz, off, adj, cw, mass, fp, sampled, pos, F, Fprev, speed, ws_fa,
                                          stream=s)
             ev[4].record(s)
         s.synchronize()
         t = [ev[0].elapsed_time(ev[i]) for i in range(1, 5)]
         return dict(total=t[3], sketch=t[0], communities=t[1] - t[0], supergraph=t[2] - t[1], fa2=t[3] - t[2],
-                    fa2_stages=stages, K=K)
+                    fa2_stages=[x / sampled for x in stages], K=K)
 
     def flush_l2():
         flush.zero_()
@@ -306,7 +311,7 @@ def gpu_arm(args, dist: Dist):
     # dominant kernel: Barnes-Hut repulsion (one launch per FA2 iteration)
     steps_run = st1.steps_total - st0.steps_total
     inter_per_launch = (st1.interactions_total - st0.interactions_total) / max(steps_run, 1)
-    rep_launch_ms = fa2_stage_ms["repulsion"] / iters
+    rep_launch_ms = fa2_stage_ms["repulsion"]  # per iteration = per launch
     achieved_tf = inter_per_launch * FLOPS_PER_INTERACTION / (rep_launch_ms * 1e-3) / 1e12
     peak_tf = fp32_peak_tflops()
     roofline = {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(achieved_tf, 3),
@@ -364,7 +369,9 @@ def gpu_arm(args, dist: Dist):
         "K": K, "Es": Es, "m_cut": m_cut,
         "fa2_iters_per_s": round(iters / (stage_ms["fa2"] * 1e-3), 2),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "fa2_stage_ms": {k: round(v, 4) for k, v in fa2_stage_ms.items()},
+        "fa2_stage_us_per_iteration": {k: round(1000 * v, 2) for k, v in fa2_stage_ms.items()},
+        "fa2_stage_note": f"CUDA events at the stage boundaries of the last {sampled} iterations of every timed step "
+                          "(launched one by one; the others replay a captured step)",
         "roofline": roofline,
         "edge_roofline": edge_roofline,
         "e2e": {"value": round(m * dist.world / (e2e_ms * 1e-3), 1), "unit": "edges/s",
@@ -434,6 +441,7 @@ def gpu_arm_whole(args, dist: Dist):
     nnz_h = torch.zeros(1, dtype=torch.int64).pin_memory()
     K_h = torch.zeros(1, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sampled = min(10, iters)
 
     def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -457,13 +465,14 @@ def gpu_arm_whole(args, dist: Dist):
         nnz = int(nnz_h.item())
         with torch.cuda.stream(s):
             B.bgv_fa2_init(n, fp, pos, Fprev, speed, stream=s)
-            stages = B.bgv_fa2_run_timed(n, nnz, off, adj, cw, mass, fp, iters, pos, F, Fprev, speed, ws_fa,
+            B.bgv_fa2_run(n, nnz, off, adj, cw, mass, fp, iters - sampled, 1, pos, F, Fprev, speed, ws_fa, stream=s)
+            stages = B.bgv_fa2_run_timed(n, nnz, off, adj, cw, mass, fp, sampled, pos, F, Fprev, speed, ws_fa,
                                          stream=s)
             ev[3].record(s)
         s.synchronize()
         t = [ev[0].elapsed_time(ev[i]) for i in range(1, 4)]
-        return dict(total=t[2], communities=t[0], graph_csr=t[1] - t[0], fa2=t[2] - t[1], fa2_stages=stages,
-                    nnz=nnz)
+        return dict(total=t[2], communities=t[0], graph_csr=t[1] - t[0], fa2=t[2] - t[1],
+                    fa2_stages=[x / sampled for x in stages], nnz=nnz)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -487,7 +496,7 @@ def gpu_arm_whole(args, dist: Dist):
     fa2_ms = float(np.mean([r["fa2"] for r in results]))
     stage = {nm: float(np.mean([r["fa2_stages"][i] for r in results])) for i, nm in enumerate(B.FA2_STAGE_NAMES)}
     inter = (st1.interactions_total - st0.interactions_total) / max(st1.steps_total - st0.steps_total, 1)
-    rep_ms = stage["repulsion"] / iters
+    rep_ms = stage["repulsion"]  # per iteration = per launch
     ach = inter * FLOPS_PER_INTERACTION / (rep_ms * 1e-3) / 1e12
     out = {
         "metric": METRIC, "value": round(m * dist.world / (ms * 1e-3), 1), "unit": "edges/s",
@@ -499,7 +508,7 @@ def gpu_arm_whole(args, dist: Dist):
         "fa2_iters_per_s": round(iters / (fa2_ms * 1e-3), 2),
         "stage_ms": {k: round(float(np.mean([r[k] for r in results])), 4)
                      for k in ("communities", "graph_csr", "fa2")},
-        "fa2_stage_ms": {k: round(v, 4) for k, v in stage.items()},
+        "fa2_stage_us_per_iteration": {k: round(1000 * v, 2) for k, v in stage.items()},
         "roofline": {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(ach, 3),
                      "peak": round(fp32_peak_tflops(), 2), "unit": "TFLOP/s",
                      "frac": round(ach / fp32_peak_tflops(), 4), "traffic": None,

@@ -619,6 +619,51 @@ __device__ __forceinline__ void put_piece(bool first, bool last, bool began, boo
     else full[row] = v;
 }
 
+// One lane's kLaneEntries consecutive entries of a step (one plan chunk):
+// neighbours, weights and rows; nv of them exist.
+struct LaneEntries {
+    int32_t j[kLaneEntries], r[kLaneEntries];
+    uint32_t wt[kLaneEntries];
+    int nv;
+};
+
+__device__ __forceinline__ void load_lane(int64_t b, int64_t e1, int lane, int64_t K, const int32_t *__restrict__ off,
+                                          const int32_t *__restrict__ chunk_row,
+                                          const unsigned long long *__restrict__ chunk_meta,
+                                          const int32_t *__restrict__ adj, const uint32_t *__restrict__ w, bool vec,
+                                          LaneEntries &le) {
+    const int64_t ea = b + int64_t(lane) * kLaneEntries;
+    const int nv = ea >= e1 ? 0 : (e1 - ea < kLaneEntries ? int(e1 - ea) : kLaneEntries);
+    le.nv = nv;
+    if (nv == kLaneEntries && vec) {
+        const int4 a4 = __ldcs(reinterpret_cast<const int4 *>(adj + ea));
+        const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w + ea));
+        le.j[0] = a4.x; le.j[1] = a4.y; le.j[2] = a4.z; le.j[3] = a4.w;
+        le.wt[0] = w4.x; le.wt[1] = w4.y; le.wt[2] = w4.z; le.wt[3] = w4.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kLaneEntries; ++k) {
+            le.j[k] = k < nv ? __ldcs(adj + ea + k) : -1;
+            le.wt[k] = k < nv ? __ldcs(w + ea + k) : 0u;
+        }
+    }
+    if (nv > 0) {
+        const int64_t g = ea / kChunk;
+        const int32_t r0 = chunk_row[g];
+        const unsigned long long meta = chunk_meta[g];
+        const int k0 = int(ea - g * kChunk);
+#pragma unroll
+        for (int k = 0; k < kLaneEntries; ++k) {
+            const int kk = k0 + k;
+            le.r[k] = (meta & kMetaWalk) ? (k < nv ? entry_row(ea + k, K, off, chunk_row, chunk_meta) : r0)
+                                         : r0 + int32_t(kk ? unsigned(meta >> (8 * kk)) & 0xFFu : 0u);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kLaneEntries; ++k) le.r[k] = INT32_MAX;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ chunk_row,
                                                       const unsigned long long *__restrict__ chunk_meta,
@@ -638,54 +683,32 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
         const bool goes_on = off[row_last + 1] > e1;
         int32_t crow = -1;  // row open at the end of the previous step, and its sum
         float cx = 0.0f, cy = 0.0f;
+        LaneEntries le;
+        load_lane(e0, e1, lane, K, off, chunk_row, chunk_meta, adj, w, vec, le);
         for (int64_t b = e0; b < e1; b += kStep) {
-            // this lane's kLaneEntries consecutive entries (one plan chunk)
-            const int64_t ea = b + int64_t(lane) * kLaneEntries;
-            const int nv = ea >= e1 ? 0 : (e1 - ea < kLaneEntries ? int(e1 - ea) : kLaneEntries);
-            int32_t j[kLaneEntries], r[kLaneEntries];
-            uint32_t wt[kLaneEntries];
-            if (nv == kLaneEntries && vec) {
-                const int4 a4 = __ldcs(reinterpret_cast<const int4 *>(adj + ea));
-                const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w + ea));
-                j[0] = a4.x; j[1] = a4.y; j[2] = a4.z; j[3] = a4.w;
-                wt[0] = w4.x; wt[1] = w4.y; wt[2] = w4.z; wt[3] = w4.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < kLaneEntries; ++k) {
-                    j[k] = k < nv ? __ldcs(adj + ea + k) : -1;
-                    wt[k] = k < nv ? __ldcs(w + ea + k) : 0u;
-                }
-            }
-            if (nv > 0) {
-                const int64_t g = ea / kChunk;
-                const int32_t r0 = chunk_row[g];
-                const unsigned long long meta = chunk_meta[g];
-                const int k0 = int(ea - g * kChunk);
-#pragma unroll
-                for (int k = 0; k < kLaneEntries; ++k) {
-                    const int kk = k0 + k;
-                    r[k] = (meta & kMetaWalk) ? (k < nv ? entry_row(ea + k, K, off, chunk_row, chunk_meta) : r0)
-                                              : r0 + int32_t(kk ? unsigned(meta >> (8 * kk)) & 0xFFu : 0u);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kLaneEntries; ++k) r[k] = INT32_MAX;
-            }
+            // the next step's entries are requested before this step's work
+            LaneEntries nxt;
+            if (b + kStep < e1) load_lane(b + kStep, e1, lane, K, off, chunk_row, chunk_meta, adj, w, vec, nxt);
+            const int nv = le.nv;
             float vx[kLaneEntries], vy[kLaneEntries];
 #pragma unroll
             for (int k = 0; k < kLaneEntries; ++k) {
                 vx[k] = 0.0f;
                 vy[k] = 0.0f;
-                if (k < nv && static_cast<uint64_t>(j[k]) < static_cast<uint64_t>(K)) {  // else an invalid entry
-                    const float2 pj = pos[j[k]], pi = pos[r[k]];
-                    const float wf = __uint2float_rn(wt[k]);
+                if (k < nv && static_cast<uint64_t>(le.j[k]) < static_cast<uint64_t>(K)) {  // else an invalid entry
+                    const float2 pj = pos[le.j[k]], pi = pos[le.r[k]];
+                    const float wf = __uint2float_rn(le.wt[k]);
                     vx[k] = wf * (pj.x - pi.x);
                     vy[k] = wf * (pj.y - pi.y);
                 }
             }
             // In-lane runs: the first row's run (ra, pa), rows complete inside
             // the lane (written at once), the last row's run (rb, pb).
-            const int32_t ra = r[0], rb = nv > 0 ? r[nv - 1] : INT32_MAX;
+            const int32_t ra = le.r[0];
+            int32_t rb = INT32_MAX;
+#pragma unroll
+            for (int k = 0; k < kLaneEntries; ++k)
+                if (k < nv) rb = le.r[k];
             float pax = 0.0f, pay = 0.0f, pbx = 0.0f, pby = 0.0f;
             {
                 int32_t cur = ra;
@@ -693,14 +716,14 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
 #pragma unroll
                 for (int k = 0; k < kLaneEntries; ++k) {
                     if (k < nv) {
-                        if (r[k] != cur) {
+                        if (le.r[k] != cur) {
                             if (cur == ra) {
                                 pax = ax;
                                 pay = ay;
                             } else {
                                 put_piece(false, false, began, goes_on, q, cur, ax, ay, full, head, tail);
                             }
-                            cur = r[k];
+                            cur = le.r[k];
                             ax = 0.0f;
                             ay = 0.0f;
                         }
@@ -752,6 +775,7 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
             crow = __shfl_sync(0xFFFFFFFFu, rb, L);
             cx = __shfl_sync(0xFFFFFFFFu, pbx, L);
             cy = __shfl_sync(0xFFFFFFFFu, pby, L);
+            le = nxt;
         }
         if (lane == 0) put_piece(crow == row_first, true, began, goes_on, q, crow, cx, cy, full, head, tail);
     }

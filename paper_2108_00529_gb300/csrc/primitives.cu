@@ -232,8 +232,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_offsets(uint32_t *counts,
     }
 }
 
+// With 8 keys per thread, 4 blocks fit on an SM (registers capped at 64), so
+// the ~480 tiles of a million keys run in one wave, and the scatter goes
+// through shared memory: keys are first placed in digit order inside the
+// tile, then written out so that neighbouring threads write neighbouring
+// addresses of one digit's run.
 template <bool kVals, int kItems>
-__global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned long long *__restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_onesweep(const unsigned long long *__restrict__ kin,
                                                                 unsigned long long *__restrict__ kout,
                                                                 const uint32_t *__restrict__ vin,
                                                                 uint32_t *__restrict__ vout, int64_t cap,
@@ -242,8 +247,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
                                                                 unsigned int *tile_counter,
                                                                 unsigned long long *status, uint32_t *dev_status,
                                                                 unsigned long long tag) {
+    constexpr bool kStage = kItems <= 8;
+    constexpr int kTileKeys = kSortThreads * kItems;
     __shared__ uint32_t cnt[kSortWarps][kBins];
     __shared__ uint32_t tile_base[kBins];
+    __shared__ uint32_t local_start[kBins];
+    __shared__ unsigned long long skey[kStage ? kTileKeys : 1];
+    __shared__ uint32_t sval[kStage && kVals ? kTileKeys : 1];
     __shared__ unsigned int tile_sh;
     if (threadIdx.x == 0) tile_sh = atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kSortWarps * kBins; i += kSortThreads) (&cnt[0][0])[i] = 0;
@@ -303,6 +313,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
             cnt[w][d] = total;
             total += c;
         }
+        if (kStage) {
+            uint32_t all;
+            local_start[d] = block_exclusive(total, &all);
+        }
         volatile unsigned long long *st = status;
         unsigned long long excl = 0;
         if (tile == 0) {
@@ -346,6 +360,28 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_onesweep(const unsigned l
         tile_base[d] = digit_base[d] + uint32_t(excl);
     }
     __syncthreads();
+    if (kStage) {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int64_t i = base + int64_t(k) * 32 + lane;
+            if (i >= n) continue;
+            const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+            const uint32_t slot = local_start[d] + cnt[warp][d] + rank[k];
+            skey[slot] = key[k];
+            if (kVals) sval[slot] = val[k];
+        }
+        __syncthreads();
+        const int64_t t0 = tile * kTileKeys;
+        const int tile_n = n - t0 < kTileKeys ? int(n - t0) : kTileKeys;
+        for (int slot = threadIdx.x; slot < tile_n; slot += kSortThreads) {
+            const unsigned long long k = skey[slot];
+            const uint32_t d = static_cast<uint32_t>(k >> shift) & 0xFFu;
+            const uint32_t pos = tile_base[d] + uint32_t(slot) - local_start[d];
+            kout[pos] = k;
+            if (kVals) vout[pos] = sval[slot];
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int64_t i = base + int64_t(k) * 32 + lane;
