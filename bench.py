@@ -657,6 +657,65 @@ def gpu_arm_batched(args, dist: Dist):
     }
 
 
+def gpu_sweep(args, dist: Dist):
+    """Parameter sweep of the edge stages on the workload (the paper's Tables
+    2 and 3: sketch rows and community rounds; and the community variants):
+    per setting, the time of sketch + rounds + supergraph, the supernode and
+    superedge counts, and the modularity of the labels."""
+    import torch
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    from paper_2108_00529_gb300 import build
+    build.build()
+    from paper_2108_00529_gb300 import load
+    B = load()
+    cfg = WORKLOADS[args.workload]
+    n, edges_np, _ = graphgen.load(args.workload)
+    m = edges_np.shape[0]
+    width = cfg["width"]
+    s = torch.cuda.Stream(device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    E = torch.from_numpy(edges_np).to(dev)
+    S = torch.zeros(16 * width, **i32)
+    dh, labels, node_map = torch.zeros(n, **i32), torch.zeros(n, **i32), torch.zeros(n, **i32)
+    Kd, Esd = torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev)
+    ssrc, sdst, sw = (torch.zeros(m, **i32) for _ in range(3))
+    mass, off = torch.zeros(n, **i32), torch.zeros(n + 1, **i32)
+    adj, cw = torch.zeros(2 * m, **i32), torch.zeros(2 * m, **i32)
+    ws_sk = B.alloc_ws(B.bgv_sketch_degrees_ws_size(m, n, 4, width), dev)
+    ws_cm = B.alloc_ws(B.bgv_communities_ex_ws_size(m, n), dev)
+    ws_sg = B.alloc_ws(B.bgv_supergraph_ws_size(m, n, 4, width), dev)
+    ws_q = B.alloc_ws(B.bgv_modularity_ws_size(n), dev)
+    settings = [dict(rows=r, passes=3, growth=2, tmode=0, jumps=0) for r in (1, 2, 3, 4)]
+    settings += [dict(rows=4, passes=p, growth=2, tmode=0, jumps=0) for p in (2, 4)]
+    settings += [dict(rows=4, passes=3, growth=2, tmode=1, jumps=0), dict(rows=4, passes=3, growth=0, tmode=1, jumps=0),
+                 dict(rows=4, passes=3, growth=2, tmode=0, jumps=2)]
+    out = []
+    for st in settings:
+        times = []
+        for rep in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s):
+                e0.record(s)
+                B.bgv_sketch_degrees(E, m, n, st["rows"], width, 1, S, dh, ws_sk, stream=s)
+                D = B.bgv_communities_ex(E, m, n, dh, st["passes"], 0, st["growth"], 0, st["tmode"], st["jumps"],
+                                         labels, None, ws_cm, stream=s)
+                B.bgv_supergraph(E, m, n, labels, dh, st["rows"], width, 1, node_map, Kd, ssrc, sdst, sw, Esd, mass,
+                                 off, adj, cw, None, None, None, ws_sg, stream=s)
+                e1.record(s)
+            s.synchronize()
+            if rep:
+                times.append(e0.elapsed_time(e1))
+        q = B.bgv_modularity(E, m, n, labels, ws_q, stream=s)
+        out.append({**st, "threshold": D, "edge_stage_ms": round(float(np.median(times)), 3), "K": int(Kd.item()),
+                    "Es": int(Esd.item()), "modularity": round(q, 4)})
+    return {"sweep": f"{args.workload}: {cfg['desc']}", "sketch_width": width, "n": n, "m": m,
+            "note": "tmode 1 = mode-degree threshold; growth 0 = delta^i schedule; jumps = pointer-jumping steps "
+                    "per round; the time of a mode-degree setting includes the read-back of the mode",
+            "settings": out}
+
+
 def reference_arm_batched(args, dist: Dist):
     """The oracle on the batching workload: graphs taken in a fixed strided
     order (every 32nd, so small and large ones alike) until about 10 s of
@@ -738,6 +797,8 @@ def main():
                     help="override the workload's FA2 iteration count (short profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the timed step: sketch rows, rounds and community variants on the workload")
     ap.add_argument("--no-per-graph", action="store_true",
                     help="batched workload: skip the one-call-per-graph comparison")
     ap.add_argument("--precision-sample", type=int, default=0,
@@ -749,6 +810,8 @@ def main():
     try:
         if args.impl == "reference":
             out = reference_arm(args, dist)
+        elif args.sweep:
+            out = gpu_sweep(args, dist)
         elif WORKLOADS[args.workload].get("whole"):
             out = gpu_arm_whole(args, dist)
         elif WORKLOADS[args.workload].get("batched"):

@@ -132,15 +132,50 @@ int bgv_sketch_degrees_noalloc(const int32_t *edges, int64_t m, int32_t n, int32
  * the other's label; on equal degrees nothing happens (tie_mode 0) or the
  * lower id takes the higher id's label (tie_mode 1).  At the end of the
  * round each node with proposals takes the one from the lowest edge index
- * and its degree grows by 1 (saturating).  Then D = min(D * growth, 2^32-1).
+ * and its degree grows by 1 (saturating).  Then D = min(D * growth, 2^32-1);
+ * growth 0 multiplies by the first round's D instead, so round i uses D^i
+ * (the delta^i schedule of Section 4.2.2).
  *   deg_est  [n] uint32 (in)     labels [n] int32 (out)
  *   deg_out  [n] uint32 (out, optional: final degrees, may be NULL)
- * Limits: passes >= 0, growth >= 1, tie_mode in {0, 1}.
+ * Limits: passes >= 0, tie_mode in {0, 1}.
  * ---------------------------------------------------------------------- */
 size_t bgv_communities_ws_size(int64_t m, int32_t n);
 int bgv_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est,
                     int32_t passes, uint32_t threshold, uint32_t growth, int32_t tie_mode,
                     int32_t *labels, uint32_t *deg_out, void *ws, size_t ws_bytes, void *stream);
+
+/* Variants of the rounds.  threshold_mode 1 with threshold 0 starts from the
+ * mode degree (Section 4.2.2 follows SCoDA in taking the most common degree):
+ * the most frequent nonzero value of deg_est, ties to the smaller, computed
+ * on the device and read back once (the call synchronises `stream` then).
+ * (bgv_layout with threshold_mode 1 takes the mode of the exact degrees,
+ * which it counts anyway for the sketch.)
+ * jumps (0..64) synchronous pointer-jumping steps follow every round: each
+ * label becomes its label's label, all read before the step.  The first
+ * round's threshold is returned in *threshold_out (host, may be NULL).
+ * Other arguments as bgv_communities. */
+size_t bgv_communities_ex_ws_size(int64_t m, int32_t n);
+int bgv_communities_ex(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
+                       uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t threshold_mode, int32_t jumps,
+                       int32_t *labels, uint32_t *deg_out, uint32_t *threshold_out, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/* Mode degree of deg [n] (device uint32): the most frequent value among the
+ * nonzero ones, ties to the smaller, 0 if all are 0; returned in *mode_out
+ * (host).  Synchronises `stream`. */
+size_t bgv_mode_degree_ws_size(int32_t n);
+int bgv_mode_degree(const uint32_t *deg, int32_t n, uint32_t *mode_out, void *ws, size_t ws_bytes, void *stream);
+
+/* Modularity of a labelling (the quality the paper reports for its
+ * communities, Table 1 column M): Q = sum over labels c of in_c / 2m -
+ * (vol_c / 2m)^2, in_c twice the edges with both endpoints labelled c, vol_c
+ * the number of endpoints labelled c.  Counted as exact integers and
+ * combined in one FP64 division, so Q does not depend on thread order.
+ * labels [n] int32 (device, values in [0, n)); *q_out host double.
+ * Synchronises `stream`. */
+size_t bgv_modularity_ws_size(int32_t n);
+int bgv_modularity(const int32_t *edges, int64_t m, int32_t n, const int32_t *labels, double *q_out, void *ws,
+                   size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * 3. Supergraph (Section 4.1; Algorithm 3, "compute community sizes" and
@@ -193,6 +228,19 @@ int bgv_graph_csr(const int32_t *edges, int64_t m, int32_t n, int32_t *csr_off, 
 size_t bgv_colour_groups_ws_size(int64_t K);
 int bgv_colour_groups(int64_t K, const uint32_t *sizes, uint8_t *group, int32_t n, const int32_t *node_map,
                       uint8_t *node_colour, void *ws, size_t ws_bytes, void *stream);
+
+/* Drawing: discs of radius[k] (sqrt of the size, Section 4.1) at xy[k] in
+ * the colour of group[k] (Section 4.3: 0 brown, 1..10 light purple, purple,
+ * light orange, orange, light red, red, light green, green, light blue,
+ * blue), into rgba [H][W][4] uint8 (device, row-major, 4-byte aligned,
+ * background white, alpha 255).  The discs' bounding box maps to the image
+ * with one scale s = min(W, H) / largest extent from its low corner; pixel
+ * (px, py) takes the disc whose scaled circle covers (px + 0.5, py + 0.5);
+ * where discs overlap the smaller radius wins, then the smaller index.
+ * Coverage is decided in FP32 with round-to-nearest steps.  W, H <= 32768. */
+size_t bgv_render_ws_size(int32_t W, int32_t H);
+int bgv_render(int64_t K, const float *xy, const float *radius, const uint8_t *group, int32_t W, int32_t H,
+               uint8_t *rgba, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * 4. ForceAtlas2 (Section 3.1; Algorithm 1; the force model and adaptive
@@ -303,8 +351,10 @@ typedef struct bgv_layout_params {
     uint64_t seed;       /* hash seed (1) */
     int32_t passes;      /* community rounds (3) */
     uint32_t threshold;  /* degree threshold; 0 = floor(2m / n) (0) */
-    uint32_t growth;     /* threshold factor per round (2) */
+    uint32_t growth;     /* threshold factor per round; 0 = the first threshold (delta^i) (2) */
     int32_t tie_mode;    /* 0 or 1 (0) */
+    int32_t threshold_mode; /* with threshold 0: 0 = floor(2m / n), 1 = the graph's most common degree (0) */
+    int32_t jumps;       /* pointer-jumping steps after every round, 0..64 (0) */
     int32_t iterations;  /* ForceAtlas2 steps (200) */
     int32_t use_graph;   /* replay the FA2 step as a CUDA graph (1) */
     bgv_fa2_params fa2;
@@ -382,6 +432,29 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
                         const int32_t *csr_adj, const uint32_t *csr_w, const uint32_t *mass,
                         const bgv_fa2_params *p, int32_t iterations, int32_t use_graph, float *pos, float *F,
                         float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * 7. Autotuner.  The radix sort of the supergraph and ForceAtlas2 stages
+ *    runs 8 keys per thread up to a size cutoff and 16 above it (one CTA
+ *    wave of small tiles against fewer, larger tiles).  bgv_autotune_sort
+ *    times both on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
+ *    keys with 32-bit values, SplitMix64 of the index) and sets the cutoff
+ *    to the largest size at which 8 was not slower.  The cutoff is process
+ *    wide and starts at 2^22; workspaces stay valid whatever it is.
+ *    Synchronises `stream` once per timed sort.  The paper has no
+ *    counterpart.
+ * ---------------------------------------------------------------------- */
+typedef struct bgv_tune_report {
+    int32_t count;          /* sizes timed */
+    int32_t sizes_log2[9];  /* log2 of each size */
+    float ms8[9];           /* median milliseconds, 8 keys per thread */
+    float ms16[9];          /* median milliseconds, 16 keys per thread */
+    int64_t cutoff;         /* the cutoff now in force */
+} bgv_tune_report;
+
+size_t bgv_autotune_sort_ws_size(int64_t max_keys);
+int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t ws_bytes, void *stream);
+int64_t bgv_sort_cutoff(void);
 
 #ifdef __cplusplus
 }

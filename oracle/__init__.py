@@ -69,6 +69,14 @@ def lib():
         L.orc_sketch_degrees.argtypes = [P, i64, i32, i32, i32, u64, P, P]
         L.orc_communities.restype = C.c_int
         L.orc_communities.argtypes = [P, i64, i32, P, i32, u32, u32, i32, P, P]
+        L.orc_communities_ex.restype = C.c_int
+        L.orc_communities_ex.argtypes = [P, i64, i32, P, i32, u32, u32, i32, i32, P, P]
+        L.orc_mode_degree.restype = C.c_int
+        L.orc_mode_degree.argtypes = [P, i32, C.POINTER(u32)]
+        L.orc_render.restype = C.c_int
+        L.orc_render.argtypes = [i64, P, P, P, i32, i32, P]
+        L.orc_scoda_sequential.restype = C.c_int
+        L.orc_scoda_sequential.argtypes = [P, i64, i32, u32, P]
         L.orc_supergraph.restype = C.c_int
         L.orc_supergraph.argtypes = [P, i64, i32, P, P, i32, i32, u64, P, P, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_modularity.restype = f64
@@ -158,6 +166,37 @@ def communities(edges, n: int, dhat, passes: int, threshold: int, growth: int = 
     deg = np.zeros(max(n, 1), np.uint32)
     _chk(lib().orc_communities(_p(e), m, n, _p(dh), passes, threshold, growth, tie_mode, _p(lab), _p(deg)))
     return lab[:n], deg[:n]
+
+
+def communities_ex(edges, n: int, dhat, passes: int, threshold: int, growth: int, tie_mode: int, jumps: int):
+    """Community rounds with the variants: ``growth`` 0 multiplies the
+    threshold by its first value each round (the delta^i schedule), and
+    ``jumps`` pointer-jumping steps follow every round.  Returns
+    ``(labels, degrees)``."""
+    e, m = _edges(edges)
+    dh = np.ascontiguousarray(dhat, dtype=np.uint32)
+    lab = np.zeros(max(n, 1), np.int32)
+    deg = np.zeros(max(n, 1), np.uint32)
+    _chk(lib().orc_communities_ex(_p(e), m, n, _p(dh), passes, threshold, growth, tie_mode, jumps, _p(lab),
+                                  _p(deg)))
+    return lab[:n], deg[:n]
+
+
+def mode_degree(dhat) -> int:
+    """Most frequent value of dhat among nodes with dhat >= 1 (ties: the
+    smaller value; 0 if there is none)."""
+    dh = np.ascontiguousarray(dhat, dtype=np.uint32)
+    out = C.c_uint32(0)
+    _chk(lib().orc_mode_degree(_p(dh), dh.shape[0], C.byref(out)))
+    return int(out.value)
+
+
+def scoda_sequential(edges, n: int, D: int):
+    """Sequential SCoDA (one ordered pass, degrees from 0); returns labels."""
+    e, m = _edges(edges)
+    lab = np.zeros(max(n, 1), np.int32)
+    _chk(lib().orc_scoda_sequential(_p(e), m, n, D, _p(lab)))
+    return lab[:n]
 
 
 def supergraph(edges, n: int, labels, dhat, rows: int, width: int, seed: int):
@@ -348,3 +387,14 @@ def layout(K: int, csr_off, csr_adj, csr_w, mass, params: FA2Params, iterations:
     for _ in range(iterations):
         fa2_step(st, csr_off, csr_adj, csr_w, mass, params)
     return st
+
+
+def render(xy, radius, group, W: int, H: int):
+    """RGBA image [H][W][4] uint8 of the discs (Section 4.1 radii, Section 4.3
+    colour groups), pixel by pixel over all discs."""
+    xy = np.ascontiguousarray(np.asarray(xy, np.float32).reshape(-1, 2))
+    r = np.ascontiguousarray(radius, dtype=np.float32)
+    g = np.ascontiguousarray(group, dtype=np.uint8)
+    out = np.zeros((H, W, 4), np.uint8)
+    _chk(lib().orc_render(xy.shape[0], _p(xy), _p(r), _p(g), W, H, _p(out)))
+    return out

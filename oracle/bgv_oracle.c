@@ -141,11 +141,56 @@ int orc_sketch_degrees(const int32_t *edges, int64_t m, int32_t n, int32_t rows,
  *   proposal of the lowest edge index and its degree grows by one
  *   (saturating).  Then D = min(D * growth, 2^32 - 1) (Section 3.2.1: the
  *   threshold is multiplied by a constant factor each round). */
-int orc_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *dhat, int32_t passes,
-                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels,
-                    uint32_t *deg_out)
+/* Mode degree (Section 4.2.2 "Community Detection": the most common degree
+ * is the threshold SCoDA suggests): the most frequent value of dhat among
+ * nodes with dhat >= 1; ties go to the smaller value; 0 when every dhat is
+ * 0. */
+static int cmp_u32(const void *x, const void *y)
 {
-    if (n < 0 || m < 0 || passes < 0 || (tie_mode != 0 && tie_mode != 1)) return ORC_EINVAL;
+    uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
+    return (a > b) - (a < b);
+}
+
+int orc_mode_degree(const uint32_t *dhat, int32_t n, uint32_t *mode)
+{
+    if (n < 0 || !mode) return ORC_EINVAL;
+    uint32_t *v = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!v) return ORC_ENOMEM;
+    int32_t k = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (dhat[i] >= 1) v[k++] = dhat[i];
+    /* sort, then the longest run of equal values; runs are met in ascending
+     * value order, so a strict improvement keeps the smaller value on ties */
+    qsort(v, (size_t)k, sizeof(uint32_t), cmp_u32);
+    uint32_t best = 0;
+    int64_t best_count = 0;
+    for (int32_t i = 0; i < k;) {
+        int32_t j = i;
+        while (j < k && v[j] == v[i]) ++j;
+        if (j - i > best_count) {
+            best = v[i];
+            best_count = j - i;
+        }
+        i = j;
+    }
+    free(v);
+    *mode = best;
+    return ORC_OK;
+}
+
+/* Community passes (Algorithm 3 lines 8-22; Section 3.2.1).
+ * Readings: degrees start at the sketched dhat and a node's degree grows by
+ * one when it moves; both endpoints must be <= D; every edge reads the state
+ * at the start of the pass, and a node with several proposals takes the one
+ * of the lowest edge index; D <- min(D * growth, 2^32 - 1) after each pass,
+ * with growth 0 meaning "multiply by the first-pass threshold", i.e. the
+ * delta^i schedule of Section 4.2.2.  After each pass, `jumps` synchronous
+ * pointer-jumping steps replace every label by its label's label. */
+int orc_communities_ex(const int32_t *edges, int64_t m, int32_t n, const uint32_t *dhat, int32_t passes,
+                       uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t jumps, int32_t *labels,
+                       uint32_t *deg_out)
+{
+    if (n < 0 || m < 0 || passes < 0 || jumps < 0 || (tie_mode != 0 && tie_mode != 1)) return ORC_EINVAL;
     if (check_edges(edges, m, n)) return ORC_EBADEDGE;
     uint32_t *d = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     int64_t *prop_e = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -159,6 +204,7 @@ int orc_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
         d[v] = dhat[v];
     }
     uint64_t D = threshold;
+    const uint64_t factor = growth ? growth : threshold;
     for (int32_t p = 0; p < passes; ++p) {
         for (int32_t v = 0; v < n; ++v) prop_e[v] = -1;
         for (int64_t e = 0; e < m; ++e) {
@@ -188,11 +234,50 @@ int orc_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
                 if (d[v] != UINT32_MAX) d[v] += 1;
             }
         }
-        D = D * (uint64_t)growth;
+        for (int32_t j = 0; j < jumps; ++j) {
+            for (int32_t v = 0; v < n; ++v) prop_l[v] = labels[labels[v]];
+            memcpy(labels, prop_l, sizeof(int32_t) * (size_t)n);
+        }
+        D = D * factor;
         if (D > UINT32_MAX) D = UINT32_MAX;
     }
     if (deg_out) memcpy(deg_out, d, sizeof(uint32_t) * (size_t)n);
     free(d); free(prop_e); free(prop_l);
+    return ORC_OK;
+}
+
+int orc_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *dhat, int32_t passes,
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels,
+                    uint32_t *deg_out)
+{
+    if (growth < 1) return ORC_EINVAL;
+    return orc_communities_ex(edges, m, n, dhat, passes, threshold, growth, tie_mode, 0, labels, deg_out);
+}
+
+/* Sequential SCoDA (Hollocou et al. 2017, as Section 3.2 describes it): one
+ * pass over the edges in order, every node starting at degree 0 in its own
+ * community; each edge first increments both endpoint degrees, then, if
+ * both are at most D, the endpoint of smaller degree joins the community of
+ * the other (ties: the first endpoint joins the second's).  The prior art
+ * the GPU rounds replace; used to compare community quality. */
+int orc_scoda_sequential(const int32_t *edges, int64_t m, int32_t n, uint32_t D, int32_t *labels)
+{
+    if (n < 0 || m < 0) return ORC_EINVAL;
+    if (check_edges(edges, m, n)) return ORC_EBADEDGE;
+    uint32_t *d = (uint32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(uint32_t));
+    if (!d) return ORC_ENOMEM;
+    for (int32_t v = 0; v < n; ++v) labels[v] = v;
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t u = edges[2 * e], v = edges[2 * e + 1];
+        if (u == v) continue;
+        d[u] += 1;
+        d[v] += 1;
+        if (d[u] <= D && d[v] <= D) {
+            if (d[u] > d[v]) labels[v] = labels[u];
+            else labels[u] = labels[v];
+        }
+    }
+    free(d);
     return ORC_OK;
 }
 
@@ -864,5 +949,70 @@ int orc_colour_groups(int64_t K, const uint32_t *size, uint8_t *group)
         else group[k] = (uint8_t)(1 + (10 * (r - half)) / rest);
     }
     free(order);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Drawing the supergraph (Section 4.1: radius proportional to the square   */
+/* root of the size; Section 4.3: eleven colour groups) into an RGBA image.  */
+/* ------------------------------------------------------------------------ */
+
+/* Reading: the image maps the discs' bounding box [min(x - r), max(x + r)]
+ * to the W x H pixels with one scale s = min(W, H) / (largest extent) (1 if
+ * the extent is 0), origin at the box's low corner.  Pixel (px, py) shows
+ * the disc whose centre (u, v) = ((x - lo_x) s, (y - lo_y) s) and radius
+ * r s cover its centre (px + 0.5, py + 0.5): (px + 0.5 - u)^2 + (py + 0.5 -
+ * v)^2 <= (r s)^2.  Where discs overlap the smaller radius is drawn on top,
+ * equal radii by the smaller id, so small communities stay visible.  All in
+ * FP32, operation by operation.  Colours: group 0 brown, groups 1..10 light
+ * purple, purple, light orange, orange, light red, red, light green, green,
+ * light blue, blue (the ColorBrewer "Paired" qualitative scheme); background
+ * white; alpha 255.  Pixel-centric brute force over all discs. */
+static const uint8_t orc_palette[11][3] = {
+    {177, 89, 40},   {202, 178, 214}, {106, 61, 154}, {253, 191, 111}, {255, 127, 0}, {251, 154, 153},
+    {227, 26, 28},   {178, 223, 138}, {51, 160, 44},  {166, 206, 227}, {31, 120, 180}};
+
+int orc_render(int64_t K, const float *xy, const float *radius, const uint8_t *group, int32_t W, int32_t H,
+               uint8_t *rgba)
+{
+    if (K < 0 || W < 1 || H < 1) return ORC_EINVAL;
+    float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
+    for (int64_t k = 0; k < K; ++k) {
+        float x = xy[2 * k], y = xy[2 * k + 1], r = radius[k];
+        float a = x - r, b = y - r, c = x + r, d = y + r;
+        if (a < lx) lx = a;
+        if (b < ly) ly = b;
+        if (c > hx) hx = c;
+        if (d > hy) hy = d;
+    }
+    float ex = hx - lx, ey = hy - ly;
+    float ext = ex > ey ? ex : ey;
+    float s = (K > 0 && ext > 0.0f) ? (float)(W < H ? W : H) / ext : 1.0f;
+    for (int32_t py = 0; py < H; ++py) {
+        for (int32_t px = 0; px < W; ++px) {
+            int64_t best = -1;
+            float best_r = 0.0f;
+            float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
+            for (int64_t k = 0; k < K; ++k) {
+                float u = (xy[2 * k] - lx) * s, v = (xy[2 * k + 1] - ly) * s, rs = radius[k] * s;
+                float dx = cx - u, dy = cy - v;
+                float d2 = dx * dx + dy * dy;
+                if (d2 <= rs * rs) {
+                    if (best < 0 || radius[k] < best_r) {  /* k ascends, so ties keep the smaller id */
+                        best = k;
+                        best_r = radius[k];
+                    }
+                }
+            }
+            uint8_t *o = rgba + 4 * ((size_t)py * (size_t)W + (size_t)px);
+            if (best < 0) {
+                o[0] = o[1] = o[2] = 255;
+            } else {
+                const uint8_t *c = orc_palette[group[best] <= 10 ? group[best] : 0];
+                o[0] = c[0]; o[1] = c[1]; o[2] = c[2];
+            }
+            o[3] = 255;
+        }
+    }
     return ORC_OK;
 }

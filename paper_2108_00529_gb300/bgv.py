@@ -37,10 +37,15 @@ class bgv_fa2_stats(C.Structure):
                 ("interactions_total", u64), ("steps_total", u64), ("status", u32), ("reserved", u32)]
 
 
+class bgv_tune_report(C.Structure):
+    _fields_ = [("count", i32), ("sizes_log2", i32 * 9), ("ms8", C.c_float * 9), ("ms16", C.c_float * 9),
+                ("cutoff", i64)]
+
+
 class bgv_layout_params(C.Structure):
     _fields_ = [("rows", i32), ("width", i32), ("seed", u64), ("passes", i32), ("threshold", u32),
-                ("growth", u32), ("tie_mode", i32), ("iterations", i32), ("use_graph", i32),
-                ("fa2", bgv_fa2_params)]
+                ("growth", u32), ("tie_mode", i32), ("threshold_mode", i32), ("jumps", i32), ("iterations", i32),
+                ("use_graph", i32), ("fa2", bgv_fa2_params)]
 
 
 def _sig(name, res, args):
@@ -59,12 +64,20 @@ _sig("bgv_sketch_degrees", C.c_int, [P, i64, i32, i32, i32, u64, P, P, P, sz, P]
 _sig("bgv_sketch_degrees_noalloc", C.c_int, [P, i64, i32, i32, i32, u64, P, P, P, P])
 _sig("bgv_communities_ws_size", sz, [i64, i32])
 _sig("bgv_communities", C.c_int, [P, i64, i32, P, i32, u32, u32, i32, P, P, P, sz, P])
+_sig("bgv_communities_ex_ws_size", sz, [i64, i32])
+_sig("bgv_communities_ex", C.c_int, [P, i64, i32, P, i32, u32, u32, i32, i32, i32, P, P, C.POINTER(u32), P, sz, P])
+_sig("bgv_mode_degree_ws_size", sz, [i32])
+_sig("bgv_mode_degree", C.c_int, [P, i32, C.POINTER(u32), P, sz, P])
+_sig("bgv_modularity_ws_size", sz, [i32])
+_sig("bgv_modularity", C.c_int, [P, i64, i32, P, C.POINTER(C.c_double), P, sz, P])
 _sig("bgv_supergraph_ws_size", sz, [i64, i32, i32, i32])
 _sig("bgv_supergraph", C.c_int, [P, i64, i32, P, P, i32, i32, u64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, sz, P])
 _sig("bgv_graph_csr_ws_size", sz, [i64, i32])
 _sig("bgv_graph_csr", C.c_int, [P, i64, i32, P, P, P, P, P, P, sz, P])
 _sig("bgv_colour_groups_ws_size", sz, [i64])
 _sig("bgv_colour_groups", C.c_int, [i64, P, P, i32, P, P, P, sz, P])
+_sig("bgv_render_ws_size", sz, [i32, i32])
+_sig("bgv_render", C.c_int, [i64, P, P, P, i32, i32, P, P, sz, P])
 _sig("bgv_fa2_default_params", None, [C.POINTER(bgv_fa2_params)])
 _sig("bgv_fa2_init", C.c_int, [i64, C.POINTER(bgv_fa2_params), P, P, P, P])
 _sig("bgv_fa2_ws_size", sz, [i64, i64])
@@ -91,14 +104,22 @@ _sig("bgv_fa2_forces_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_
 _sig("bgv_fa2_run_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P,
                                       sz, P])
 
+_sig("bgv_autotune_sort_ws_size", sz, [i64])
+_sig("bgv_autotune_sort", C.c_int, [i64, C.POINTER(bgv_tune_report), P, sz, P])
+_sig("bgv_sort_cutoff", i64, [])
+
 #: every symbol this binding resolves from the library
 EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees", "bgv_sketch_degrees_noalloc",
-           "bgv_communities_ws_size", "bgv_communities", "bgv_supergraph_ws_size", "bgv_supergraph",
+           "bgv_communities_ws_size", "bgv_communities", "bgv_communities_ex_ws_size", "bgv_communities_ex",
+           "bgv_mode_degree_ws_size", "bgv_mode_degree", "bgv_modularity_ws_size", "bgv_modularity",
+           "bgv_supergraph_ws_size", "bgv_supergraph",
            "bgv_graph_csr_ws_size", "bgv_graph_csr", "bgv_colour_groups_ws_size", "bgv_colour_groups",
+           "bgv_render_ws_size", "bgv_render",
            "bgv_fa2_default_params", "bgv_fa2_init", "bgv_fa2_ws_size", "bgv_fa2_forces", "bgv_fa2_step",
            "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
            "bgv_layout_host_ws_size", "bgv_layout_host", "bgv_layout_batched_ws_size", "bgv_layout_batched",
-           "bgv_fa2_ws_size_batched", "bgv_fa2_init_batched", "bgv_fa2_forces_batched", "bgv_fa2_run_batched"]
+           "bgv_fa2_ws_size_batched", "bgv_fa2_init_batched", "bgv_fa2_forces_batched", "bgv_fa2_run_batched",
+           "bgv_autotune_sort_ws_size", "bgv_autotune_sort", "bgv_sort_cutoff"]
 
 
 class BgvError(RuntimeError):
@@ -188,6 +209,42 @@ def bgv_communities(edges, m, n, deg_est, passes, threshold, growth, tie_mode, l
                               _p(deg_out), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_communities")
 
 
+def bgv_communities_ex_ws_size(m: int, n: int) -> int:
+    return _lib.bgv_communities_ex_ws_size(m, n)
+
+
+def bgv_communities_ex(edges, m, n, deg_est, passes, threshold, growth, tie_mode, threshold_mode, jumps, labels,
+                       deg_out, ws, ws_bytes=None, stream=None) -> int:
+    """Returns the first round's threshold."""
+    D = u32(0)
+    _chk(_lib.bgv_communities_ex(_p(edges), m, n, _p(deg_est), passes, threshold, growth, tie_mode, threshold_mode,
+                                 jumps, _p(labels), _p(deg_out), C.byref(D), _p(ws), _nbytes(ws, ws_bytes),
+                                 _s(stream)), "bgv_communities_ex")
+    return D.value
+
+
+def bgv_mode_degree_ws_size(n: int) -> int:
+    return _lib.bgv_mode_degree_ws_size(n)
+
+
+def bgv_mode_degree(deg, n, ws, ws_bytes=None, stream=None) -> int:
+    out = u32(0)
+    _chk(_lib.bgv_mode_degree(_p(deg), n, C.byref(out), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_mode_degree")
+    return out.value
+
+
+def bgv_modularity_ws_size(n: int) -> int:
+    return _lib.bgv_modularity_ws_size(n)
+
+
+def bgv_modularity(edges, m, n, labels, ws, ws_bytes=None, stream=None) -> float:
+    q = C.c_double(0.0)
+    _chk(_lib.bgv_modularity(_p(edges), m, n, _p(labels), C.byref(q), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_modularity")
+    return q.value
+
+
 def bgv_supergraph_ws_size(m: int, n: int, rows: int, width: int) -> int:
     return _lib.bgv_supergraph_ws_size(m, n, rows, width)
 
@@ -216,6 +273,15 @@ def bgv_colour_groups_ws_size(K: int) -> int:
 def bgv_colour_groups(K, sizes, group, ws, n=0, node_map=None, node_colour=None, ws_bytes=None, stream=None):
     _chk(_lib.bgv_colour_groups(K, _p(sizes), _p(group), n, _p(node_map), _p(node_colour), _p(ws),
                                 _nbytes(ws, ws_bytes), _s(stream)), "bgv_colour_groups")
+
+
+def bgv_render_ws_size(W: int, H: int) -> int:
+    return _lib.bgv_render_ws_size(W, H)
+
+
+def bgv_render(K, xy, radius, group, W, H, rgba, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_render(K, _p(xy), _p(radius), _p(group), W, H, _p(rgba), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_render")
 
 
 def bgv_fa2_default_params() -> bgv_fa2_params:
@@ -352,3 +418,18 @@ def bgv_fa2_run_batched(G, koff, nnz, csr_off, csr_adj, csr_w, mass, params, ite
     _chk(_lib.bgv_fa2_run_batched(G, pk, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params),
                                   iterations, use_graph, _p(pos), _p(F), _p(Fprev), _p(speed), _p(ws),
                                   _nbytes(ws, ws_bytes), _s(stream)), "bgv_fa2_run_batched")
+
+
+def bgv_autotune_sort_ws_size(max_keys: int) -> int:
+    return _lib.bgv_autotune_sort_ws_size(max_keys)
+
+
+def bgv_autotune_sort(max_keys, ws, ws_bytes=None, stream=None) -> bgv_tune_report:
+    r = bgv_tune_report()
+    _chk(_lib.bgv_autotune_sort(max_keys, C.byref(r), _p(ws), _nbytes(ws, ws_bytes), _s(stream)),
+         "bgv_autotune_sort")
+    return r
+
+
+def bgv_sort_cutoff() -> int:
+    return _lib.bgv_sort_cutoff()

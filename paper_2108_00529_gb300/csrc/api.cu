@@ -58,6 +58,7 @@ size_t super_ws(int64_t m, int32_t n, int32_t rows, int32_t width) {
 // ------------------------------------------------------------- pipeline
 struct LayoutBuffers {
     uint32_t *sketch, *deg_est;
+    uint32_t *mode;  // first-round threshold from the mode degree
     int32_t *labels;
     int64_t *K_dev, *Es_dev;
     int32_t *ssrc, *sdst;
@@ -72,9 +73,12 @@ struct LayoutBuffers {
 size_t stage_scratch_bytes(int64_t m, int32_t n, const bgv_layout_params *p, int32_t G = 1) {
     size_t need = 0;
     {
+        // the sketch's exact degree counters, then the mode degree from them
         Carver c(nullptr, 0);
         SketchScratch s;
         carve_sketch(c, m, n, p->rows, p->width, s);
+        ModeScratch ms;
+        carve_mode(c, n, G, ms);
         need = c.used() > need ? c.used() : need;
     }
     {
@@ -97,6 +101,7 @@ void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, L
     const size_t nn = size_t(n), mm = size_t(m > 0 ? m : 1), gg = size_t(G > 1 ? G : 1);
     b.sketch = c.take<uint32_t>(size_t(p->rows) * size_t(p->width) * gg);
     b.deg_est = c.take<uint32_t>(nn);
+    b.mode = c.take<uint32_t>(1);
     b.labels = c.take<int32_t>(nn);
     b.K_dev = c.take<int64_t>(1);
     b.Es_dev = c.take<int64_t>(1);
@@ -116,8 +121,8 @@ void carve_layout(Carver &c, int64_t m, int32_t n, const bgv_layout_params *p, L
 int check_layout_params(const bgv_layout_params *p) {
     if (!p) return BGV_EINVAL;
     BGV_TRY(check_sketch_shape(p->rows, p->width));
-    if (p->passes < 0 || p->growth < 1 || (p->tie_mode != 0 && p->tie_mode != 1) || p->iterations < 0)
-        return BGV_EINVAL;
+    if (p->passes < 0 || (p->tie_mode != 0 && p->tie_mode != 1) || p->iterations < 0) return BGV_EINVAL;
+    if ((p->threshold_mode != 0 && p->threshold_mode != 1) || p->jumps < 0 || p->jumps > 64) return BGV_EINVAL;
     return fa2_check_params(&p->fa2);
 }
 
@@ -208,6 +213,21 @@ __global__ void k_radius(const uint32_t *mass, const int64_t *K_dev, float *radi
         radius[k] = sqrtf(__uint2float_rn(mass[k]));
 }
 
+// First-round threshold from the mode of the sketched degrees (computed on
+// the device, read back once).
+int mode_threshold(const uint32_t *deg, int32_t n, uint32_t *mode_dev, void *scratch, uint32_t *status,
+                   cudaStream_t st, uint32_t *D) {
+    Carver c(scratch, 0);
+    ModeScratch ms;
+    carve_mode(c, n, 1, ms);
+    BGV_TRY(run_mode_degree(deg, n, nullptr, mode_dev, ms, status, st));
+    uint32_t h = 0;
+    BGV_CUDA(cudaMemcpyAsync(&h, mode_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BGV_CUDA(cudaStreamSynchronize(st));
+    *D = h;
+    return BGV_OK;
+}
+
 int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_params *p, int32_t *node_map,
                   float *xy, float *radius, int64_t *K_out, int64_t *Es_out, void *ws, cudaStream_t st,
                   LayoutBuffers &b) {
@@ -215,19 +235,28 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
     uint32_t *status = &hdr->status;
     const HashFamily h = make_hash_family(p->seed, p->rows, uint32_t(p->width));
     BGV_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
+    uint32_t D = p->threshold ? p->threshold : uint32_t((2 * m) / n);
     {
         Carver c(b.scratch, 0);
         SketchScratch s;
         carve_sketch(c, m, n, p->rows, p->width, s);
         BGV_TRY(run_sketch(edges, m, n, h, b.sketch, b.deg_est, s, status, st));
+        if (!p->threshold && p->threshold_mode == 1) {
+            // the most common degree of the graph (exact degrees, still in
+            // the sketch's counters)
+            ModeScratch ms;
+            carve_mode(c, n, 1, ms);
+            BGV_TRY(run_mode_degree(s.deg, n, nullptr, b.mode, ms, status, st));
+            BGV_CUDA(cudaMemcpyAsync(&D, b.mode, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            BGV_CUDA(cudaStreamSynchronize(st));
+        }
     }
     {
         Carver c(b.scratch, 0);
         CommScratch s;
         carve_comm(c, m, n, s);
-        uint32_t D = p->threshold ? p->threshold : uint32_t((2 * m) / n);
-        BGV_TRY(run_communities(edges, m, n, b.deg_est, p->passes, D, p->growth, p->tie_mode, b.labels, nullptr, s,
-                                status, st));
+        BGV_TRY(run_communities(edges, m, n, b.deg_est, p->passes, D, p->growth, p->tie_mode, p->jumps, b.labels,
+                                nullptr, s, status, st));
     }
     {
         Carver c(b.scratch, 0);
@@ -399,12 +428,19 @@ int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, c
         SketchScratch s;
         carve_sketch(sc, m, N, p->rows, p->width, s);
         BGV_TRY(run_sketch(bb.edges, m, N, h, b.sketch, b.deg_est, s, status, st, &view));
+        if (!p->threshold && p->threshold_mode == 1) {
+            // each graph's most common degree, straight into D0
+            ModeScratch ms;
+            carve_mode(sc, N, G, ms);
+            BGV_TRY(run_mode_degree(s.deg, N, &view, bb.D0, ms, status, st));
+        }
     }
     {
         Carver sc(b.scratch, 0);
         CommScratch s;
         carve_comm(sc, m, N, s, true);
-        BGV_TRY(run_communities(bb.edges, m, N, b.deg_est, p->passes, 0, p->growth, p->tie_mode, b.labels, nullptr, s,
+        BGV_TRY(run_communities(bb.edges, m, N, b.deg_est, p->passes, 0, p->growth, p->tie_mode, p->jumps, b.labels,
+                                nullptr, s,
                                 status, st, &view));
     }
     {
@@ -521,14 +557,73 @@ int bgv_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
                     void *ws, size_t ws_bytes, void *stream) {
     BGV_TRY(check_graph(edges, m, n));
-    if (!deg_est || !labels || passes < 0 || growth < 1 || (tie_mode != 0 && tie_mode != 1)) return BGV_EINVAL;
+    if (!deg_est || !labels || passes < 0 || (tie_mode != 0 && tie_mode != 1)) return BGV_EINVAL;
     BGV_TRY(check_ws(ws, ws_bytes, comm_ws(m, n)));
     Carver c(ws, kHeaderBytes);
     CommScratch s;
     carve_comm(c, m, n, s);
     const uint32_t D = threshold ? threshold : uint32_t((2 * m) / n);
-    return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, labels, deg_out, s, status_ptr(ws),
+    return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, 0, labels, deg_out, s, status_ptr(ws),
                            as_stream(stream));
+}
+
+size_t bgv_communities_ex_ws_size(int64_t m, int32_t n) {
+    size_t comm = 0, mode = 0;
+    {
+        Carver c(nullptr, 0);
+        CommScratch s;
+        carve_comm(c, m, n, s);
+        comm = c.used();
+    }
+    {
+        Carver c(nullptr, 0);
+        ModeScratch s;
+        carve_mode(c, n, 1, s);
+        mode = c.used();
+    }
+    Carver c(nullptr, kHeaderBytes);
+    c.take<uint32_t>(1);
+    c.take<char>(comm > mode ? comm : mode);
+    return c.used();
+}
+
+int bgv_communities_ex(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
+                       uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t threshold_mode, int32_t jumps,
+                       int32_t *labels, uint32_t *deg_out, uint32_t *threshold_out, void *ws, size_t ws_bytes,
+                       void *stream) {
+    BGV_TRY(check_graph(edges, m, n));
+    if (!deg_est || !labels || passes < 0 || (tie_mode != 0 && tie_mode != 1)) return BGV_EINVAL;
+    if ((threshold_mode != 0 && threshold_mode != 1) || jumps < 0 || jumps > 64) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_communities_ex_ws_size(m, n)));
+    cudaStream_t st = as_stream(stream);
+    Carver c(ws, kHeaderBytes);
+    uint32_t *mode_dev = c.take<uint32_t>(1);
+    char *region = c.take<char>(0);
+    uint32_t D = threshold ? threshold : uint32_t((2 * m) / n);
+    if (!threshold && threshold_mode == 1) BGV_TRY(mode_threshold(deg_est, n, mode_dev, region, status_ptr(ws), st, &D));
+    if (threshold_out) *threshold_out = D;
+    Carver rc(region, 0);
+    CommScratch s;
+    carve_comm(rc, m, n, s);
+    return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, jumps, labels, deg_out, s,
+                           status_ptr(ws), st);
+}
+
+size_t bgv_mode_degree_ws_size(int32_t n) {
+    Carver c(nullptr, kHeaderBytes);
+    c.take<uint32_t>(1);
+    ModeScratch s;
+    carve_mode(c, n, 1, s);
+    return c.used();
+}
+
+int bgv_mode_degree(const uint32_t *deg, int32_t n, uint32_t *mode_out, void *ws, size_t ws_bytes, void *stream) {
+    if (n < 1 || n >= 0x7FFFFFFF || !deg || !mode_out) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_mode_degree_ws_size(n)));
+    Carver c(ws, kHeaderBytes);
+    uint32_t *mode_dev = c.take<uint32_t>(1);
+    char *region = c.take<char>(0);
+    return mode_threshold(deg, n, mode_dev, region, status_ptr(ws), as_stream(stream), mode_out);
 }
 
 size_t bgv_supergraph_ws_size(int64_t m, int32_t n, int32_t rows, int32_t width) {
@@ -714,6 +809,8 @@ void bgv_layout_default_params(bgv_layout_params *p) {
     p->passes = 3;
     p->threshold = 0;
     p->growth = 2;
+    p->threshold_mode = 0;
+    p->jumps = 0;
     p->tie_mode = 0;
     p->iterations = 200;
     p->use_graph = 1;
@@ -866,5 +963,30 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
     return fa2_loop(K, nnz, csr_off, csr_adj, csr_w, mass, *p, iterations, use_graph, pos, F, Fprev, speed,
                     header(ws), scratch, st, G, dkoff);
 }
+
+size_t bgv_autotune_sort_ws_size(int64_t max_keys) {
+    Carver c(nullptr, kHeaderBytes);
+    SortBuffers b;
+    carve_sort(c, max_keys > 0 ? max_keys : 1, true, b);
+    return c.used();
+}
+
+int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t ws_bytes, void *stream) {
+    if (max_keys < (int64_t(1) << 14) || max_keys >= (int64_t(1) << 31)) return BGV_EINVAL;
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_autotune_sort_ws_size(max_keys)));
+    Carver c(ws, kHeaderBytes);
+    SortBuffers b;
+    carve_sort(c, max_keys, true, b);
+    bgv_tune_report r;
+    memset(&r, 0, sizeof(r));
+    int32_t count = 0;
+    BGV_TRY(autotune_sort(max_keys, b, as_stream(stream), status_ptr(ws), r.ms8, r.ms16, r.sizes_log2, &count));
+    r.count = count;
+    r.cutoff = sort_cutoff();
+    if (out) *out = r;
+    return BGV_OK;
+}
+
+int64_t bgv_sort_cutoff(void) { return sort_cutoff(); }
 
 }  // extern "C"

@@ -129,8 +129,19 @@ struct SortBuffers {
 };
 int64_t sort_tiles(int64_t cap);
 void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
+// `items` 8 or 16 forces the keys per thread; anything else follows the
+// size cutoff (see autotune_sort).
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
-               int *result_buffer, uint32_t *dev_status);
+               int *result_buffer, uint32_t *dev_status, int items = 0);
+
+// Sort autotuner: times 8 against 16 keys per thread for 2^14, 2^16, ...
+// up to max_keys and sets the cutoff between them for the whole process.
+// Per size k (count of them in *count): ms8[k], ms16[k], sizes_log2[k]
+// (host arrays, may be NULL; 9 entries suffice).  b must hold max_keys
+// pairs.
+int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
+                  int32_t *sizes_log2, int32_t *count);
+int64_t sort_cutoff();
 
 
 
@@ -166,16 +177,29 @@ int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, 
 
 struct CommScratch {
     uint2 *state;                   // (degree, label) per node
-    uint4 *bstate;                  // batched form: (degree, label, threshold, 0)
+    uint4 *bstate;                  // batched form: (degree, label, threshold, first threshold)
     unsigned long long *best;       // packed (edge index, label) proposals
+    uint32_t *jump;                 // labels after a pointer-jumping step
 };
 void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched = false);
+// growth 0: the threshold is multiplied by its first value every round (the
+// delta^i schedule).  `jumps` pointer-jumping steps follow every round.
 // With `batch`, the threshold of every node starts at its graph's D0 and
 // `threshold` is ignored.
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
-                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels,
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t jumps, int32_t *labels,
                     uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st,
                     const BatchView *batch = nullptr);
+
+// Mode degree: the most frequent nonzero value of deg (ties: the smaller),
+// 0 if none; with `batch`, one per graph.  mode_dev: device, 1 or G values.
+struct ModeScratch {
+    SortBuffers sort;            // n keys (graph << 32 | degree)
+    unsigned long long *best;    // per graph: (run length, ~degree)
+};
+void carve_mode(Carver &c, int32_t n, int32_t G, ModeScratch &s);
+int run_mode_degree(const uint32_t *deg, int32_t n, const BatchView *batch, uint32_t *mode_dev,
+                    const ModeScratch &s, uint32_t *status, cudaStream_t st);
 
 struct SuperScratch {
     uint32_t *flags;        // [n] label present / CSR counts

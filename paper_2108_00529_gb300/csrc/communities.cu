@@ -81,7 +81,7 @@ __device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, i
 __device__ __forceinline__ void propose_edge_b(int32_t u, int32_t v, uint32_t e, int32_t n, const uint4 *state,
                                                unsigned long long *best, int tie_mode, uint32_t *status) {
     if (!endpoints_ok(u, v, n, status)) return;
-    const uint4 su = state[u], sv = state[v];  // (degree, label, threshold, 0)
+    const uint4 su = state[u], sv = state[v];  // (degree, label, threshold, first threshold)
     uint32_t lab;
     const int32_t w = edge_rule(u, v, su.x, su.y, sv.x, sv.y, su.z, tie_mode, &lab);
     if (w >= 0) offer(best, w, e, lab);
@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(kThreads) k_comm_init_b(const uint32_t *__rest
                                                           unsigned long long *__restrict__ best) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        state[v] = make_uint4(deg_est[v], uint32_t(v), D0[node_graph[v]], 0u);
+        const uint32_t d0 = D0[node_graph[v]];
+        state[v] = make_uint4(deg_est[v], uint32_t(v), d0, d0);
         best[v] = kNone;
     }
 }
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(kThreads) k_comm_propose_b(const int32_t *__re
 }
 
 // Applies the winning proposals and moves every node's threshold to the
-// next round's (times growth, saturating at 2^32 - 1).
+// next round's (times growth, or times its graph's first threshold when
+// growth is 0; saturating at 2^32 - 1).
 __global__ void __launch_bounds__(kThreads) k_comm_apply_b(int32_t n, uint4 *__restrict__ state,
                                                            unsigned long long *__restrict__ best, uint32_t growth) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_comm_apply_b(int32_t n, uint4 *__r
             if (s.x != 0xFFFFFFFFu) s.x += 1;
             best[v] = kNone;
         }
-        const unsigned long long D = static_cast<unsigned long long>(s.z) * growth;
+        const unsigned long long D = static_cast<unsigned long long>(s.z) * (growth ? growth : s.w);
         s.z = D > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(D);
         state[v] = s;
     }
@@ -184,6 +186,59 @@ __global__ void __launch_bounds__(kThreads) k_comm_out(int32_t n, const uint2 *_
         if (deg_out) deg_out[v] = s.x;
     }
 }
+
+// Pointer jumping (one synchronous step): every label becomes its label's
+// label, read from the state before the step.
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_comm_jump_read(int32_t n, const S *__restrict__ state,
+                                                             uint32_t *__restrict__ next) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride)
+        next[v] = state[state[v].y].y;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_comm_jump_write(int32_t n, S *__restrict__ state,
+                                                              const uint32_t *__restrict__ next) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) state[v].y = next[v];
+}
+
+// Mode degree (Section 4.2.2): the keys (graph << 32 | degree) are sorted;
+// the end of every run of equal nonzero keys finds the run's start by binary
+// search and offers (run length, complement of the degree) to its graph, so
+// the longest run wins and ties go to the smaller degree.
+__global__ void __launch_bounds__(kThreads) k_mode_keys(const uint32_t *__restrict__ deg, int32_t n,
+                                                        const int32_t *__restrict__ node_graph,
+                                                        unsigned long long *__restrict__ keys) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long g = node_graph ? static_cast<unsigned long long>(node_graph[v]) : 0ull;
+        keys[v] = (g << 32) | deg[v];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mode_runs(const unsigned long long *__restrict__ sorted, int32_t n,
+                                                        unsigned long long *best) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long k = sorted[i];
+        const uint32_t value = static_cast<uint32_t>(k & 0xFFFFFFFFull);
+        if (value == 0 || (i + 1 < n && sorted[i + 1] == k)) continue;
+        int64_t lo = 0, hi = i;  // first position holding k
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (sorted[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        const unsigned long long len = static_cast<unsigned long long>(i - lo + 1);
+        atomicMax(&best[k >> 32], (len << 32) | (0xFFFFFFFFull - value));
+    }
+}
+
+__global__ void k_mode_out(const unsigned long long *__restrict__ best, int32_t G, uint32_t *__restrict__ mode) {
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        mode[g] = best[g] ? uint32_t(0xFFFFFFFFull - (best[g] & 0xFFFFFFFFull)) : 0u;
+}
 }  // namespace
 
 void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched) {
@@ -191,11 +246,34 @@ void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched) {
     s.state = batched ? nullptr : c.take<uint2>(size_t(n));
     s.bstate = batched ? c.take<uint4>(size_t(n)) : nullptr;
     s.best = c.take<unsigned long long>(size_t(n));
+    s.jump = c.take<uint32_t>(size_t(n));
+}
+
+void carve_mode(Carver &c, int32_t n, int32_t G, ModeScratch &s) {
+    carve_sort(c, n, false, s.sort);
+    s.best = c.take<unsigned long long>(size_t(G > 0 ? G : 1));
+}
+
+int run_mode_degree(const uint32_t *deg, int32_t n, const BatchView *batch, uint32_t *mode_dev,
+                    const ModeScratch &s, uint32_t *status, cudaStream_t st) {
+    const int32_t G = batch ? batch->G : 1;
+    const int gn = grid_for(n, kThreads, 152 * 8);
+    BGV_CUDA(cudaMemsetAsync(s.best, 0, sizeof(unsigned long long) * size_t(G), st));
+    note_launch(), k_mode_keys<<<gn, kThreads, 0, st>>>(deg, n, batch ? batch->node_graph : nullptr,
+                                                        s.sort.keys[0]);
+    BGV_TRY(launch_status());
+    SortBuffers sb = s.sort;
+    int res = 0;
+    BGV_TRY(radix_sort(sb, n, nullptr, 32 + (batch ? bits_for(G) : 0), st, &res, status));
+    note_launch(), k_mode_runs<<<gn, kThreads, 0, st>>>(sb.keys[res], n, s.best);
+    note_launch(), k_mode_out<<<grid_for(G, kThreads, 152), kThreads, 0, st>>>(s.best, G, mode_dev);
+    return launch_status();
 }
 
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
-                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t *labels, uint32_t *deg_out,
-                    const CommScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch) {
+                    uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t jumps, int32_t *labels,
+                    uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st,
+                    const BatchView *batch) {
     const int gn = grid_for(n, kThreads, 152 * 8);
     if (batch) {
         const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
@@ -210,6 +288,11 @@ int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
             }
             note_launch(), k_comm_apply_b<<<gn, kThreads, 0, st>>>(n, s.bstate, s.best, growth);
             BGV_TRY(launch_status());
+            for (int32_t j = 0; j < jumps; ++j) {
+                note_launch(), k_comm_jump_read<<<gn, kThreads, 0, st>>>(n, s.bstate, s.jump);
+                note_launch(), k_comm_jump_write<<<gn, kThreads, 0, st>>>(n, s.bstate, s.jump);
+                BGV_TRY(launch_status());
+            }
         }
         note_launch(), k_comm_out_b<<<gn, kThreads, 0, st>>>(n, s.bstate, labels, deg_out);
         return launch_status();
@@ -217,6 +300,7 @@ int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
     note_launch(), k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
     BGV_TRY(launch_status());
     unsigned long long D = threshold;
+    const unsigned long long factor = growth ? growth : threshold;
     const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
     for (int32_t p = 0; p < passes; ++p) {
         if (m > 0) {
@@ -225,7 +309,12 @@ int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
         }
         note_launch(), k_comm_apply<<<gn, kThreads, 0, st>>>(n, s.state, s.best);
         BGV_TRY(launch_status());
-        D *= growth;
+        for (int32_t j = 0; j < jumps; ++j) {
+            note_launch(), k_comm_jump_read<<<gn, kThreads, 0, st>>>(n, s.state, s.jump);
+            note_launch(), k_comm_jump_write<<<gn, kThreads, 0, st>>>(n, s.state, s.jump);
+            BGV_TRY(launch_status());
+        }
+        D *= factor;
         if (D > 0xFFFFFFFFull) D = 0xFFFFFFFFull;
     }
     note_launch(), k_comm_out<<<gn, kThreads, 0, st>>>(n, s.state, labels, deg_out);

@@ -375,42 +375,52 @@ __global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__r
     if (i < K - 1) {
         const int kb = 2 * L + gbits;
         const unsigned long long ki = __ldg(&keys[i]);
-        const int d = key_delta(keys, K, kb, i, ki, i + 1) > key_delta(keys, K, kb, i, ki, i - 1) ? 1 : -1;
-        const int dmin = key_delta(keys, K, kb, i, ki, i - d);
-        int64_t lmax = 2;
-        while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
-        int64_t l = 0;
-        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-            if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
-        const int64_t j = i + l * d;
-        const int dnode = key_delta(keys, K, kb, i, ki, j);
-        const int64_t first = i < j ? i : j, last = i < j ? j : i;
-        const int lev = node_level(dnode, kb, L, gbits);
-        const int par_lev = node_level(dmin, kb, L, gbits);
-        top = par_lev < lev;
-        cell_level[i] = static_cast<int8_t>(top ? lev : -1);
-        if (top) {
-            range[i] = make_int2(int32_t(first), int32_t(last));
-            const int cnt = int(last - first) + 1;
-            const bool leaf = cnt <= leaf_cap || lev >= L;
-            // A leaf made by the depth limit (coincident keys, more than
-            // leaf_cap bodies) hides a chain of non-leaf cells with the same
-            // bodies between its parent's level and L; the deepest of them,
-            // at level L - 1, takes the opening test for the whole chain.
-            const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
-            // positions of graph g in Morton order are its index range too
-            const float4 fr = frames[bgraph ? bgraph[first] : 0];
-            const Mom hi = mom_load(PM, PX, PY, last + 1), lo = mom_load(PM, PX, PY, first);
-            const unsigned long long M = hi.M - lo.M;
-            const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
-            const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
-            const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), 2.3283064365386963e-10f)));
-            const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), 2.3283064365386963e-10f)));
-            const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
-            const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
-            cell[i] = make_float4(cx, cy, __ull2float_rn(M), side2);
-            atomicAdd(&start_count[first], 1u);
-            atomicOr(&start_levels[first], 1u << lev);
+        const int dnext = key_delta(keys, K, kb, i, ki, i + 1), dprev = key_delta(keys, K, kb, i, ki, i - 1);
+        const int d = dnext > dprev ? 1 : -1;
+        const int dmin = d > 0 ? dprev : dnext;
+        // The node's split lies between its parent's (dmin) and that of the
+        // pair (i, i + d) inside its range: when those two share a level,
+        // the node shares it with its parent and is no cell.
+        const bool may_be_cell =
+            node_level(d > 0 ? dnext : dprev, kb, L, gbits) != node_level(dmin, kb, L, gbits);
+        if (!may_be_cell) cell_level[i] = -1;
+        if (may_be_cell) {
+            int64_t lmax = 2;
+            while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
+            int64_t l = 0;
+            for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+                if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
+            const int64_t j = i + l * d;
+            const int dnode = key_delta(keys, K, kb, i, ki, j);
+            const int64_t first = i < j ? i : j, last = i < j ? j : i;
+            const int lev = node_level(dnode, kb, L, gbits);
+            const int par_lev = node_level(dmin, kb, L, gbits);
+            top = par_lev < lev;
+            cell_level[i] = static_cast<int8_t>(top ? lev : -1);
+            if (top) {
+                range[i] = make_int2(int32_t(first), int32_t(last));
+                const int cnt = int(last - first) + 1;
+                const bool leaf = cnt <= leaf_cap || lev >= L;
+                // A leaf made by the depth limit (coincident keys, more than
+                // leaf_cap bodies) hides a chain of non-leaf cells with the same
+                // bodies between its parent's level and L; the deepest of them,
+                // at level L - 1, takes the opening test for the whole chain.
+                const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
+                // positions of graph g in Morton order are its index range too
+                const float4 fr = frames[bgraph ? bgraph[first] : 0];
+                const Mom hi = mom_load(PM, PX, PY, last + 1), lo = mom_load(PM, PX, PY, first);
+                const unsigned long long M = hi.M - lo.M;
+                const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
+                const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
+                const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+                const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), two_m32)));
+                const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), two_m32)));
+                const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
+                const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
+                cell[i] = make_float4(cx, cy, __ull2float_rn(M), side2);
+                atomicAdd(&start_count[first], 1u);
+                atomicOr(&start_levels[first], 1u << lev);
+            }
         }
     }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, top);

@@ -5,6 +5,7 @@
 // trip.  Grids are sized for the host-side upper bound; blocks past the
 // device count do no work (the radix histogram still writes zeros for them so
 // the digit offsets stay consistent).
+#include <algorithm>
 #include <atomic>
 
 #include "bgv_internal.cuh"
@@ -182,13 +183,20 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
 namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-// Keys per thread: 16 for big inputs; 8 below kSmallSort keys, so that a
-// million keys still make ~500 tiles (enough blocks for 152 SMs).
+// Keys per thread: 8 up to a cutoff, 16 above it.  The cutoff starts at
+// 2^22 keys (a million keys then make ~480 tiles, enough blocks for 152
+// SMs) and bgv_autotune_sort can set it from measurements on this GPU.
 constexpr int kSortItemsBig = 16, kSortItemsSmall = 8;
-constexpr int64_t kSmallSort = int64_t(1) << 22;
+std::atomic<int64_t> g_small_sort_cutoff{int64_t(1) << 22};
 constexpr int kSortItems = 16;  // the counting kernel's items per thread
 constexpr int kSortTile = kSortThreads * kSortItems;
-inline int sort_items(int64_t cap) { return cap <= kSmallSort ? kSortItemsSmall : kSortItemsBig; }
+inline int sort_items(int64_t cap) {
+    return cap <= g_small_sort_cutoff.load(std::memory_order_relaxed) ? kSortItemsSmall : kSortItemsBig;
+}
+inline int64_t tiles_for(int64_t cap, int items) {
+    const int64_t t = (cap + int64_t(kSortThreads) * items - 1) / (int64_t(kSortThreads) * items);
+    return t < 1 ? 1 : t;
+}
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
 // Look-back words: 2 flag bits, the pass number (1..8) in bits 40..47 and a
@@ -394,8 +402,10 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
 }
 }  // namespace
 
+// The look-back words are sized for the smaller tiles, so a workspace stays
+// large enough whatever tile size the cutoff picks later.
 int64_t sort_tiles(int64_t cap) {
-    const int64_t tile = int64_t(kSortThreads) * sort_items(cap);
+    const int64_t tile = int64_t(kSortThreads) * kSortItemsSmall;
     int64_t t = (cap + tile - 1) / tile;
     return t < 1 ? 1 : t;
 }
@@ -413,9 +423,9 @@ namespace {
 // One onesweep pass on the 8-bit digit at `shift`, from buffer pair `cur` to
 // `cur ^ 1`.
 int onesweep_pass(SortBuffers &b, int64_t cap, const int64_t *d_count, int cur, int shift, const uint32_t *base,
-                  unsigned *tile_counter, unsigned long long tag, cudaStream_t s, uint32_t *dev_status) {
-    const unsigned g = static_cast<unsigned>(sort_tiles(cap));
-    const bool small = sort_items(cap) == kSortItemsSmall;
+                  unsigned *tile_counter, unsigned long long tag, int items, cudaStream_t s, uint32_t *dev_status) {
+    const bool small = items == kSortItemsSmall;
+    const unsigned g = static_cast<unsigned>(tiles_for(cap, items));
     unsigned long long *ki = b.keys[cur], *ko = b.keys[cur ^ 1];
     uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1];
     if (b.vals[0] && small)
@@ -437,8 +447,9 @@ inline unsigned long long pass_tag(int p) { return static_cast<unsigned long lon
 }  // namespace
 
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
-               int *result_buffer, uint32_t *dev_status) {
-    const int64_t tiles = sort_tiles(cap);
+               int *result_buffer, uint32_t *dev_status, int items) {
+    if (items != kSortItemsSmall && items != kSortItemsBig) items = sort_items(cap);
+    const int64_t tiles = tiles_for(cap, items);
     const int passes = (end_bit + 7) / 8;
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
@@ -451,12 +462,76 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     int cur = 0;
     BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
     for (int p = 0; p < passes; ++p) {
-        BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p), s,
-                              dev_status));
+        BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p),
+                              items, s, dev_status));
         cur ^= 1;
     }
     *result_buffer = cur;
     return BGV_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+// Times the sort of 48-bit keys with values at 8 and at 16 keys per thread
+// for sizes 2^14 .. max_keys (powers of four) and sets the cutoff to the
+// largest size at which 8 was not slower.  Keys come from SplitMix64 of the
+// index, so every GPU sees the same inputs.
+namespace {
+__global__ void k_tune_keys(unsigned long long *keys, uint32_t *vals, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        unsigned long long z = 0x5EEDull + static_cast<unsigned long long>(i) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        keys[i] = (z ^ (z >> 31)) & ((1ull << 48) - 1);
+        vals[i] = uint32_t(i);
+    }
+}
+}  // namespace
+
+int64_t sort_cutoff() { return g_small_sort_cutoff.load(std::memory_order_relaxed); }
+
+int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
+                  int32_t *sizes_log2, int32_t *count) {
+    cudaEvent_t e0, e1;
+    BGV_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BGV_ECUDA;
+    }
+    int rc = BGV_OK;
+    int64_t cutoff = 0;
+    int k = 0;
+    for (int lg = 14; lg <= 30 && (int64_t(1) << lg) <= max_keys && rc == BGV_OK; lg += 2, ++k) {
+        const int64_t n = int64_t(1) << lg;
+        float best[2] = {0.0f, 0.0f};
+        for (int v = 0; v < 2 && rc == BGV_OK; ++v) {
+            const int items = v == 0 ? kSortItemsSmall : kSortItemsBig;
+            float times[3];
+            for (int r = 0; r < 4 && rc == BGV_OK; ++r) {
+                note_launch(), k_tune_keys<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(b.keys[0], b.vals[0], n);
+                int res = 0;
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = BGV_ECUDA;
+                if (rc == BGV_OK) rc = radix_sort(b, n, nullptr, 48, s, &res, dev_status, items);
+                if (rc == BGV_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = BGV_ECUDA;
+                if (rc == BGV_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = BGV_ECUDA;
+                float ms = 0.0f;
+                if (rc == BGV_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BGV_ECUDA;
+                if (r > 0) times[r - 1] = ms;  // the first run warms up
+            }
+            if (rc != BGV_OK) break;
+            std::sort(times, times + 3);
+            best[v] = times[1];
+        }
+        if (rc != BGV_OK) break;
+        if (ms8) ms8[k] = best[0];
+        if (ms16) ms16[k] = best[1];
+        if (sizes_log2) sizes_log2[k] = lg;
+        if (best[0] <= best[1]) cutoff = n;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (count) *count = k;
+    if (rc == BGV_OK) g_small_sort_cutoff.store(cutoff, std::memory_order_relaxed);
+    return rc;
 }
 
 }  // namespace bgv

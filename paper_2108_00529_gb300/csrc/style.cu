@@ -1,4 +1,5 @@
-// style.cu -- supernode colour groups (Section 4.3).
+// style.cu -- supernode colour groups (Section 4.3) and drawing the discs
+// into an image (Section 4.1 radii, Section 4.3 colours).
 //
 // Communities are ordered by size (a stable radix sort of (size, id), so
 // ties keep id order).  With alpha the total size, the longest prefix of
@@ -119,4 +120,131 @@ extern "C" int bgv_colour_groups(int64_t K, const uint32_t *sizes, uint8_t *grou
         BGV_TRY(launch_status());
     }
     return BGV_OK;
+}
+
+// ------------------------------------------------------------- drawing
+// Discs of radius r (sqrt of the size, Section 4.1) in the colour of their
+// group (Section 4.3), splatted into an RGBA image: the discs' bounding box
+// maps to the pixels with one scale s = min(W, H) / largest extent; pixel
+// (px, py) shows the disc whose scaled circle covers its centre (px + 0.5,
+// py + 0.5); overlaps keep the smaller radius, then the smaller id.  One
+// warp per disc marks the covered pixels with an atomicMax of (priority,
+// id); a second pass shades.  FP32 with explicit round-to-nearest
+// operations, so the coverage equals the plain definition's.
+namespace bgv {
+namespace {
+__constant__ uint8_t c_palette[11][3] = {
+    {177, 89, 40},   {202, 178, 214}, {106, 61, 154}, {253, 191, 111}, {255, 127, 0}, {251, 154, 153},
+    {227, 26, 28},   {178, 223, 138}, {51, 160, 44},  {166, 206, 227}, {31, 120, 180}};
+
+__global__ void __launch_bounds__(kStyleThreads) k_render_frame(const float2 *__restrict__ xy,
+                                                                const float *__restrict__ radius, int64_t K,
+                                                                int32_t W, int32_t H, float4 *frame) {
+    float lx = INFINITY, ly = INFINITY, hx = -INFINITY, hy = -INFINITY;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+        const float2 p = xy[k];
+        const float r = radius[k];
+        lx = fminf(lx, __fsub_rn(p.x, r)); ly = fminf(ly, __fsub_rn(p.y, r));
+        hx = fmaxf(hx, __fadd_rn(p.x, r)); hy = fmaxf(hy, __fadd_rn(p.y, r));
+    }
+    __shared__ float4 part[kStyleThreads / 32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xFFFFFFFFu, lx, d)); ly = fminf(ly, __shfl_xor_sync(0xFFFFFFFFu, ly, d));
+        hx = fmaxf(hx, __shfl_xor_sync(0xFFFFFFFFu, hx, d)); hy = fmaxf(hy, __shfl_xor_sync(0xFFFFFFFFu, hy, d));
+    }
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = make_float4(lx, ly, hx, hy);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    float4 b = part[0];
+    for (int w = 1; w < kStyleThreads / 32; ++w) {
+        b.x = fminf(b.x, part[w].x); b.y = fminf(b.y, part[w].y);
+        b.z = fmaxf(b.z, part[w].z); b.w = fmaxf(b.w, part[w].w);
+    }
+    const float ex = __fsub_rn(b.z, b.x), ey = __fsub_rn(b.w, b.y);
+    const float ext = ex > ey ? ex : ey;
+    const float s = (K > 0 && ext > 0.0f) ? __fdiv_rn(float(W < H ? W : H), ext) : 1.0f;
+    *frame = make_float4(b.x, b.y, s, 0.0f);
+}
+
+__global__ void __launch_bounds__(kStyleThreads) k_render_splat(const float2 *__restrict__ xy,
+                                                                const float *__restrict__ radius, int64_t K,
+                                                                int32_t W, int32_t H, const float4 *frame,
+                                                                unsigned long long *__restrict__ zbuf) {
+    const int lane = threadIdx.x & 31;
+    const float4 f = *frame;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < K; k += warps) {
+        const float2 p = xy[k];
+        const float r = radius[k];
+        const float u = __fmul_rn(__fsub_rn(p.x, f.x), f.z), v = __fmul_rn(__fsub_rn(p.y, f.y), f.z);
+        const float rs = __fmul_rn(r, f.z), rs2 = __fmul_rn(rs, rs);
+        // pixels whose centre can lie within rs of (u, v), one pixel of slack
+        const int x0 = max(0, int(floorf(u - rs)) - 1), x1 = min(W - 1, int(ceilf(u + rs)) + 1);
+        const int y0 = max(0, int(floorf(v - rs)) - 1), y1 = min(H - 1, int(ceilf(v + rs)) + 1);
+        if (!(rs >= 0.0f) || x0 > x1 || y0 > y1) continue;
+        const unsigned long long key =
+            (static_cast<unsigned long long>(0xFFFFFFFFu - __float_as_uint(r)) << 32) | (0xFFFFFFFFull - uint64_t(k));
+        const int bw = x1 - x0 + 1;
+        const int64_t cells = int64_t(bw) * (y1 - y0 + 1);
+        for (int64_t c = lane; c < cells; c += 32) {
+            const int px = x0 + int(c % bw), py = y0 + int(c / bw);
+            const float dx = __fsub_rn(__fadd_rn(float(px), 0.5f), u), dy = __fsub_rn(__fadd_rn(float(py), 0.5f), v);
+            const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            if (d2 <= rs2) atomicMax(&zbuf[size_t(py) * W + px], key);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kStyleThreads) k_render_shade(const unsigned long long *__restrict__ zbuf,
+                                                                int64_t pixels, int64_t K,
+                                                                const uint8_t *__restrict__ group,
+                                                                uchar4 *__restrict__ rgba) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < pixels;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long z = zbuf[i];
+        uchar4 o = make_uchar4(255, 255, 255, 255);
+        if (z) {
+            const int64_t k = int64_t(0xFFFFFFFFull - (z & 0xFFFFFFFFull));
+            const uint8_t g = k < K ? group[k] : 0;
+            const int c = g <= 10 ? g : 0;
+            o = make_uchar4(c_palette[c][0], c_palette[c][1], c_palette[c][2], 255);
+        }
+        rgba[i] = o;
+    }
+}
+}  // namespace
+}  // namespace bgv
+
+extern "C" size_t bgv_render_ws_size(int32_t W, int32_t H) {
+    Carver c(nullptr, kHeaderBytes);
+    c.take<float4>(1);
+    c.take<unsigned long long>(size_t(W > 0 ? W : 1) * size_t(H > 0 ? H : 1));
+    return c.used();
+}
+
+extern "C" int bgv_render(int64_t K, const float *xy, const float *radius, const uint8_t *group, int32_t W, int32_t H,
+                          uint8_t *rgba, void *ws, size_t ws_bytes, void *stream) {
+    if (K < 0 || K >= 0xFFFFFFFFll || W < 1 || H < 1 || W > 32768 || H > 32768 || !rgba) return BGV_EINVAL;
+    if (K > 0 && (!xy || !radius || !group || reinterpret_cast<uintptr_t>(xy) % 8)) return BGV_EINVAL;
+    if (reinterpret_cast<uintptr_t>(rgba) % 4) return BGV_EINVAL;
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign) return BGV_EINVAL;
+    if (ws_bytes < bgv_render_ws_size(W, H)) return BGV_ENOSPC;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Carver c(ws, kHeaderBytes);
+    float4 *frame = c.take<float4>(1);
+    const int64_t pixels = int64_t(W) * H;
+    unsigned long long *zbuf = c.take<unsigned long long>(size_t(pixels));
+    BGV_CUDA(cudaMemsetAsync(zbuf, 0, sizeof(unsigned long long) * size_t(pixels), st));
+    const float2 *p = reinterpret_cast<const float2 *>(xy);
+    note_launch(), k_render_frame<<<1, kStyleThreads, 0, st>>>(p, radius, K, W, H, frame);
+    BGV_TRY(launch_status());
+    if (K > 0) {
+        note_launch(), k_render_splat<<<grid_for(K * 32, kStyleThreads, 152 * 16), kStyleThreads, 0, st>>>(
+            p, radius, K, W, H, frame, zbuf);
+        BGV_TRY(launch_status());
+    }
+    note_launch(), k_render_shade<<<grid_for(pixels, kStyleThreads, 152 * 8), kStyleThreads, 0, st>>>(
+        zbuf, pixels, K, group, reinterpret_cast<uchar4 *>(rgba));
+    return launch_status();
 }

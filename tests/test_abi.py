@@ -44,10 +44,11 @@ def test_binding_covers_the_header(lib):
 def test_struct_layouts(lib):
     from paper_2108_00529_gb300 import bgv
     assert C.sizeof(bgv.bgv_fa2_params) == 48
-    assert C.sizeof(bgv.bgv_layout_params) == 88
+    assert C.sizeof(bgv.bgv_layout_params) == 96
     assert C.sizeof(bgv.bgv_fa2_stats) == 56
     p = bgv.bgv_layout_default_params()
     assert (p.rows, p.width, p.passes, p.growth, p.iterations) == (4, 4096, 3, 2, 200)
+    assert (p.threshold_mode, p.jumps, p.use_graph) == (0, 0, 1)
     assert abs(p.fa2.theta - 1.2) < 1e-6 and p.fa2.max_depth == 24 and p.fa2.leaf_cap == 1
 
 
@@ -74,8 +75,12 @@ def test_host_validation_rejects_bad_arguments(lib):
                                 None) == bgv.BGV_EINVAL  # edges not 16-byte aligned
     assert L.bgv_sketch_degrees(C.c_void_p(16), 1, 10, 4, 16, 1, C.c_void_p(16), C.c_void_p(16), fake_ws, 64,
                                 None) == bgv.BGV_ENOSPC
-    assert L.bgv_communities(C.c_void_p(16), 1, 10, C.c_void_p(16), 1, 5, 0, 0, C.c_void_p(16), None, fake_ws,
-                             1 << 20, None) == bgv.BGV_EINVAL  # growth 0
+    assert L.bgv_communities(C.c_void_p(16), 1, 10, C.c_void_p(16), 1, 5, 2, 2, C.c_void_p(16), None, fake_ws,
+                             1 << 20, None) == bgv.BGV_EINVAL  # tie_mode 2
+    assert L.bgv_communities_ex(C.c_void_p(16), 1, 10, C.c_void_p(16), 1, 0, 2, 0, 2, 0, C.c_void_p(16), None, None,
+                                fake_ws, 1 << 20, None) == bgv.BGV_EINVAL  # threshold_mode 2
+    assert L.bgv_communities_ex(C.c_void_p(16), 1, 10, C.c_void_p(16), 1, 0, 2, 0, 0, 65, C.c_void_p(16), None, None,
+                                fake_ws, 1 << 20, None) == bgv.BGV_EINVAL  # jumps above 64
     p = bgv.bgv_fa2_default_params()
     p.max_depth = 25
     assert L.bgv_fa2_step(10, 20, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.byref(p),

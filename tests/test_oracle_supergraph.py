@@ -149,3 +149,50 @@ def test_colour_groups_properties():
             assert sizes[g == a].max() <= sizes[g == a + 1].min()
     counts = np.bincount(g, minlength=11)[1:]
     assert counts.max() - counts.min() <= 1
+
+
+# ------------------------------------------------------------------ drawing
+# Section 4.1 (radius ~ sqrt of the size) and Section 4.3 (colours).
+
+PALETTE = {0: (177, 89, 40), 1: (202, 178, 214), 2: (106, 61, 154), 3: (253, 191, 111), 4: (255, 127, 0),
+           5: (251, 154, 153), 6: (227, 26, 28), 7: (178, 223, 138), 8: (51, 160, 44), 9: (166, 206, 227),
+           10: (31, 120, 180)}  # ColorBrewer "Paired": brown, then light/dark purple, orange, red, green, blue
+
+
+def test_render_single_disc_fills_the_square():
+    # One disc: its bounding box is the whole image, so the scaled radius is
+    # W/2 and the covered pixels are those whose centres lie in the inscribed
+    # circle -- counted here independently in integers: (2px+1-W)^2 +
+    # (2py+1-W)^2 <= W^2.
+    W = 40
+    img = oracle.render([[3.0, -7.0]], [2.5], [4], W, W)
+    px, py = np.meshgrid(np.arange(W), np.arange(W))
+    inside = (2 * px + 1 - W) ** 2 + (2 * py + 1 - W) ** 2 <= W * W
+    assert np.array_equal(np.all(img[..., :3] == PALETTE[4], axis=-1), inside)
+    assert np.all(img[~inside][:, :3] == 255) and np.all(img[..., 3] == 255)
+
+
+def test_render_smaller_disc_on_top_and_palette():
+    # A big disc with a small one inside it: the small one wins where they
+    # overlap; every group maps to its colour.
+    for g in range(11):
+        img = oracle.render([[0.0, 0.0], [0.0, 0.0]], [10.0, 2.0], [0, g], 50, 50)
+        centre = tuple(img[25, 25, :3])
+        assert centre == PALETTE[g]
+        assert tuple(img[25, 3, :3]) == PALETTE[0]
+        assert tuple(img[0, 0, :3]) == (255, 255, 255)  # corner outside the inscribed circle
+
+
+def test_render_equal_radii_smaller_index_wins():
+    img = oracle.render([[0.0, 0.0], [0.0, 0.0], [5.0, 0.0]], [3.0, 3.0, 1.0], [2, 6, 8], 30, 30)
+    assert tuple(img[15, 8, :3]) == PALETTE[2]  # discs 0 and 1 coincide: disc 0 is drawn
+
+
+def test_render_wide_aspect_uses_one_scale():
+    # Discs spread along x: one scale for both axes, set by the wider extent.
+    img = oracle.render([[0.0, 0.0], [30.0, 0.0]], [1.0, 1.0], [1, 2], 64, 64)
+    # the box is 32 wide and 2 high: scale 2; each disc covers ~pi * 2^2 pixels near y in [0, 4)
+    for g in (1, 2):
+        cnt = int(np.all(img[..., :3] == PALETTE[g], axis=-1).sum())
+        assert 8 <= cnt <= 16
+    assert np.all(img[8:, :, :3] == 255)
