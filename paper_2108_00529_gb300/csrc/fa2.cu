@@ -183,11 +183,14 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float2 *__restrict__ po
     }
 }
 
+// Also clears the per-body cell counters that k_tree fills.
 __global__ void __launch_bounds__(kThreads) k_gather(const uint32_t *__restrict__ perm, int64_t K,
                                                      const float2 *__restrict__ pos,
                                                      const uint32_t *__restrict__ mass,
                                                      const uint2 *__restrict__ U, float4 *__restrict__ body,
-                                                     uint2 *__restrict__ sU, uint32_t *__restrict__ smass) {
+                                                     uint2 *__restrict__ sU, uint32_t *__restrict__ smass,
+                                                     uint32_t *__restrict__ start_count,
+                                                     uint32_t *__restrict__ start_levels) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < K; s += stride) {
         const uint32_t i = perm[s];
@@ -196,6 +199,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(const uint32_t *__restrict_
         body[s] = make_float4(p.x, p.y, __uint2float_rn(m), __int_as_float(int(i)));
         sU[s] = U[i];
         smass[s] = m;
+        start_count[s] = 0u;
+        start_levels[s] = 0u;
     }
 }
 
@@ -1262,7 +1267,8 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     int res = 0;
     BGV_TRY(radix_sort(s.sort, K, nullptr, 2 * L + gbits, st, &res, &hdr->status));
     BGV_TRY(mark(2));
-    note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass);
+    note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass,
+                                                     s.start_count, s.start_levels);
     BGV_TRY(launch_status());
     BGV_TRY(mark(3));
     if (K >= 2) {
@@ -1273,8 +1279,6 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         note_launch(), k_mom_tiles<<<1, kThreads, 0, st>>>(s.TM, s.TX, s.TY, tiles);
         note_launch(), k_mom_down<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY, s.PM, s.PX, s.PY);
         BGV_TRY(launch_status());
-        BGV_CUDA(cudaMemsetAsync(s.start_count, 0, sizeof(uint32_t) * size_t(K), st));
-        BGV_CUDA(cudaMemsetAsync(s.start_levels, 0, sizeof(uint32_t) * size_t(K), st));
         note_launch(), k_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph,
                                                        s.PM, s.PX, s.PY, s.range, s.cell_level, s.cell,
                                                        s.start_count, s.start_levels, &hdr->tree_nodes);
