@@ -134,6 +134,20 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
                int *result_buffer, uint32_t *dev_status, int items = 0);
 
+// The same order for n (key, value) pairs (host-known count) when the keys
+// are nearly always told apart above their low 16 bits: LSD passes on bits
+// 16.. only, then every run of equal high bits sorted locally on its low
+// bits.
+struct RunFixBuffers {
+    uint8_t *descent;   // per 32-key chunk: holds a key below its predecessor in the same run
+    uint32_t *runs;     // starts of runs too long for one thread
+    uint32_t *big;      // starts of runs too long for one warp
+    uint32_t *counts;   // [0] runs, [1] big
+};
+void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r);
+int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
+                    int *result_buffer, uint32_t *dev_status);
+
 // Sort autotuner: times 8 against 16 keys per thread for 2^14, 2^16, ...
 // up to max_keys and sets the cutoff between them for the whole process.
 // Per size k (count of them in *count): ms8[k], ms16[k], sizes_log2[k]

@@ -1131,6 +1131,7 @@ struct Fa2Scratch {
     int32_t *bgraph;       // batched form: graph of each body
     float2 *rowst;         // batched form: per-row swing, traction
     SortBuffers sort;
+    RunFixBuffers runfix;
     uint2 *U;
     float4 *body;
     uint2 *sU;
@@ -1165,6 +1166,7 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.bgraph = batched ? c.take<int32_t>(k) : nullptr;
     s.rowst = batched ? c.take<float2>(k) : nullptr;
     carve_sort(c, int64_t(k), true, s.sort);
+    carve_run_fix(c, int64_t(k), s.runfix);
     s.U = c.take<uint2>(k);
     s.body = c.take<float4>(k);
     s.sU = c.take<uint2>(k);
@@ -1230,6 +1232,32 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
     return launch_status();
 }
 
+// A second stream per host thread and device, made on first use.
+cudaStream_t aux_stream() {
+    static thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+
+// The two events of a fork onto the second stream and the join back,
+// destroyed when the step's work has been enqueued (work already enqueued
+// keeps them valid).
+struct ForkJoin {
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t make() {
+        cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        return e;
+    }
+    ~ForkJoin() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+    }
+};
+
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
@@ -1254,6 +1282,37 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     BGV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(hdr) + offsetof(WsHeader, interactions), 0,
                              offsetof(WsHeader, reserved) - offsetof(WsHeader, interactions), st));
     BGV_TRY(mark(0));
+    ForkJoin ev;
+    cudaStream_t aux = nullptr;
+    if (nnz > 0) {
+        aux = aux_stream();
+        if (!aux || ev.make() != cudaSuccess) return BGV_ECUDA;
+    }
+    // The attraction needs only the positions and the CSR: it runs on a
+    // second stream while the tree is built and traversed, and k_node waits
+    // for it.
+    if (nnz > 0) {
+        BGV_CUDA(cudaEventRecord(ev.fork, st));
+        BGV_CUDA(cudaStreamWaitEvent(aux, ev.fork, 0));
+        if (build_plan) {
+            BGV_CUDA(cudaMemsetAsync(s.long_count, 0, sizeof(int32_t), aux));
+            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, aux>>>(
+                K, nnz, csr_off, s.chunk_row, s.long_rows, s.long_count);
+            BGV_TRY(launch_status());
+            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0,
+                                          aux>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
+            BGV_TRY(launch_status());
+        }
+        const int64_t nranges = (nnz + kRange - 1) / kRange;
+        note_launch(), k_attract<<<grid_for(nranges * 32, kThreads, (nranges * 32 + kThreads - 1) / kThreads), kThreads,
+                                   0, aux>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
+                                         s.head, s.tail);
+        BGV_TRY(launch_status());
+        note_launch(), k_long_rows<<<152 * 16, kLongThreads, 0, aux>>>(csr_off, s.long_rows, s.long_count, s.head,
+                                                                       s.tail, s.full);
+        BGV_TRY(launch_status());
+        BGV_CUDA(cudaEventRecord(ev.join, aux));
+    }
     if (batched)
         note_launch(), k_frame_seg<<<G, kThreads, 0, st>>>(pos, koff, s.frame, s.bgraph);
     else
@@ -1265,7 +1324,7 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     BGV_TRY(launch_status());
     BGV_TRY(mark(1));
     int res = 0;
-    BGV_TRY(radix_sort(s.sort, K, nullptr, 2 * L + gbits, st, &res, &hdr->status));
+    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, 2 * L + gbits, st, &res, &hdr->status));
     BGV_TRY(mark(2));
     note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass,
                                                      s.start_count, s.start_levels);
@@ -1301,24 +1360,8 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         BGV_TRY(mark(5));
     }
     BGV_TRY(mark(6));
-    if (nnz > 0) {
-        if (build_plan) {
-            BGV_CUDA(cudaMemsetAsync(s.long_count, 0, sizeof(int32_t), st));
-            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, st>>>(
-                K, nnz, csr_off, s.chunk_row, s.long_rows, s.long_count);
-            BGV_TRY(launch_status());
-            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0,
-                                          st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
-            BGV_TRY(launch_status());
-        }
-        const int64_t nranges = (nnz + kRange - 1) / kRange;
-        note_launch(), k_attract<<<grid_for(nranges * 32, kThreads, (nranges * 32 + kThreads - 1) / kThreads), kThreads,
-                                   0, st>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
-                                         s.head, s.tail);
-        BGV_TRY(launch_status());
-        note_launch(), k_long_rows<<<152 * 16, kLongThreads, 0, st>>>(csr_off, s.long_rows, s.long_count, s.head,
-                                                                       s.tail, s.full);
-        BGV_TRY(launch_status());
+    if (nnz > 0) {  // the attraction ran alongside on the second stream
+        BGV_CUDA(cudaStreamWaitEvent(st, ev.join, 0));
     }
     note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(
         mode, K, csr_off, s.full, s.head, s.tail, mass, pos, s.Frep, p.kg, p.strong_gravity, F, Fprev,

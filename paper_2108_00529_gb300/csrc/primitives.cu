@@ -470,6 +470,302 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     return BGV_OK;
 }
 
+// ----------------------------------------------- sort with a local finish
+// For keys whose order is almost always decided above their lowest 16 bits
+// (Morton keys of spread-out points): LSD passes on bits 16 and up only,
+// which leave every run of equal high bits contiguous and in input order,
+// then each run put in order of its low 16 bits on its own, stably, so the
+// result is the stable sort of the whole key.  A pass over all keys marks
+// every 32-key chunk holding a descent (a key whose low bits are below its
+// predecessor's in the same run) and sorts runs of up to kShortRun keys in
+// registers; a warp skips the longer runs without a marked chunk (equal or
+// already ordered keys: coincident bodies) and ranks those of up to
+// kWarpRun keys; a block sorts each longer run by four 4-bit LSD passes
+// through the idle half of the ping-pong buffers.
+namespace {
+constexpr int kShortRun = 8;
+constexpr int kWarpRun = 256;
+constexpr int kFixThreads = 256;
+
+__device__ __forceinline__ unsigned long long run_key(unsigned long long k, int64_t pos) {
+    return ((k & 0xFFFFull) << 32) | static_cast<unsigned long long>(pos);
+}
+
+// End of the run of equal high bits that starts at `start` (the array is
+// sorted on the high bits).
+__device__ __forceinline__ int64_t run_end(const unsigned long long *keys, int64_t n, int64_t start) {
+    const unsigned long long hi = keys[start] >> 16;
+    int64_t lo = start, up = n;
+    while (lo < up) {
+        const int64_t mid = (lo + up) >> 1;
+        if ((keys[mid] >> 16) <= hi) lo = mid + 1; else up = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__restrict__ keys,
+                                                          uint32_t *__restrict__ vals, int64_t n,
+                                                          uint8_t *__restrict__ descent, uint32_t *__restrict__ runs,
+                                                          uint32_t *run_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
+        bool head = false, desc = false;
+        unsigned long long hi = 0;
+        if (i < n) {
+            const unsigned long long k = keys[i];
+            hi = k >> 16;
+            if (i > 0) {
+                const unsigned long long p = keys[i - 1];
+                desc = (p >> 16) == hi && (k & 0xFFFFull) < (p & 0xFFFFull);
+                head = (p >> 16) != hi;
+            } else {
+                head = true;
+            }
+            head = head && i + 1 < n && (keys[i + 1] >> 16) == hi;  // runs of one need nothing
+        }
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, desc);
+        if (lane == 0) descent[i >> 5] = mask != 0u;
+        if (!head) continue;
+        int r = 2;
+        while (r <= kShortRun && i + r < n && (keys[i + r] >> 16) == hi) ++r;
+        if (r > kShortRun) {
+            runs[atomicAdd(run_count, 1u)] = uint32_t(i);
+            continue;
+        }
+        unsigned long long kk[kShortRun];
+        uint32_t vv[kShortRun];
+        bool ordered = true;
+#pragma unroll
+        for (int a = 0; a < kShortRun; ++a) {
+            kk[a] = a < r ? run_key(keys[i + a], a) : ~0ull;
+            vv[a] = a < r ? vals[i + a] : 0u;
+            if (a > 0) ordered = ordered && kk[a - 1] < kk[a];
+        }
+        if (ordered) continue;
+#pragma unroll
+        for (int a = 0; a < kShortRun; ++a) {
+            if (a < r) {
+                uint32_t rk = 0;
+#pragma unroll
+                for (int c = 0; c < kShortRun; ++c) rk += kk[c] < kk[a] ? 1u : 0u;
+                keys[i + rk] = (hi << 16) | (kk[a] >> 32);
+                vals[i + rk] = vv[a];
+            }
+        }
+    }
+}
+
+// One warp per listed run: a run with no marked chunk is in order already;
+// one of up to kWarpRun keys is ranked in registers (each lane holds up to
+// 8 keys and counts the smaller ones through shuffles); longer ones go on
+// to the block kernel's list.
+__global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__restrict__ keys,
+                                                          uint32_t *__restrict__ vals, int64_t n,
+                                                          const uint8_t *__restrict__ descent,
+                                                          const uint32_t *__restrict__ runs,
+                                                          const uint32_t *run_count, uint32_t *__restrict__ big,
+                                                          uint32_t *big_count) {
+    constexpr int kPer = kWarpRun / 32;
+    const int lane = threadIdx.x & 31;
+    const uint32_t count = *run_count;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < count; q += warps) {
+        const int64_t start = runs[q];
+        const int64_t end = __shfl_sync(0xFFFFFFFFu, lane == 0 ? run_end(keys, n, start) : 0, 0);
+        const int64_t len = end - start;
+        // chunks (start+1)/32 .. (end-1)/32 hold every descent of the run
+        // (and maybe some of its neighbours': a needless sort at worst)
+        bool marked = false;
+        const int64_t c_lo = (start + 1) >> 5, c_hi = (end - 1) >> 5;
+#pragma unroll 4
+        for (int64_t w = (c_lo >> 4) + lane; w <= (c_hi >> 4); w += 32) {  // 16 chunk marks per load
+            const uint4 m = reinterpret_cast<const uint4 *>(descent)[w];
+            const uint32_t word[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+            for (int b = 0; b < 16; ++b) {
+                const int64_t c = 16 * w + b;
+                marked |= c >= c_lo && c <= c_hi && ((word[b >> 2] >> (8 * (b & 3))) & 0xFFu) != 0u;
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, marked)) continue;
+        if (len > kWarpRun) {
+            if (lane == 0) big[atomicAdd(big_count, 1u)] = uint32_t(start);
+            continue;
+        }
+        const unsigned long long hi = keys[start] >> 16;
+        unsigned long long kk[kPer];
+        uint32_t vv[kPer], rank[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t t = lane + 32 * j;
+            kk[j] = t < len ? run_key(keys[start + t], t) : ~0ull;
+            vv[j] = t < len ? vals[start + t] : 0u;
+            rank[j] = 0;
+        }
+#pragma unroll
+        for (int jj = 0; jj < kPer; ++jj) {
+            if (32 * jj >= len) break;
+            for (int src = 0; src < 32; ++src) {
+                const unsigned long long other = __shfl_sync(0xFFFFFFFFu, kk[jj], src);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) rank[j] += other < kk[j] ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t t = lane + 32 * j;
+            if (t < len) {
+                keys[start + rank[j]] = (hi << 16) | (kk[j] >> 32);
+                vals[start + rank[j]] = vv[j];
+            }
+        }
+    }
+}
+
+// One block per listed run: four stable counting passes on 4-bit digits of
+// the low 16 bits, from the run to the same range of the other ping-pong
+// buffer and back.  The digit counts of all four passes come from one read
+// (a stable pass does not change them).  A tile holds kBlockItems keys per
+// thread; a key's place among equal digits comes from __match_any_sync in
+// its warp and the counts of the (item, warp) groups before it, so input
+// order is kept.
+constexpr int kBlockItems = 8;
+__global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *__restrict__ keys,
+                                                           uint32_t *__restrict__ vals,
+                                                           unsigned long long *__restrict__ alt_keys,
+                                                           uint32_t *__restrict__ alt_vals, int64_t n,
+                                                           const uint32_t *__restrict__ big,
+                                                           const uint32_t *big_count) {
+    constexpr int kWarps = kFixThreads / 32;
+    constexpr int kGroups = kBlockItems * kWarps;
+    __shared__ uint32_t hist[4][16];
+    __shared__ uint32_t base[16];
+    __shared__ uint32_t wcount[kGroups][17];
+    __shared__ int64_t end_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t count = *big_count;
+    for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
+        const int64_t start = big[q];
+        if (threadIdx.x == 0) end_sh = run_end(keys, n, start);
+        if (threadIdx.x < 64) (&hist[0][0])[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t len = end_sh - start;
+        unsigned long long *sk = keys + start, *dk = alt_keys + start;
+        uint32_t *sv = vals + start, *dv = alt_vals + start;
+        for (int64_t t0 = 0; t0 < len; t0 += blockDim.x) {
+            const int64_t t = t0 + threadIdx.x;
+            const unsigned long long k = t < len ? sk[t] : 0ull;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int d = t < len ? int((k >> (4 * p)) & 15) : 16;
+                const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+                if (d < 16 && (peers & lt_mask) == 0u) atomicAdd(&hist[p][d], __popc(peers));
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < 4; ++p) {
+            const int shift = 4 * p;
+            if (threadIdx.x == 0) {
+                uint32_t run = 0;
+                for (int d = 0; d < 16; ++d) {
+                    base[d] = run;
+                    run += hist[p][d];
+                }
+            }
+            for (int64_t t0 = 0; t0 < len; t0 += int64_t(blockDim.x) * kBlockItems) {
+                unsigned long long k[kBlockItems];
+                uint32_t v[kBlockItems];
+                int d[kBlockItems];
+#pragma unroll
+                for (int j = 0; j < kBlockItems; ++j) {
+                    const int64_t t = t0 + int64_t(j) * blockDim.x + threadIdx.x;
+                    k[j] = t < len ? sk[t] : 0ull;
+                    v[j] = t < len ? sv[t] : 0u;
+                    d[j] = t < len ? int((k[j] >> shift) & 15) : 16;
+                }
+                for (int e = threadIdx.x; e < kGroups * 17; e += blockDim.x) (&wcount[0][0])[e] = 0;
+                __syncthreads();
+                unsigned peers[kBlockItems];
+#pragma unroll
+                for (int j = 0; j < kBlockItems; ++j) {
+                    peers[j] = __match_any_sync(0xFFFFFFFFu, d[j]);
+                    if ((peers[j] & lt_mask) == 0u) wcount[j * kWarps + warp][d[j]] = __popc(peers[j]);
+                }
+                __syncthreads();
+                if (threadIdx.x < 16) {  // first place of each group's keys of digit threadIdx.x
+                    uint32_t run = base[threadIdx.x];
+                    for (int g = 0; g < kGroups; ++g) {
+                        const uint32_t c = wcount[g][threadIdx.x];
+                        wcount[g][threadIdx.x] = run;
+                        run += c;
+                    }
+                    base[threadIdx.x] = run;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < kBlockItems; ++j) {
+                    if (d[j] < 16) {
+                        const uint32_t pos = wcount[j * kWarps + warp][d[j]] + __popc(peers[j] & lt_mask);
+                        dk[pos] = k[j];
+                        dv[pos] = v[j];
+                    }
+                }
+                __syncthreads();
+            }
+            unsigned long long *tk = sk;
+            sk = dk;
+            dk = tk;
+            uint32_t *tv = sv;
+            sv = dv;
+            dv = tv;
+        }
+    }
+}
+}  // namespace
+
+void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r) {
+    r.descent = c.take<uint8_t>(size_t((cap + 31) / 32 + 16));
+    r.runs = c.take<uint32_t>(size_t(cap / (kShortRun + 1) + 1));
+    r.big = c.take<uint32_t>(size_t(cap / (kWarpRun + 1) + 1));
+    r.counts = c.take<uint32_t>(2);
+}
+
+int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
+                    int *result_buffer, uint32_t *dev_status) {
+    const int passes = (end_bit + 7) / 8;
+    if (!b.vals[0] || end_bit <= 16 || passes > kMaxPasses || n >= (int64_t(1) << 32))
+        return radix_sort(b, n, nullptr, end_bit, s, result_buffer, dev_status);
+    const int items = sort_items(n);
+    uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
+    BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
+    BGV_CUDA(cudaMemsetAsync(r.counts, 0, 2 * sizeof(uint32_t), s));
+    const int64_t count_blocks = (n + kSortTile - 1) / kSortTile;
+    note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
+        b.keys[0], n, nullptr, passes, b.counts);
+    note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
+    BGV_TRY(launch_status());
+    BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles_for(n, items)), s));
+    int cur = 0;
+    for (int p = 2; p < passes; ++p) {
+        BGV_TRY(onesweep_pass(b, n, nullptr, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p), items,
+                              s, dev_status));
+        cur ^= 1;
+    }
+    if (n > 1) {
+        note_launch(), k_fix_runs<<<grid_for(n, kFixThreads, 152 * 8), kFixThreads, 0, s>>>(
+            b.keys[cur], b.vals[cur], n, r.descent, r.runs, r.counts);
+        note_launch(), k_fix_warp<<<152 * 8, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], n, r.descent, r.runs,
+                                                                  r.counts, r.big, r.counts + 1);
+        note_launch(), k_fix_block<<<152 * 2, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                                                   b.vals[cur ^ 1], n, r.big, r.counts + 1);
+        BGV_TRY(launch_status());
+    }
+    *result_buffer = cur;
+    return BGV_OK;
+}
+
 // ------------------------------------------------------------- autotuner
 // Times the sort of 48-bit keys with values at 8 and at 16 keys per thread
 // for sizes 2^14 .. max_keys (powers of four) and sets the cutoff to the
