@@ -188,8 +188,6 @@ constexpr int kSortWarps = kSortThreads / 32;
 // SMs) and bgv_autotune_sort can set it from measurements on this GPU.
 constexpr int kSortItemsBig = 16, kSortItemsSmall = 8;
 std::atomic<int64_t> g_small_sort_cutoff{int64_t(1) << 22};
-constexpr int kSortItems = 16;  // the counting kernel's items per thread
-constexpr int kSortTile = kSortThreads * kSortItems;
 inline int sort_items(int64_t cap) {
     return cap <= g_small_sort_cutoff.load(std::memory_order_relaxed) ? kSortItemsSmall : kSortItemsBig;
 }
@@ -208,23 +206,31 @@ constexpr int kTagShift = 40;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookBack = 4;  // predecessors read per look-back round
 
+// Digit counts of passes first..passes-1.  Each thread loads its kCountItems
+// keys before counting, so their loads are in flight together.
+constexpr int kCountItems = 8;
+constexpr int kCountTile = kSortThreads * kCountItems;
 __global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long long *__restrict__ keys, int64_t cap,
-                                                             const int64_t *d_count, int passes,
+                                                             const int64_t *d_count, int first, int passes,
                                                              uint32_t *__restrict__ counts) {
     __shared__ uint32_t h[kMaxPasses][kBins];
     for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kSortThreads) (&h[0][0])[i] = 0;
-    __syncthreads();
     const int64_t n = load_count(d_count, cap);
-    const int64_t base = int64_t(blockIdx.x) * kSortTile;
-    for (int k = 0; k < kSortItems; ++k) {
+    const int64_t base = int64_t(blockIdx.x) * kCountTile;
+    unsigned long long key[kCountItems];
+#pragma unroll
+    for (int k = 0; k < kCountItems; ++k) {
         const int64_t i = base + int64_t(k) * kSortThreads + threadIdx.x;
-        if (i < n) {
-            const unsigned long long key = keys[i];
-            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][uint32_t(key >> (8 * p)) & 0xFFu], 1u);
-        }
+        key[k] = i < n ? keys[i] : 0ull;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kBins; i += kSortThreads) {
+#pragma unroll
+    for (int k = 0; k < kCountItems; ++k) {
+        if (base + int64_t(k) * kSortThreads + threadIdx.x < n)
+            for (int p = first; p < passes; ++p) atomicAdd(&h[p][uint32_t(key[k] >> (8 * p)) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    for (int i = first * kBins + threadIdx.x; i < passes * kBins; i += kSortThreads) {
         const uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&counts[i], c);
     }
@@ -454,9 +460,9 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
-    const int64_t count_blocks = (cap + kSortTile - 1) / kSortTile;
+    const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
-        b.keys[0], cap, d_count, passes, b.counts);
+        b.keys[0], cap, d_count, 0, passes, b.counts);
     note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
     BGV_TRY(launch_status());
     int cur = 0;
@@ -741,9 +747,9 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_b
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
     BGV_CUDA(cudaMemsetAsync(r.counts, 0, 2 * sizeof(uint32_t), s));
-    const int64_t count_blocks = (n + kSortTile - 1) / kSortTile;
+    const int64_t count_blocks = (n + kCountTile - 1) / kCountTile;
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
-        b.keys[0], n, nullptr, passes, b.counts);
+        b.keys[0], n, nullptr, 2, passes, b.counts);
     note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
     BGV_TRY(launch_status());
     BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles_for(n, items)), s));
