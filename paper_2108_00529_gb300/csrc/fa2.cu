@@ -3,14 +3,17 @@
 // One iteration is a fixed chain of kernels with no host round trip:
 //   k_frame     bounding square of the positions (last-block finalise)
 //   k_keys      fixed-point coordinates U and 2L-bit Morton keys
-//   radix sort  (key, body) pairs -> Morton order
-//   k_gather    bodies in Morton order (position, mass, fixed coords)
-//   k_radix_tree binary radix tree over the sorted keys, one thread per
-//               internal node (exponential + binary search on key prefixes)
-//   k_mom_*     exact prefix sums of (m, m*Ux, m*Uy) in 64/128-bit integers
-//               over the Morton order, so a node's moments are a difference
-//   k_cells     quadtree cells: binary nodes whose 2-bit level exceeds their
-//               parent's; FP32 centre of mass from the exact moments
+//   radix sort  (key, body) pairs -> Morton order: LSD passes on the bits
+//               above 16, then each run of equal high bits ordered locally
+//   k_gather_moments
+//               bodies in Morton order, and exact prefix sums of (m, m*Ux,
+//               m*Uy) in 64/128-bit integers over that order (one pass,
+//               decoupled look-back), so a node's moments are a difference
+//   k_tree      binary radix tree over the sorted keys, one thread per
+//               internal node (exponential + binary search on key prefixes),
+//               and the quadtree cells: binary nodes whose 2-bit level
+//               exceeds their parent's, FP32 centre of mass from the exact
+//               moments
 //   k_preorder  cells and bodies laid out in depth-first pre-order with skip
 //               indices (positions from a prefix count of cells per body)
 //   k_repulse   Barnes-Hut repulsion: one thread per body walks the
@@ -18,10 +21,11 @@
 //               subtree, open -> next element); every body takes its own
 //               opening decisions, so its interaction set is exactly the
 //               one the definition gives
-//   k_attract   attraction over fixed 256-entry ranges of the CSR, one warp
+//   k_attract   attraction over fixed 512-entry ranges of the CSR, one warp
 //               per range (balanced whatever the degrees): segmented scan by
 //               row, row pieces kept per range; k_long_rows sums the rows
-//               spread over many ranges
+//               spread over many ranges.  Both run on a second stream while
+//               the tree is built and walked.
 //   k_node      per node: attraction pieces in range order, gravity, total
 //               force, swing and traction (FP64, compensated); the last block
 //               merges the block partials and updates the global speed
@@ -159,6 +163,14 @@ __global__ void __launch_bounds__(kThreads) k_frame_seg(const float2 *__restrict
 }
 
 // ------------------------------------------------------------------ keys
+// Fixed-point position of a body in its graph's frame: U = floor(2^32 (p -
+// origin) / side) per axis, FP32 with round-to-nearest steps.
+__device__ __forceinline__ uint2 fixed_point(float2 p, float4 fr) {
+    const float ux = __fdiv_rn(__fsub_rn(p.x, fr.x), fr.z);
+    const float uy = __fdiv_rn(__fsub_rn(p.y, fr.y), fr.z);
+    return make_uint2(__float2uint_rz(__fmul_rn(ux, 4294967296.0f)), __float2uint_rz(__fmul_rn(uy, 4294967296.0f)));
+}
+
 // Morton key of the body's fixed-point position in its graph's frame; in the
 // batched form the graph id sits above the 2L Morton bits, so each graph's
 // bodies stay together and form their own subtree.
@@ -166,41 +178,14 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float2 *__restrict__ po
                                                    const float4 *__restrict__ frames,
                                                    const int32_t *__restrict__ bgraph, int L,
                                                    unsigned long long *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals, uint2 *__restrict__ U) {
+                                                   uint32_t *__restrict__ vals) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
         const int g = bgraph ? bgraph[i] : 0;
-        const float4 fr = frames[g];
-        const float2 p = pos[i];
-        const float ux = __fdiv_rn(__fsub_rn(p.x, fr.x), fr.z);
-        const float uy = __fdiv_rn(__fsub_rn(p.y, fr.y), fr.z);
-        const uint32_t Ux = __float2uint_rz(__fmul_rn(ux, 4294967296.0f));
-        const uint32_t Uy = __float2uint_rz(__fmul_rn(uy, 4294967296.0f));
-        const uint32_t qx = Ux >> (32 - L), qy = Uy >> (32 - L);
+        const uint2 U = fixed_point(pos[i], frames[g]);
+        const uint32_t qx = U.x >> (32 - L), qy = U.y >> (32 - L);
         keys[i] = (static_cast<unsigned long long>(g) << (2 * L)) | (spread_bits(qx) << 1) | spread_bits(qy);
         vals[i] = uint32_t(i);
-        U[i] = make_uint2(Ux, Uy);
-    }
-}
-
-// Also clears the per-body cell counters that k_tree fills.
-__global__ void __launch_bounds__(kThreads) k_gather(const uint32_t *__restrict__ perm, int64_t K,
-                                                     const float2 *__restrict__ pos,
-                                                     const uint32_t *__restrict__ mass,
-                                                     const uint2 *__restrict__ U, float4 *__restrict__ body,
-                                                     uint2 *__restrict__ sU, uint32_t *__restrict__ smass,
-                                                     uint32_t *__restrict__ start_count,
-                                                     uint32_t *__restrict__ start_levels) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < K; s += stride) {
-        const uint32_t i = perm[s];
-        const float2 p = pos[i];
-        const uint32_t m = mass[i];
-        body[s] = make_float4(p.x, p.y, __uint2float_rn(m), __int_as_float(int(i)));
-        sU[s] = U[i];
-        smass[s] = m;
-        start_count[s] = 0u;
-        start_levels[s] = 0u;
     }
 }
 
@@ -221,7 +206,7 @@ __device__ __forceinline__ int key_delta(const unsigned long long *__restrict__ 
 // Exact moment prefix sums over the Morton order: P[s] = sum over bodies
 // t < s of (m, m*Ux, m*Uy), in 64/128-bit integers, so every node's moments
 // are P[last+1] - P[first] (exact, order-free).
-constexpr int kMomItems = 8;
+constexpr int kMomItems = 4;
 constexpr int kMomTile = kThreads * kMomItems;
 
 struct Mom {
@@ -243,17 +228,6 @@ __device__ __forceinline__ Mom mom_shfl_up(const Mom &a, int d) {
     const unsigned long long yh = __shfl_up_sync(0xFFFFFFFFu, static_cast<unsigned long long>(a.Y >> 64), d);
     r.X = (u128(xh) << 64) | xl;
     r.Y = (u128(yh) << 64) | yl;
-    return r;
-}
-__device__ __forceinline__ Mom body_mom(const uint2 *sU, const uint32_t *smass, int64_t s, int64_t K) {
-    Mom r{0ull, 0, 0};
-    if (s < K) {
-        const uint2 u = sU[s];
-        const unsigned long long m = smass[s];
-        r.M = m;
-        r.X = u128(m) * u.x;
-        r.Y = u128(m) * u.y;
-    }
     return r;
 }
 __device__ __forceinline__ void mom_store(Mom v, unsigned long long *PM, ulonglong2 *PX, ulonglong2 *PY, int64_t s) {
@@ -296,54 +270,207 @@ __device__ __forceinline__ Mom mom_block_exclusive(Mom v, Mom *total) {
     return ex;
 }
 
-__global__ void __launch_bounds__(kThreads) k_mom_reduce(const uint2 *__restrict__ sU,
-                                                         const uint32_t *__restrict__ smass, int64_t K,
-                                                         unsigned long long *__restrict__ TM,
-                                                         ulonglong2 *__restrict__ TX, ulonglong2 *__restrict__ TY) {
-    const int64_t s0 = int64_t(blockIdx.x) * kMomTile + int64_t(threadIdx.x) * kMomItems;
-    Mom acc{0ull, 0, 0};
+// Sorted bodies and moment prefix sums in one pass, with a decoupled
+// look-back across tiles.  Tiles of kMomTile sorted positions are taken in
+// order from a counter (a tile waits only on tiles already taken, so the
+// waits end); a thread gathers kMomItems consecutive positions: the body's
+// position, mass and index (body[s]), and its fixed-point coordinates
+// recomputed from the position as the keys were.  The tile publishes its
+// total, warp 0 adds the totals or inclusive prefixes of the tiles before it
+// (32 at a time), and the prefixes go out through shared memory so that
+// every store is coalesced.  Also clears the per-body cell counters that
+// k_tree fills.  P[K], the grand total, is written by the last tile.
+struct MomTile {
+    unsigned long long M, xl, xh, yl, yh, pad;
+};
+enum : uint32_t { kMomAgg = 1u, kMomIncl = 2u };  // look-back flags (0: nothing published)
+constexpr int kMomSpinLimit = 1 << 22;
+
+__device__ __forceinline__ void mom_tile_store(MomTile *t, const Mom &v) {
+    t->M = v.M;
+    t->xl = static_cast<unsigned long long>(v.X);
+    t->xh = static_cast<unsigned long long>(v.X >> 64);
+    t->yl = static_cast<unsigned long long>(v.Y);
+    t->yh = static_cast<unsigned long long>(v.Y >> 64);
+}
+__device__ __forceinline__ Mom mom_tile_load(const MomTile *t) {  // from L2: written by other blocks
+    return Mom{__ldcg(&t->M), (u128(__ldcg(&t->xh)) << 64) | __ldcg(&t->xl),
+               (u128(__ldcg(&t->yh)) << 64) | __ldcg(&t->yl)};
+}
+__device__ __forceinline__ Mom mom_warp_sum(Mom v) {
 #pragma unroll
-    for (int k = 0; k < kMomItems; ++k) acc = mom_add(acc, body_mom(sU, smass, s0 + k, K));
-    Mom tot;
-    mom_block_exclusive(acc, &tot);
-    if (threadIdx.x == 0) mom_store(tot, TM, TX, TY, blockIdx.x);
-}
-
-__global__ void __launch_bounds__(kThreads) k_mom_tiles(unsigned long long *TM, ulonglong2 *TX, ulonglong2 *TY,
-                                                        int64_t tiles) {
-    Mom carry{0ull, 0, 0};
-    for (int64_t base = 0; base < tiles; base += kThreads) {
-        const int64_t t = base + threadIdx.x;
-        const Mom v = t < tiles ? mom_load(TM, TX, TY, t) : Mom{0ull, 0, 0};
-        Mom tot;
-        const Mom ex = mom_block_exclusive(v, &tot);
-        if (t < tiles) mom_store(mom_add(carry, ex), TM, TX, TY, t);
-        carry = mom_add(carry, tot);
+    for (int d = 16; d > 0; d >>= 1) {
+        Mom o;
+        o.M = __shfl_xor_sync(0xFFFFFFFFu, v.M, d);
+        const unsigned long long xl = __shfl_xor_sync(0xFFFFFFFFu, static_cast<unsigned long long>(v.X), d);
+        const unsigned long long xh = __shfl_xor_sync(0xFFFFFFFFu, static_cast<unsigned long long>(v.X >> 64), d);
+        const unsigned long long yl = __shfl_xor_sync(0xFFFFFFFFu, static_cast<unsigned long long>(v.Y), d);
+        const unsigned long long yh = __shfl_xor_sync(0xFFFFFFFFu, static_cast<unsigned long long>(v.Y >> 64), d);
+        o.X = (u128(xh) << 64) | xl;
+        o.Y = (u128(yh) << 64) | yl;
+        v = mom_add(v, o);
     }
+    return v;
+}
+// Staging slot of tile element e: one 16-byte pad after every 8 elements, so
+// the per-thread writes (stride 8) fall in different banks.
+__device__ __forceinline__ int stage_slot(int e) { return e + (e >> 3); }
+__device__ __forceinline__ uint4 u128_words(u128 v) {
+    return make_uint4(uint32_t(v), uint32_t(v >> 32), uint32_t(v >> 64), uint32_t(v >> 96));
+}
+__device__ __forceinline__ ulonglong2 words_u128(uint4 v) {
+    return make_ulonglong2((static_cast<unsigned long long>(v.y) << 32) | v.x,
+                           (static_cast<unsigned long long>(v.w) << 32) | v.z);
 }
 
-__global__ void __launch_bounds__(kThreads) k_mom_down(const uint2 *__restrict__ sU,
-                                                       const uint32_t *__restrict__ smass, int64_t K,
-                                                       const unsigned long long *__restrict__ TM,
-                                                       const ulonglong2 *__restrict__ TX,
-                                                       const ulonglong2 *__restrict__ TY,
-                                                       unsigned long long *__restrict__ PM,
-                                                       ulonglong2 *__restrict__ PX, ulonglong2 *__restrict__ PY) {
-    const int64_t s0 = int64_t(blockIdx.x) * kMomTile + int64_t(threadIdx.x) * kMomItems;
-    Mom items[kMomItems];
+__global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
+    const uint32_t *__restrict__ perm, int64_t K, const float2 *__restrict__ pos, const uint32_t *__restrict__ mass,
+    const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
+    unsigned long long *__restrict__ PM, ulonglong2 *__restrict__ PX, ulonglong2 *__restrict__ PY,
+    uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
+    MomTile *incl, uint32_t *dev_status) {
+    __shared__ uint4 stage[kMomTile + kMomTile / 8];
+    __shared__ unsigned tile_sh;
+    __shared__ unsigned long long pre_sh[5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tiles = (K + kMomTile - 1) / kMomTile;
+    if (threadIdx.x == 0) tile_sh = atomicAdd(&flags[tiles], 1u);
+    __syncthreads();
+    const int64_t tile = tile_sh;
+    if (tile >= tiles) return;
+    const int64_t t0 = tile * kMomTile;
+    const int64_t s0 = t0 + int64_t(threadIdx.x) * kMomItems;
+    // sorted position s holds body perm[s]
+    uint32_t m[kMomItems], ux[kMomItems], uy[kMomItems];
     Mom acc{0ull, 0, 0};
 #pragma unroll
     for (int k = 0; k < kMomItems; ++k) {
-        items[k] = body_mom(sU, smass, s0 + k, K);
-        acc = mom_add(acc, items[k]);
+        const int64_t sk = s0 + k;
+        uint4 b = make_uint4(0u, 0u, 0u, 0u);
+        m[k] = 0u;
+        ux[k] = 0u;
+        uy[k] = 0u;
+        if (sk < K) {
+            const uint32_t i = perm[sk];
+            const float2 p = pos[i];
+            const uint2 U = fixed_point(p, frames[bgraph ? bgraph[i] : 0]);
+            m[k] = mass[i];
+            ux[k] = U.x;
+            uy[k] = U.y;
+            b = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(__uint2float_rn(m[k])), i);
+        }
+        stage[stage_slot(threadIdx.x * kMomItems + k)] = b;
+        acc.M += m[k];
+        acc.X += u128(m[k]) * ux[k];
+        acc.Y += u128(m[k]) * uy[k];
     }
-    Mom tot;
-    Mom run = mom_add(mom_load(TM, TX, TY, blockIdx.x), mom_block_exclusive(acc, &tot));
+    Mom total;
+    Mom run = mom_block_exclusive(acc, &total);  // synchronises: the staged bodies are complete
+    if (threadIdx.x == 0) {
+        mom_tile_store(tile == 0 ? &incl[0] : &agg[tile], total);
+        __threadfence();
+        atomicExch(&flags[tile], tile == 0 ? kMomIncl : kMomAgg);
+    }
 #pragma unroll
-    for (int k = 0; k < kMomItems; ++k) {
-        const int64_t s = s0 + k;
-        if (s <= K) mom_store(run, PM, PX, PY, s);
-        run = mom_add(run, items[k]);
+    for (int r = 0; r < kMomItems; ++r) {
+        const int e = r * kThreads + threadIdx.x;
+        const int64_t sk = t0 + e;
+        if (sk < K) {
+            const uint4 v = stage[stage_slot(e)];
+            body[sk] = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                                   __uint_as_float(v.w));
+            start_count[sk] = 0u;
+            start_levels[sk] = 0u;
+        }
+    }
+    if (warp == 0) {
+        Mom excl{0ull, 0, 0};
+        int64_t j = tile - 1;
+        int spins = 0;
+        while (j >= 0) {
+            const int64_t idx = j - lane;  // lane 0 reads the nearest predecessor
+            const uint32_t f = idx >= 0 ? *reinterpret_cast<volatile uint32_t *>(&flags[idx]) : kMomIncl;
+            const unsigned inc_mask = __ballot_sync(0xFFFFFFFFu, f == kMomIncl);
+            const unsigned none_mask = __ballot_sync(0xFFFFFFFFu, f == 0u);
+            const unsigned first = inc_mask & (0u - inc_mask);
+            const unsigned need = inc_mask ? (first << 1) - 1u : 0xFFFFFFFFu;
+            if (none_mask & need) {  // a tile up to the first inclusive one has published nothing yet
+                if (++spins > kMomSpinLimit) {
+                    if (lane == 0) raise_status(dev_status, BGV_DEV_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            __threadfence();
+            Mom v{0ull, 0, 0};
+            if (((need >> lane) & 1u) && idx >= 0) v = mom_tile_load(f == kMomIncl ? &incl[idx] : &agg[idx]);
+            excl = mom_add(excl, mom_warp_sum(v));
+            if (inc_mask) break;
+            j -= 32;
+        }
+        if (lane == 0) {
+            if (tile > 0) {
+                mom_tile_store(&incl[tile], mom_add(excl, total));
+                __threadfence();
+                atomicExch(&flags[tile], kMomIncl);
+            }
+            pre_sh[0] = excl.M;
+            pre_sh[1] = static_cast<unsigned long long>(excl.X);
+            pre_sh[2] = static_cast<unsigned long long>(excl.X >> 64);
+            pre_sh[3] = static_cast<unsigned long long>(excl.Y);
+            pre_sh[4] = static_cast<unsigned long long>(excl.Y >> 64);
+        }
+    }
+    __syncthreads();
+    const Mom tile_pre{pre_sh[0], (u128(pre_sh[2]) << 64) | pre_sh[1], (u128(pre_sh[4]) << 64) | pre_sh[3]};
+    run = mom_add(run, tile_pre);
+    if (tile == tiles - 1 && threadIdx.x == 0) mom_store(mom_add(tile_pre, total), PM, PX, PY, K);
+    // the prefix sums, one component at a time through the staging buffer
+    unsigned long long *stage8 = reinterpret_cast<unsigned long long *>(stage);
+    {
+        unsigned long long r = run.M;
+#pragma unroll
+        for (int k = 0; k < kMomItems; ++k) {
+            stage8[stage_slot(threadIdx.x * kMomItems + k)] = r;
+            r += m[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMomItems; ++r) {
+        const int e = r * kThreads + threadIdx.x;
+        if (t0 + e < K) PM[t0 + e] = stage8[stage_slot(e)];
+    }
+    __syncthreads();
+    {
+        u128 r = run.X;
+#pragma unroll
+        for (int k = 0; k < kMomItems; ++k) {
+            stage[stage_slot(threadIdx.x * kMomItems + k)] = u128_words(r);
+            r += u128(m[k]) * ux[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMomItems; ++r) {
+        const int e = r * kThreads + threadIdx.x;
+        if (t0 + e < K) PX[t0 + e] = words_u128(stage[stage_slot(e)]);
+    }
+    __syncthreads();
+    {
+        u128 r = run.Y;
+#pragma unroll
+        for (int k = 0; k < kMomItems; ++k) {
+            stage[stage_slot(threadIdx.x * kMomItems + k)] = u128_words(r);
+            r += u128(m[k]) * uy[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMomItems; ++r) {
+        const int e = r * kThreads + threadIdx.x;
+        if (t0 + e < K) PY[t0 + e] = words_u128(stage[stage_slot(e)]);
     }
 }
 
@@ -1132,14 +1259,13 @@ struct Fa2Scratch {
     float2 *rowst;         // batched form: per-row swing, traction
     SortBuffers sort;
     RunFixBuffers runfix;
-    uint2 *U;
-    float4 *body;
-    uint2 *sU;
-    uint32_t *smass;
+    float4 *body;          // sorted bodies: x, y, mass, index
     int2 *range;           // per binary node that is a cell: its bodies
     int8_t *cell_level;    // per binary node: its level if a cell, else -1
-    unsigned long long *PM, *TM;   // moment prefix sums, per-tile sums
-    ulonglong2 *PX, *PY, *TX, *TY;
+    unsigned long long *PM;  // moment prefix sums, K + 1 entries
+    ulonglong2 *PX, *PY;
+    uint32_t *mom_flags;   // look-back flags per tile, then the tile counter
+    MomTile *mom_agg, *mom_incl;
     float4 *cell;          // per binary node: centre, mass, side^2 (cells only)
     uint32_t *start_count; // cells per first body
     uint32_t *start_levels;  // levels of the cells per first body (bit mask)
@@ -1167,19 +1293,16 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.rowst = batched ? c.take<float2>(k) : nullptr;
     carve_sort(c, int64_t(k), true, s.sort);
     carve_run_fix(c, int64_t(k), s.runfix);
-    s.U = c.take<uint2>(k);
     s.body = c.take<float4>(k);
-    s.sU = c.take<uint2>(k);
-    s.smass = c.take<uint32_t>(k);
     const size_t tiles = (k + kMomTile - 1) / kMomTile;
     s.range = c.take<int2>(k);
     s.cell_level = c.take<int8_t>(k);
     s.PM = c.take<unsigned long long>(k + 1);
     s.PX = c.take<ulonglong2>(k + 1);
     s.PY = c.take<ulonglong2>(k + 1);
-    s.TM = c.take<unsigned long long>(tiles);
-    s.TX = c.take<ulonglong2>(tiles);
-    s.TY = c.take<ulonglong2>(tiles);
+    s.mom_flags = c.take<uint32_t>(tiles + 1);
+    s.mom_agg = c.take<MomTile>(tiles);
+    s.mom_incl = c.take<MomTile>(tiles);
     s.cell = c.take<float4>(k);
     s.start_count = c.take<uint32_t>(k + 1);
     s.start_levels = c.take<uint32_t>(k);
@@ -1319,25 +1442,24 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
     const int gk = grid_for(K, kThreads, 152 * 16);
-    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
-                                                   s.U);
+    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0]);
     BGV_TRY(launch_status());
     BGV_TRY(mark(1));
     int res = 0;
     BGV_TRY(radix_sort_high(s.sort, s.runfix, K, 2 * L + gbits, st, &res, &hdr->status));
     BGV_TRY(mark(2));
-    note_launch(), k_gather<<<gk, kThreads, 0, st>>>(s.sort.vals[res], K, pos, mass, s.U, s.body, s.sU, s.smass,
-                                                     s.start_count, s.start_levels);
-    BGV_TRY(launch_status());
+    {
+        const int64_t tiles = (K + kMomTile - 1) / kMomTile;
+        BGV_CUDA(cudaMemsetAsync(s.mom_flags, 0, sizeof(uint32_t) * size_t(tiles + 1), st));
+        note_launch(), k_gather_moments<<<unsigned(tiles), kThreads, 0, st>>>(
+            s.sort.vals[res], K, pos, mass, s.frame, s.bgraph, s.body, s.PM, s.PX, s.PY, s.start_count,
+            s.start_levels, s.mom_flags, s.mom_agg, s.mom_incl, &hdr->status);
+        BGV_TRY(launch_status());
+    }
     BGV_TRY(mark(3));
     if (K >= 2) {
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         const unsigned gi = unsigned((K - 1 + kThreads - 1) / kThreads);
-        const unsigned tiles = unsigned((K + kMomTile - 1) / kMomTile);
-        note_launch(), k_mom_reduce<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY);
-        note_launch(), k_mom_tiles<<<1, kThreads, 0, st>>>(s.TM, s.TX, s.TY, tiles);
-        note_launch(), k_mom_down<<<tiles, kThreads, 0, st>>>(s.sU, s.smass, K, s.TM, s.TX, s.TY, s.PM, s.PX, s.PY);
-        BGV_TRY(launch_status());
         note_launch(), k_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph,
                                                        s.PM, s.PX, s.PY, s.range, s.cell_level, s.cell,
                                                        s.start_count, s.start_levels, &hdr->tree_nodes);
