@@ -276,8 +276,8 @@ __device__ __forceinline__ Mom mom_block_exclusive(Mom v, Mom *total) {
 // waits end); a thread gathers kMomItems consecutive positions: the body's
 // position, mass and index (body[s]), and its fixed-point coordinates
 // recomputed from the position as the keys were.  The tile publishes its
-// total, warp 0 adds the totals or inclusive prefixes of the tiles before it
-// (32 at a time), and the prefixes go out through shared memory so that
+// total, the block adds the totals or inclusive prefixes of the tiles before
+// it (up to kMomLookBack at a time), and the prefixes go out through shared memory so that
 // every store is coalesced.  Also clears the per-body cell counters that
 // k_tree fills.  P[K], the grand total, is written by the last tile.
 struct MomTile {
@@ -285,6 +285,8 @@ struct MomTile {
 };
 enum : uint32_t { kMomAgg = 1u, kMomIncl = 2u };  // look-back flags (0: nothing published)
 constexpr int kMomSpinLimit = 1 << 22;
+constexpr int kMomLBItems = 4;                          // predecessors per thread and round
+constexpr int kMomLookBack = kThreads * kMomLBItems;    // predecessors per round
 
 __device__ __forceinline__ void mom_tile_store(MomTile *t, const Mom &v) {
     t->M = v.M;
@@ -323,7 +325,7 @@ __device__ __forceinline__ ulonglong2 words_u128(uint4 v) {
                            (static_cast<unsigned long long>(v.w) << 32) | v.z);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
+__global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     const uint32_t *__restrict__ perm, int64_t K, const float2 *__restrict__ pos, const uint32_t *__restrict__ mass,
     const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
     unsigned long long *__restrict__ PM, ulonglong2 *__restrict__ PX, ulonglong2 *__restrict__ PY,
@@ -331,7 +333,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
     MomTile *incl, uint32_t *dev_status) {
     __shared__ uint4 stage[kMomTile + kMomTile / 8];
     __shared__ unsigned tile_sh;
-    __shared__ unsigned long long pre_sh[5];
+    __shared__ int near_sh;
+    __shared__ unsigned long long red_sh[kThreads / 32][5];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tiles = (K + kMomTile - 1) / kMomTile;
     if (threadIdx.x == 0) tile_sh = atomicAdd(&flags[tiles], 1u);
@@ -383,20 +386,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
             start_levels[sk] = 0u;
         }
     }
-    if (warp == 0) {
-        Mom excl{0ull, 0, 0};
-        int64_t j = tile - 1;
+    // Look-back by the whole block, kMomLookBack predecessors per round: the
+    // nearest tile with an inclusive prefix in the window ends it; the tiles
+    // after it must have published their totals.
+    Mom excl{0ull, 0, 0};
+    {
+        int64_t hi = tile - 1;
         int spins = 0;
-        while (j >= 0) {
-            const int64_t idx = j - lane;  // lane 0 reads the nearest predecessor
-            const uint32_t f = idx >= 0 ? *reinterpret_cast<volatile uint32_t *>(&flags[idx]) : kMomIncl;
-            const unsigned inc_mask = __ballot_sync(0xFFFFFFFFu, f == kMomIncl);
-            const unsigned none_mask = __ballot_sync(0xFFFFFFFFu, f == 0u);
-            const unsigned first = inc_mask & (0u - inc_mask);
-            const unsigned need = inc_mask ? (first << 1) - 1u : 0xFFFFFFFFu;
-            if (none_mask & need) {  // a tile up to the first inclusive one has published nothing yet
+        while (hi >= 0) {
+            if (threadIdx.x == 0) near_sh = -1;
+            __syncthreads();
+            uint32_t f[kMomLBItems];
+#pragma unroll
+            for (int r = 0; r < kMomLBItems; ++r) {
+                const int64_t idx = hi - (r * kThreads + threadIdx.x);
+                f[r] = idx >= 0 ? *reinterpret_cast<volatile uint32_t *>(&flags[idx]) : 0u;
+                if (idx >= 0 && f[r] == kMomIncl) atomicMax(&near_sh, int(idx));
+            }
+            __syncthreads();
+            const int64_t near = near_sh;
+            const int64_t win_lo = hi - kMomLookBack + 1 > 0 ? hi - kMomLookBack + 1 : 0;
+            const int64_t lo = near >= 0 ? near : win_lo;
+            bool pending = false;
+#pragma unroll
+            for (int r = 0; r < kMomLBItems; ++r) {
+                const int64_t idx = hi - (r * kThreads + threadIdx.x);
+                pending |= idx >= lo && f[r] == 0u;
+            }
+            if (__syncthreads_or(pending)) {
                 if (++spins > kMomSpinLimit) {
-                    if (lane == 0) raise_status(dev_status, BGV_DEV_TIMEOUT);
+                    if (threadIdx.x == 0) raise_status(dev_status, BGV_DEV_TIMEOUT);
                     break;
                 }
                 __nanosleep(64);
@@ -404,26 +423,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
             }
             __threadfence();
             Mom v{0ull, 0, 0};
-            if (((need >> lane) & 1u) && idx >= 0) v = mom_tile_load(f == kMomIncl ? &incl[idx] : &agg[idx]);
-            excl = mom_add(excl, mom_warp_sum(v));
-            if (inc_mask) break;
-            j -= 32;
-        }
-        if (lane == 0) {
-            if (tile > 0) {
-                mom_tile_store(&incl[tile], mom_add(excl, total));
-                __threadfence();
-                atomicExch(&flags[tile], kMomIncl);
+#pragma unroll
+            for (int r = 0; r < kMomLBItems; ++r) {
+                const int64_t idx = hi - (r * kThreads + threadIdx.x);
+                if (idx >= lo) v = mom_add(v, mom_tile_load(f[r] == kMomIncl ? &incl[idx] : &agg[idx]));
             }
-            pre_sh[0] = excl.M;
-            pre_sh[1] = static_cast<unsigned long long>(excl.X);
-            pre_sh[2] = static_cast<unsigned long long>(excl.X >> 64);
-            pre_sh[3] = static_cast<unsigned long long>(excl.Y);
-            pre_sh[4] = static_cast<unsigned long long>(excl.Y >> 64);
+            v = mom_warp_sum(v);
+            if (lane == 0) {
+                red_sh[warp][0] = v.M;
+                red_sh[warp][1] = static_cast<unsigned long long>(v.X);
+                red_sh[warp][2] = static_cast<unsigned long long>(v.X >> 64);
+                red_sh[warp][3] = static_cast<unsigned long long>(v.Y);
+                red_sh[warp][4] = static_cast<unsigned long long>(v.Y >> 64);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w)
+                excl = mom_add(excl, Mom{red_sh[w][0], (u128(red_sh[w][2]) << 64) | red_sh[w][1],
+                                         (u128(red_sh[w][4]) << 64) | red_sh[w][3]});
+            if (near >= 0) break;
+            hi = lo - 1;
         }
     }
-    __syncthreads();
-    const Mom tile_pre{pre_sh[0], (u128(pre_sh[2]) << 64) | pre_sh[1], (u128(pre_sh[4]) << 64) | pre_sh[3]};
+    if (threadIdx.x == 0 && tile > 0) {
+        mom_tile_store(&incl[tile], mom_add(excl, total));
+        __threadfence();
+        atomicExch(&flags[tile], kMomIncl);
+    }
+    const Mom tile_pre = excl;
+    __syncthreads();  // the bodies have left the staging buffer
     run = mom_add(run, tile_pre);
     if (tile == tiles - 1 && threadIdx.x == 0) mom_store(mom_add(tile_pre, total), PM, PX, PY, K);
     // the prefix sums, one component at a time through the staging buffer
