@@ -204,7 +204,8 @@ constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFla
 constexpr unsigned long long kCountMask = (1ull << 40) - 1;
 constexpr int kTagShift = 40;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kLookBack = 4;  // predecessors read per look-back round
+constexpr int kLookBack = 4;       // predecessors read per look-back round (16 keys per thread)
+constexpr int kLookBackWide = 16;  // the same with 8 keys per thread (keys staged first)
 
 // Digit counts of passes first..passes-1.  Each thread loads its kCountItems
 // keys before counting, so their loads are in flight together.
@@ -244,6 +245,47 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_offsets(uint32_t *counts,
         const uint32_t ex = block_exclusive(c, &tot);
         counts[p * kBins + threadIdx.x] = ex;
     }
+}
+
+// Decoupled look-back of digit d for tile `tile`: adds the counts published
+// by the tiles before it, kW at a time (independent loads in flight
+// together), down to the nearest inclusive prefix; stops at a tile that has
+// published nothing yet and waits for it.  Publishes the tile's inclusive
+// count and returns the exclusive one.
+template <int kW>
+__device__ __forceinline__ unsigned long long look_back(volatile unsigned long long *st, int64_t tile, int d,
+                                                        unsigned long long tag, uint32_t total, uint32_t *dev_status) {
+    if (tile == 0) return 0ull;
+    unsigned long long excl = 0;
+    int64_t j = tile - 1;
+    int spins = 0;
+    while (true) {
+        unsigned long long v[kW];
+#pragma unroll
+        for (int q = 0; q < kW; ++q) v[q] = j - q >= 0 ? st[(j - q) * kBins + d] : (kFlagIncl | tag);
+        int q = 0;
+        bool done = false;
+        for (; q < kW; ++q) {
+            const unsigned long long flag = (v[q] & ~(kFlagMask | kCountMask)) == tag ? (v[q] & kFlagMask) : 0ull;
+            if (flag == 0) break;
+            excl += v[q] & kCountMask;
+            if (flag == kFlagIncl) {
+                done = true;
+                break;
+            }
+        }
+        if (done) break;
+        j -= q;
+        if (q < kW) {
+            if (++spins > kSpinLimit) {
+                raise_status(dev_status, BGV_DEV_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    st[tile * kBins + d] = kFlagIncl | tag | (excl + total);
+    return excl;
 }
 
 // With 8 keys per thread, 4 blocks fit on an SM (registers capped at 64), so
@@ -317,80 +359,43 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
         __syncwarp();
     }
     __syncthreads();
-    {
-        // thread d owns digit d: warp prefixes, tile total, look-back
-        const int d = threadIdx.x;
-        uint32_t total = 0;
+    // thread d owns digit d: warp prefixes and tile total, published at once
+    const int d = threadIdx.x;
+    uint32_t total = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = cnt[w][d];
-            cnt[w][d] = total;
-            total += c;
-        }
-        if (kStage) {
-            uint32_t all;
-            local_start[d] = block_exclusive(total, &all);
-        }
-        volatile unsigned long long *st = status;
-        unsigned long long excl = 0;
-        if (tile == 0) {
-            st[d] = kFlagIncl | tag | total;
-        } else {
-            st[tile * kBins + d] = kFlagAgg | tag | total;
-            // Look back kLookBack predecessors per round (independent loads in
-            // flight together): add aggregates up to the nearest inclusive
-            // prefix; stop at a tile that has published nothing yet and
-            // wait for it.
-            int64_t j = tile - 1;
-            int spins = 0;
-            while (true) {
-                unsigned long long v[kLookBack];
-#pragma unroll
-                for (int q = 0; q < kLookBack; ++q) v[q] = j - q >= 0 ? st[(j - q) * kBins + d] : (kFlagIncl | tag);
-                int q = 0;
-                bool done = false;
-                for (; q < kLookBack; ++q) {
-                    const unsigned long long flag =
-                        (v[q] & ~(kFlagMask | kCountMask)) == tag ? (v[q] & kFlagMask) : 0ull;
-                    if (flag == 0) break;
-                    excl += v[q] & kCountMask;
-                    if (flag == kFlagIncl) {
-                        done = true;
-                        break;
-                    }
-                }
-                if (done) break;
-                j -= q;
-                if (q < kLookBack) {
-                    if (++spins > kSpinLimit) {
-                        raise_status(dev_status, BGV_DEV_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            st[tile * kBins + d] = kFlagIncl | tag | (excl + total);
-        }
-        tile_base[d] = digit_base[d] + uint32_t(excl);
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = cnt[w][d];
+        cnt[w][d] = total;
+        total += c;
     }
-    __syncthreads();
+    volatile unsigned long long *st = status;
+    st[tile * kBins + d] = (tile == 0 ? kFlagIncl : kFlagAgg) | tag | total;
     if (kStage) {
+        // keys go to their place in the tile before the look-back, which
+        // frees their registers for a wider look-back window
+        uint32_t all;
+        local_start[d] = block_exclusive(total, &all);
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
             const int64_t i = base + int64_t(k) * 32 + lane;
             if (i >= n) continue;
-            const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
-            const uint32_t slot = local_start[d] + cnt[warp][d] + rank[k];
+            const uint32_t dk = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+            const uint32_t slot = local_start[dk] + cnt[warp][dk] + rank[k];
             skey[slot] = key[k];
             if (kVals) sval[slot] = val[k];
         }
-        __syncthreads();
+    }
+    tile_base[d] = digit_base[d] + uint32_t(look_back<kStage ? kLookBackWide : kLookBack>(st, tile, d, tag, total,
+                                                                                         dev_status));
+    __syncthreads();
+    if (kStage) {
         const int64_t t0 = tile * kTileKeys;
         const int tile_n = n - t0 < kTileKeys ? int(n - t0) : kTileKeys;
         for (int slot = threadIdx.x; slot < tile_n; slot += kSortThreads) {
             const unsigned long long k = skey[slot];
-            const uint32_t d = static_cast<uint32_t>(k >> shift) & 0xFFu;
-            const uint32_t pos = tile_base[d] + uint32_t(slot) - local_start[d];
+            const uint32_t dk = static_cast<uint32_t>(k >> shift) & 0xFFu;
+            const uint32_t pos = tile_base[dk] + uint32_t(slot) - local_start[dk];
             kout[pos] = k;
             if (kVals) vout[pos] = sval[slot];
         }
