@@ -45,7 +45,7 @@ FLOPS_PER_INTERACTION = 12     # dx, dy, d2 (3), division, k*m*M (2), two FMAs (
 # DRAM bytes (read + write) of one k_repulse launch on the rmat20 supergraph,
 # from the ncu capture summarised in profiles/k_repulse_rmat20.md; valid only
 # while k_repulse is unchanged since that capture.
-REPULSE_TRAFFIC = {"rmat20": 51_580_416}
+REPULSE_TRAFFIC = {"rmat20": 51_784_448}
 
 WORKLOADS = {
     "rmat20": dict(desc="R-MAT scale 20 (1,048,576 node ids), 10,000,000 unique edges, a,b,c,d=.57,.19,.19,.05, "
@@ -242,10 +242,10 @@ def gpu_arm(args, dist: Dist):
     fp = B.bgv_fa2_default_params()
     K_host = torch.zeros(2, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    sampled = min(10, iters)
+    sampled = max(1, min(args.stage_iterations, iters))
 
     def step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         with torch.cuda.stream(s):
             ev[0].record(s)
             B.bgv_sketch_degrees(E, m, n, rows, width, 1, S, dh, ws_sk, stream=s)
@@ -261,6 +261,7 @@ def gpu_arm(args, dist: Dist):
         K = int(K_host[0].item())
         nnz = 2 * int(K_host[1].item())
         with torch.cuda.stream(s):
+            ev[4].record(s)  # the gap before it is the host reading K and Es
             B.bgv_fa2_init(K, fp, pos, Fprev, speed, stream=s)
             # the iterations run as replays of one captured step, as in
             # bgv_layout; the last `sampled` run launch by launch with events
@@ -268,11 +269,11 @@ def gpu_arm(args, dist: Dist):
             B.bgv_fa2_run(K, nnz, off, adj, cw, mass, fp, iters - sampled, 1, pos, F, Fprev, speed, ws_fa, stream=s)
             stages = B.bgv_fa2_run_timed(K, nnz, off, adj, cw, mass, fp, sampled, pos, F, Fprev, speed, ws_fa,
                                          stream=s)
-            ev[4].record(s)
+            ev[5].record(s)
         s.synchronize()
-        t = [ev[0].elapsed_time(ev[i]) for i in range(1, 5)]
-        return dict(total=t[3], sketch=t[0], communities=t[1] - t[0], supergraph=t[2] - t[1], fa2=t[3] - t[2],
-                    fa2_stages=[x / sampled for x in stages], K=K)
+        t = [ev[0].elapsed_time(ev[i]) for i in range(1, 6)]
+        return dict(total=t[4], sketch=t[0], communities=t[1] - t[0], supergraph=t[2] - t[1], host_k=t[3] - t[2],
+                    fa2=t[4] - t[3], fa2_stages=[x / sampled for x in stages], K=K)
 
     def flush_l2():
         flush.zero_()
@@ -304,7 +305,8 @@ def gpu_arm(args, dist: Dist):
     K = results[-1]["K"]
     Es = int(Esd.item())
     m_cut = int(sw[:Es].to(torch.int64).sum().item())
-    stage_ms = {k: float(np.mean([r[k] for r in results])) for k in ("sketch", "communities", "supergraph", "fa2")}
+    stage_ms = {k: float(np.mean([r[k] for r in results]))
+                for k in ("sketch", "communities", "supergraph", "host_k", "fa2")}
     fa2_stage_ms = {nm: float(np.mean([r["fa2_stages"][i] for r in results]))
                     for i, nm in enumerate(B.FA2_STAGE_NAMES)}
 
@@ -441,7 +443,7 @@ def gpu_arm_whole(args, dist: Dist):
     nnz_h = torch.zeros(1, dtype=torch.int64).pin_memory()
     K_h = torch.zeros(1, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    sampled = min(10, iters)
+    sampled = max(1, min(args.stage_iterations, iters))
 
     def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -795,6 +797,9 @@ def main():
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
     ap.add_argument("--fa2-iterations", type=int, default=0,
                     help="override the workload's FA2 iteration count (short profiling runs only)")
+    ap.add_argument("--stage-iterations", type=int, default=10,
+                    help="FA2 iterations per timed step launched one by one with events at the stage boundaries "
+                         "(the per-stage times and the roofline's kernel duration); the others replay a graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--sweep", action="store_true",
