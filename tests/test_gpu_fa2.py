@@ -78,6 +78,36 @@ def test_coincident_points_and_duplicates():
         assert G.rel_err(r["Fr"], Fr0) <= TOL
 
 
+@pytest.mark.parametrize("sizes", [(3000,), (100, 150, 40), (5, 7, 3, 9, 12)])
+def test_dense_clusters_inside_one_fine_cell(sizes):
+    # Clusters smaller than 2^-16 of the frame (side 2000, cells of 0.03 at
+    # that level) share the Morton bits above 16: long runs that the sort
+    # orders run by run on the low bits (in registers up to 8 keys, by a warp
+    # up to 256, by a block above).  The tree must equal the oracle's: the
+    # interaction counts are equal exactly.  Inside such a cluster the
+    # spacing is below what FP32 cell centres resolve in this frame (about
+    # 1e-4), so forces are compared on the bodies outside the clusters.
+    rng = np.random.default_rng(len(sizes))
+    parts = [np.array([[-1000.0, -1000.0], [1000.0, 1000.0]]), rng.random((500, 2)) * 2000 - 1000]
+    for k in sizes:
+        parts.append(rng.random(2) * 1000 - 500 + rng.random((k, 2)) * 0.02)
+    pos = np.concatenate(parts).astype(np.float32)
+    outside = np.zeros(pos.shape[0], bool)
+    outside[:502] = True
+    order = rng.permutation(pos.shape[0])
+    pos, outside = pos[order], outside[order]
+    K = pos.shape[0]
+    mass = rng.integers(1, 9, K).astype(np.uint32)
+    off, adj, w = G.csr_from_edges(graphgen.random_graph(K, 2 * K, seed=7), K)
+    for leaf_cap in (1, 8):
+        p = FA2Params(theta=1.2, leaf_cap=leaf_cap)
+        r = G.fa2_forces(pos, mass, off, adj, w, p)
+        Fr0, inter0 = oracle.bh_repulsion(pos, mass, p)
+        assert r["status"] == 0
+        assert r["interactions"] == inter0
+        assert G.rel_err(r["Fr"][outside], Fr0[outside]) <= TOL
+
+
 def test_shallow_tree_depth():
     pos, mass, off, adj, w = _case(3000, 8, 7, "clustered")
     for L in (1, 2, 5):
