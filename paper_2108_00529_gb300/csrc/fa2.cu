@@ -660,18 +660,14 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
             const uint32_t sk = uint32_t(skip[cur]);
             const float dx = __fsub_rn(bi.x, e.x), dy = __fsub_rn(bi.y, e.y);
             const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            const bool holds = self >= cur && self < sk;
-            if (!holds && e.w < __fmul_rn(theta2, d2)) {
-                if (d2 > 0.0f) {
-                    const float f = __fdividef(kmi * e.z, d2);
-                    fx += f * dx;
-                    fy += f * dy;
-                }
-                ++inter;
-                cur = sk;
-            } else {
-                cur = cur + 1;
-            }
+            // accepted: not an element holding the body (cur <= self < sk) and
+            // the opening test passes; no branch, so lanes stay converged
+            const bool accept = self - cur >= sk - cur && e.w < __fmul_rn(theta2, d2);
+            const float f = accept && d2 > 0.0f ? __fdividef(kmi * e.z, d2) : 0.0f;
+            fx += f * dx;
+            fy += f * dy;
+            inter += accept ? 1u : 0u;
+            cur = accept ? sk : cur + 1;
         }
         Frep[__float_as_int(bi.w)] = make_float2(fx, fy);
     }
