@@ -45,7 +45,7 @@ FLOPS_PER_INTERACTION = 12     # dx, dy, d2 (3), division, k*m*M (2), two FMAs (
 # DRAM bytes (read + write) of one k_repulse launch on the rmat20 supergraph,
 # from the ncu capture summarised in profiles/k_repulse_rmat20.md; valid only
 # while k_repulse is unchanged since that capture.
-REPULSE_TRAFFIC = {"rmat20": 51_784_448}
+REPULSE_TRAFFIC = {"rmat20": 51_802_880}
 
 WORKLOADS = {
     "rmat20": dict(desc="R-MAT scale 20 (1,048,576 node ids), 10,000,000 unique edges, a,b,c,d=.57,.19,.19,.05, "
