@@ -42,7 +42,7 @@ namespace bgv {
 namespace {
 constexpr int kThreads = 256;
 constexpr int kFrameBlocks = 304;      // 2 x 152 SMs
-constexpr int kNodeBlocks = 152 * 8;  // node-kernel grid (rows are grid-strided)
+constexpr int kNodeBlocks = 152 * 4;  // node-kernel grid (rows are grid-strided; fewer blocks, fewer FP64 partials to merge)
 
 typedef unsigned __int128 u128;
 
