@@ -997,11 +997,6 @@ __global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__res
 struct Comp {
     double s, c;
 };
-__device__ __forceinline__ Comp comp_add(Comp a, double x) {
-    const double t = a.s + x;
-    const double e = fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
-    return Comp{t, a.c + e};
-}
 __device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
     const double t = a.s + b.s;
     const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
@@ -1173,19 +1168,22 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
     hdr->node_ticket = 0u;
 }
 
-// Batched form: one block per graph sums its rows' swing and traction (FP64,
-// compensated, fixed order) and updates that graph's speed.
+// Batched form: one block per graph sums its rows' swing and traction (FP64
+// in a fixed order, compensated across threads) and updates that graph's
+// speed.
 __global__ void __launch_bounds__(kThreads) k_speed_seg(const float2 *__restrict__ rowst,
                                                         const int64_t *__restrict__ koff, double *speed, float tau,
                                                         WsHeader *hdr) {
     const int g = blockIdx.x;
     const int64_t a = koff[g], b = koff[g + 1];
-    Comp S{0.0, 0.0}, T{0.0, 0.0};
+    // plain FP64 per thread, compensated where the threads' sums meet
+    double s = 0.0, t = 0.0;
     for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
         const float2 v = rowst[i];
-        S = comp_add(S, double(v.x));
-        T = comp_add(T, double(v.y));
+        s += double(v.x);
+        t += double(v.y);
     }
+    Comp S{s, 0.0}, T{t, 0.0};
     block_merge(S, T);
     if (threadIdx.x != 0) return;
     const double Ssum = S.s + S.c, Tsum = T.s + T.c;
