@@ -73,6 +73,12 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units per step, at the slowest rank's step time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 class Dist:
     def __init__(self):
         self.rank, self.world, self.local = dist_env()
@@ -353,7 +359,7 @@ def gpu_arm(args, dist: Dist):
 
     out = {
         "metric": METRIC,
-        "value": round(m * dist.world / (ms_max * 1e-3), 1),
+        "value": round(aggregate_throughput(m, dist.world, ms_max), 1),
         "unit": "edges/s",
         "n_gpus": dist.world,
         "steps": args.steps,
@@ -376,7 +382,7 @@ def gpu_arm(args, dist: Dist):
                           "(launched one by one; the others replay a captured step)",
         "roofline": roofline,
         "edge_roofline": edge_roofline,
-        "e2e": {"value": round(m * dist.world / (e2e_ms * 1e-3), 1), "unit": "edges/s",
+        "e2e": {"value": round(aggregate_throughput(m, dist.world, e2e_ms), 1), "unit": "edges/s",
                 "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(8 * m),
                 "d2h_bytes_per_step": int(4 * n + 12 * K2), "entry": "bgv_layout_host"},
         "gpu_launches": int(launches),
@@ -501,7 +507,7 @@ def gpu_arm_whole(args, dist: Dist):
     rep_ms = stage["repulsion"]  # per iteration = per launch
     ach = inter * FLOPS_PER_INTERACTION / (rep_ms * 1e-3) / 1e12
     out = {
-        "metric": METRIC, "value": round(m * dist.world / (ms * 1e-3), 1), "unit": "edges/s",
+        "metric": METRIC, "value": round(aggregate_throughput(m, dist.world, ms), 1), "unit": "edges/s",
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m, "fa2_iterations": iters,
@@ -643,8 +649,8 @@ def gpu_arm_batched(args, dist: Dist):
                      "entry": "bgv_layout, one call per graph", "counts_equal_batched": bool(same)}
     inter = (st1.interactions_total - st0.interactions_total) / max(st1.steps_total - st0.steps_total, 1)
     return {
-        "metric": "graphs/s laid out (sketch, communities, supergraph, FA2)", "value": round(Gn * dist.world /
-                                                                                              (ms * 1e-3), 3),
+        "metric": "graphs/s laid out (sketch, communities, supergraph, FA2)",
+        "value": round(aggregate_throughput(Gn, dist.world, ms), 3),
         "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32+f32", "data": "synthetic",
@@ -652,7 +658,7 @@ def gpu_arm_batched(args, dist: Dist):
                    "sketch": f"{cfg['rows']}x{cfg['width']} per graph", "passes": cfg["passes"],
                    "fa2_iterations": iters, "K": int(K_off[-1]), "Es": int(Es_off[-1]),
                    "l2": "flushed before every timed step (256 MiB write)", "parallelism": "single GPU"},
-        "edges_per_s": round(m * dist.world / (ms * 1e-3), 1),
+        "edges_per_s": round(aggregate_throughput(m, dist.world, ms), 1),
         "interactions_per_iteration": int(inter),
         "per_graph_launches": per_graph,
         "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // max(args.steps, 1)), "clocks": clk,
