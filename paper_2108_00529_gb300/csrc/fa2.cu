@@ -241,6 +241,31 @@ __device__ __forceinline__ Mom mom_load(const unsigned long long *PM, const ulon
     return Mom{PM[s], (u128(x.y) << 64) | x.x, (u128(y.y) << 64) | y.x};
 }
 
+// Moment prefix of one body in one 32-byte record (one sector per access):
+// M in 64 bits, the coordinate sums in 96 (their totals stay below 2^95).
+struct __align__(32) MomP {
+    unsigned long long M, xl, yl;
+    uint32_t xh, yh;
+};
+__device__ __forceinline__ uint4 momp_first_half(unsigned long long M, u128 X) {
+    return make_uint4(uint32_t(M), uint32_t(M >> 32), uint32_t(X), uint32_t(X >> 32));
+}
+__device__ __forceinline__ uint4 momp_second_half(u128 X, u128 Y) {
+    return make_uint4(uint32_t(Y), uint32_t(Y >> 32), uint32_t(X >> 64), uint32_t(Y >> 64));
+}
+__device__ __forceinline__ void momp_store(MomP *P, int64_t s, const Mom &v) {
+    uint4 *p = reinterpret_cast<uint4 *>(P + s);
+    p[0] = momp_first_half(v.M, v.X);
+    p[1] = momp_second_half(v.X, v.Y);
+}
+__device__ __forceinline__ Mom momp_load(const MomP *P, int64_t s) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(P + s);
+    const uint4 a = p[0], b = p[1];
+    const unsigned long long xl = (static_cast<unsigned long long>(a.w) << 32) | a.z;
+    const unsigned long long yl = (static_cast<unsigned long long>(b.y) << 32) | b.x;
+    return Mom{(static_cast<unsigned long long>(a.y) << 32) | a.x, (u128(b.z) << 64) | xl, (u128(b.w) << 64) | yl};
+}
+
 // Block-wide exclusive scan of one Mom per thread; returns the prefix and
 // the block total.
 __device__ __forceinline__ Mom mom_block_exclusive(Mom v, Mom *total) {
@@ -277,9 +302,10 @@ __device__ __forceinline__ Mom mom_block_exclusive(Mom v, Mom *total) {
 // position, mass and index (body[s]), and its fixed-point coordinates
 // recomputed from the position as the keys were.  The tile publishes its
 // total, the block adds the totals or inclusive prefixes of the tiles before
-// it (up to kMomLookBack at a time), and the prefixes go out through shared memory so that
-// every store is coalesced.  Also clears the per-body cell counters that
-// k_tree fills.  P[K], the grand total, is written by the last tile.
+// it (up to kMomLookBack at a time), and the prefix records go out through
+// shared memory, one 16-byte half of each per round.  Also clears the
+// per-body cell counters that k_tree fills.  P[K], the grand total, is
+// written by the last tile.
 struct MomTile {
     unsigned long long M, xl, xh, yl, yh, pad;
 };
@@ -317,19 +343,10 @@ __device__ __forceinline__ Mom mom_warp_sum(Mom v) {
 // Staging slot of tile element e: one 16-byte pad after every 8 elements, so
 // the per-thread writes (stride 8) fall in different banks.
 __device__ __forceinline__ int stage_slot(int e) { return e + (e >> 3); }
-__device__ __forceinline__ uint4 u128_words(u128 v) {
-    return make_uint4(uint32_t(v), uint32_t(v >> 32), uint32_t(v >> 64), uint32_t(v >> 96));
-}
-__device__ __forceinline__ ulonglong2 words_u128(uint4 v) {
-    return make_ulonglong2((static_cast<unsigned long long>(v.y) << 32) | v.x,
-                           (static_cast<unsigned long long>(v.w) << 32) | v.z);
-}
-
 __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     const uint32_t *__restrict__ perm, int64_t K, const float2 *__restrict__ pos, const uint32_t *__restrict__ mass,
     const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
-    unsigned long long *__restrict__ PM, ulonglong2 *__restrict__ PX, ulonglong2 *__restrict__ PY,
-    uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
+    MomP *__restrict__ P, uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
     MomTile *incl, uint32_t *dev_status) {
     __shared__ uint4 stage[kMomTile + kMomTile / 8];
     __shared__ unsigned tile_sh;
@@ -453,52 +470,40 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     const Mom tile_pre = excl;
     __syncthreads();  // the bodies have left the staging buffer
     run = mom_add(run, tile_pre);
-    if (tile == tiles - 1 && threadIdx.x == 0) mom_store(mom_add(tile_pre, total), PM, PX, PY, K);
-    // the prefix sums, one component at a time through the staging buffer
-    unsigned long long *stage8 = reinterpret_cast<unsigned long long *>(stage);
+    if (tile == tiles - 1 && threadIdx.x == 0) momp_store(P, K, mom_add(tile_pre, total));
+    // the prefix records, one 16-byte half at a time through the staging buffer
+    uint4 *P4 = reinterpret_cast<uint4 *>(P);
     {
-        unsigned long long r = run.M;
+        unsigned long long rm = run.M;
+        u128 rx = run.X;
 #pragma unroll
         for (int k = 0; k < kMomItems; ++k) {
-            stage8[stage_slot(threadIdx.x * kMomItems + k)] = r;
-            r += m[k];
+            stage[stage_slot(threadIdx.x * kMomItems + k)] = momp_first_half(rm, rx);
+            rm += m[k];
+            rx += u128(m[k]) * ux[k];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kMomItems; ++r) {
         const int e = r * kThreads + threadIdx.x;
-        if (t0 + e < K) PM[t0 + e] = stage8[stage_slot(e)];
+        if (t0 + e < K) P4[2 * (t0 + e)] = stage[stage_slot(e)];
     }
     __syncthreads();
     {
-        u128 r = run.X;
+        u128 rx = run.X, ry = run.Y;
 #pragma unroll
         for (int k = 0; k < kMomItems; ++k) {
-            stage[stage_slot(threadIdx.x * kMomItems + k)] = u128_words(r);
-            r += u128(m[k]) * ux[k];
+            stage[stage_slot(threadIdx.x * kMomItems + k)] = momp_second_half(rx, ry);
+            rx += u128(m[k]) * ux[k];
+            ry += u128(m[k]) * uy[k];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kMomItems; ++r) {
         const int e = r * kThreads + threadIdx.x;
-        if (t0 + e < K) PX[t0 + e] = words_u128(stage[stage_slot(e)]);
-    }
-    __syncthreads();
-    {
-        u128 r = run.Y;
-#pragma unroll
-        for (int k = 0; k < kMomItems; ++k) {
-            stage[stage_slot(threadIdx.x * kMomItems + k)] = u128_words(r);
-            r += u128(m[k]) * uy[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kMomItems; ++r) {
-        const int e = r * kThreads + threadIdx.x;
-        if (t0 + e < K) PY[t0 + e] = words_u128(stage[stage_slot(e)]);
+        if (t0 + e < K) P4[2 * (t0 + e) + 1] = stage[stage_slot(e)];
     }
 }
 
@@ -523,9 +528,7 @@ __device__ __forceinline__ int node_level(int delta, int kb, int L, int gbits) {
 __global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__restrict__ keys, int64_t K, int L,
                                                    int gbits, int leaf_cap, const float4 *__restrict__ frames,
                                                    const int32_t *__restrict__ bgraph,
-                                                   const unsigned long long *__restrict__ PM,
-                                                   const ulonglong2 *__restrict__ PX,
-                                                   const ulonglong2 *__restrict__ PY, int2 *__restrict__ range,
+                                                   const MomP *__restrict__ P, int2 *__restrict__ range,
                                                    int8_t *__restrict__ cell_level, float4 *__restrict__ cell,
                                                    uint32_t *__restrict__ start_count,
                                                    uint32_t *__restrict__ start_levels,
@@ -568,7 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__r
                 const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
                 // positions of graph g in Morton order are its index range too
                 const float4 fr = frames[bgraph ? bgraph[first] : 0];
-                const Mom hi = mom_load(PM, PX, PY, last + 1), lo = mom_load(PM, PX, PY, first);
+                const Mom hi = momp_load(P, last + 1), lo = momp_load(P, first);
                 const unsigned long long M = hi.M - lo.M;
                 const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
                 const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
@@ -1284,8 +1287,7 @@ struct Fa2Scratch {
     float4 *body;          // sorted bodies: x, y, mass, index
     int2 *range;           // per binary node that is a cell: its bodies
     int8_t *cell_level;    // per binary node: its level if a cell, else -1
-    unsigned long long *PM;  // moment prefix sums, K + 1 entries
-    ulonglong2 *PX, *PY;
+    MomP *P;               // moment prefix sums, K + 1 records
     uint32_t *mom_flags;   // look-back flags per tile, then the tile counter
     MomTile *mom_agg, *mom_incl;
     float4 *cell;          // per binary node: centre, mass, side^2 (cells only)
@@ -1319,9 +1321,7 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     const size_t tiles = (k + kMomTile - 1) / kMomTile;
     s.range = c.take<int2>(k);
     s.cell_level = c.take<int8_t>(k);
-    s.PM = c.take<unsigned long long>(k + 1);
-    s.PX = c.take<ulonglong2>(k + 1);
-    s.PY = c.take<ulonglong2>(k + 1);
+    s.P = c.take<MomP>(k + 1);
     s.mom_flags = c.take<uint32_t>(tiles + 1);
     s.mom_agg = c.take<MomTile>(tiles);
     s.mom_incl = c.take<MomTile>(tiles);
@@ -1474,7 +1474,7 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         const int64_t tiles = (K + kMomTile - 1) / kMomTile;
         BGV_CUDA(cudaMemsetAsync(s.mom_flags, 0, sizeof(uint32_t) * size_t(tiles + 1), st));
         note_launch(), k_gather_moments<<<unsigned(tiles), kThreads, 0, st>>>(
-            s.sort.vals[res], K, pos, mass, s.frame, s.bgraph, s.body, s.PM, s.PX, s.PY, s.start_count,
+            s.sort.vals[res], K, pos, mass, s.frame, s.bgraph, s.body, s.P, s.start_count,
             s.start_levels, s.mom_flags, s.mom_agg, s.mom_incl, &hdr->status);
         BGV_TRY(launch_status());
     }
@@ -1483,7 +1483,7 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         const unsigned gi = unsigned((K - 1 + kThreads - 1) / kThreads);
         note_launch(), k_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph,
-                                                       s.PM, s.PX, s.PY, s.range, s.cell_level, s.cell,
+                                                       s.P, s.range, s.cell_level, s.cell,
                                                        s.start_count, s.start_levels, &hdr->tree_nodes);
         BGV_TRY(launch_status());
         BGV_TRY(mark(4));
