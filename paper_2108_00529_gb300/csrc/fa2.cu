@@ -303,7 +303,7 @@ __device__ __forceinline__ Mom mom_block_exclusive(Mom v, Mom *total) {
 // recomputed from the position as the keys were.  The tile publishes its
 // total, the block adds the totals or inclusive prefixes of the tiles before
 // it (up to kMomLookBack at a time), and the prefix records go out through
-// shared memory, one 16-byte half of each per round.  Also clears the
+// shared memory so that every store is coalesced.  Also clears the
 // per-body cell counters that k_tree fills.  P[K], the grand total, is
 // written by the last tile.
 struct MomTile {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
     MomP *__restrict__ P, uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
     MomTile *incl, uint32_t *dev_status) {
-    __shared__ uint4 stage[kMomTile + kMomTile / 8];
+    __shared__ uint4 stage[2 * (kMomTile + kMomTile / 8)];  // bodies, then two halves per prefix record
     __shared__ unsigned tile_sh;
     __shared__ int near_sh;
     __shared__ unsigned long long red_sh[kThreads / 32][5];
@@ -471,39 +471,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     __syncthreads();  // the bodies have left the staging buffer
     run = mom_add(run, tile_pre);
     if (tile == tiles - 1 && threadIdx.x == 0) momp_store(P, K, mom_add(tile_pre, total));
-    // the prefix records, one 16-byte half at a time through the staging buffer
-    uint4 *P4 = reinterpret_cast<uint4 *>(P);
+    // the prefix records through the staging buffer (the bodies have left
+    // it), then out with consecutive threads on consecutive 16-byte halves
+    uint4 *stage2 = stage;
     {
         unsigned long long rm = run.M;
-        u128 rx = run.X;
-#pragma unroll
-        for (int k = 0; k < kMomItems; ++k) {
-            stage[stage_slot(threadIdx.x * kMomItems + k)] = momp_first_half(rm, rx);
-            rm += m[k];
-            rx += u128(m[k]) * ux[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kMomItems; ++r) {
-        const int e = r * kThreads + threadIdx.x;
-        if (t0 + e < K) P4[2 * (t0 + e)] = stage[stage_slot(e)];
-    }
-    __syncthreads();
-    {
         u128 rx = run.X, ry = run.Y;
 #pragma unroll
         for (int k = 0; k < kMomItems; ++k) {
-            stage[stage_slot(threadIdx.x * kMomItems + k)] = momp_second_half(rx, ry);
+            const int slot = 2 * stage_slot(threadIdx.x * kMomItems + k);
+            stage2[slot] = momp_first_half(rm, rx);
+            stage2[slot + 1] = momp_second_half(rx, ry);
+            rm += m[k];
             rx += u128(m[k]) * ux[k];
             ry += u128(m[k]) * uy[k];
         }
     }
     __syncthreads();
+    uint4 *P4 = reinterpret_cast<uint4 *>(P);
 #pragma unroll
-    for (int r = 0; r < kMomItems; ++r) {
-        const int e = r * kThreads + threadIdx.x;
-        if (t0 + e < K) P4[2 * (t0 + e) + 1] = stage[stage_slot(e)];
+    for (int r = 0; r < 2 * kMomItems; ++r) {
+        const int u = r * kThreads + threadIdx.x;  // 16-byte half u of the tile: record u / 2
+        if (t0 + (u >> 1) < K) P4[2 * t0 + u] = stage2[2 * stage_slot(u >> 1) + (u & 1)];
     }
 }
 
