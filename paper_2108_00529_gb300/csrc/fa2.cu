@@ -42,7 +42,7 @@ namespace bgv {
 namespace {
 constexpr int kThreads = 256;
 constexpr int kFrameBlocks = 304;      // 2 x 152 SMs
-constexpr int kNodeBlocks = 152 * 4;  // node-kernel grid (rows are grid-strided; fewer blocks, fewer FP64 partials to merge)
+constexpr int kNodeBlocks = 152 * 4;  // node-kernel grid (rows are grid-strided; measured best)
 
 typedef unsigned __int128 u128;
 
@@ -1128,25 +1128,25 @@ __global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const in
     __shared__ bool last;
     block_sum_plain(S.s, T.s);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = make_double2(S.s, 0.0);
-        part[2 * blockIdx.x + 1] = make_double2(T.s, 0.0);
+        part[blockIdx.x] = make_double2(S.s, T.s);
         __threadfence();
         last = atomicAdd(&hdr->node_ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // The last block merges the block partials: each thread a strided subset
-    // in block order, then the fixed block tree.
-    Comp aS{0.0, 0.0}, aT{0.0, 0.0};
+    // The last block adds the block partials: each thread a strided subset
+    // in block order, then the fixed block tree (plain FP64: a few hundred
+    // terms, each already a block's sum).
+    double aS = 0.0, aT = 0.0;
     for (unsigned bk = threadIdx.x; bk < gridDim.x; bk += blockDim.x) {
-        const double2 ps = __ldcg(&part[2 * bk]), pt = __ldcg(&part[2 * bk + 1]);
-        aS = comp_merge(aS, Comp{ps.x, ps.y});
-        aT = comp_merge(aT, Comp{pt.x, pt.y});
+        const double2 v = __ldcg(&part[bk]);
+        aS += v.x;
+        aT += v.y;
     }
-    block_merge(aS, aT);
+    block_sum_plain(aS, aT);
     if (threadIdx.x != 0) return;
-    const double Ssum = aS.s + aS.c, Tsum = aT.s + aT.c;
+    const double Ssum = aS, Tsum = aT;
     double sp = *speed;
     if (Ssum > 0.0) {
         const double target = double(tau) * Tsum / Ssum;
@@ -1292,7 +1292,7 @@ struct Fa2Scratch {
     unsigned long long *chunk_meta;  // plan: rows of the chunk's entries, flags
     int32_t *long_rows;   // plan: rows over more than kLongRowRanges ranges
     int32_t *long_count;
-    double2 *part;  // two per block: (S, comp), (T, comp)
+    double2 *part;  // per block: (S, T)
 };
 
 static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
@@ -1329,7 +1329,7 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.chunk_meta = c.take<unsigned long long>(chunks);
     s.long_rows = c.take<int32_t>(ranges / kLongRowRanges + 1);
     s.long_count = c.take<int32_t>(1);
-    s.part = c.take<double2>(2 * kNodeBlocks);
+    s.part = c.take<double2>(kNodeBlocks);
 }
 
 size_t fa2_scratch_bytes(int64_t K, int64_t nnz, int32_t G) {
