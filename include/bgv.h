@@ -252,8 +252,9 @@ int bgv_render(int64_t K, const float *xy, const float *radius, const uint8_t *g
  *   attraction -sum_j w_ij (p_i - p_j) over CSR neighbours;
  *   gravity    -kg m_i p_i / |p_i| (strong_gravity: -kg m_i p_i).
  * Step: swing_i = |F_i - Fprev_i|, traction_i = |F_i + Fprev_i| / 2;
- * S = sum m_i swing_i, T = sum m_i traction_i in FP64 (pairwise within a
- * block, Kahan-compensated across blocks); if S > 0,
+ * S = sum m_i swing_i, T = sum m_i traction_i in FP64, added in a fixed
+ * order (per thread, per block, then the block sums; batched: compensated
+ * where a graph's threads meet); if S > 0,
  * speed += min(tau T / S - speed, speed / 2); then
  * s_i = ks speed / (1 + speed sqrt(swing_i)), capped at ksmax / |F_i|;
  * p_i += s_i F_i; Fprev = F.

@@ -27,8 +27,8 @@
 //               spread over many ranges.  Both run on a second stream while
 //               the tree is built and walked.
 //   k_node      per node: attraction pieces in range order, gravity, total
-//               force, swing and traction (FP64, compensated); the last block
-//               merges the block partials and updates the global speed
+//               force, swing and traction (FP64 sums in a fixed order); the
+//               last block adds the block sums and updates the global speed
 //   k_update    local speed, displacement, Fprev = F
 //
 // The opening test and the centre it uses are computed with explicit
@@ -984,8 +984,9 @@ __global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__res
 }
 
 // --------------------------------------------- node forces, swing, speed
-// Neumaier-compensated FP64 accumulation; merging two partial sums keeps
-// both compensations.  Used in a fixed order, so results are reproducible.
+// Neumaier-compensated FP64 accumulation (the batched form's per-graph
+// sums); merging two partial sums keeps both compensations.  Used in a fixed
+// order, so results are reproducible.
 struct Comp {
     double s, c;
 };
