@@ -154,7 +154,8 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
         if (graph) cudaGraphDestroy(graph);
         return rc != BGV_OK ? rc : BGV_ECUDA;
     }
-    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    // the captured kernels keep the priorities of the streams they came from
+    if (cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         cudaGraphDestroy(graph);
         return BGV_ECUDA;
     }

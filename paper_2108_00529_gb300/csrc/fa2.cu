@@ -1377,6 +1377,21 @@ cudaStream_t aux_stream() {
     return streams[dev];
 }
 
+// A stream at the device's highest priority per host thread and device,
+// made on first use.
+cudaStream_t priority_stream() {
+    static thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev]) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, greatest) != cudaSuccess)
+            streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 // The two events of a fork onto the second stream and the join back,
 // destroyed when the step's work has been enqueued (work already enqueued
 // keeps them valid).
@@ -1393,10 +1408,10 @@ struct ForkJoin {
     }
 };
 
-int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
-            const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
-            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
-            bool build_plan, int32_t G, const int64_t *koff) {
+static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj,
+                        const uint32_t *csr_w, const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f,
+                        float *Fprev_f, double *speed, float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch,
+                        cudaStream_t st, cudaEvent_t *marks, bool build_plan, int32_t G, const int64_t *koff) {
     if (K <= 0) return BGV_OK;
     const bool batched = G > 1;
     if (!fa2_batch_fits(G, p.max_depth)) return BGV_EINVAL;
@@ -1513,6 +1528,26 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     }
     BGV_TRY(mark(8));
     return BGV_OK;
+}
+
+// The iteration's main chain runs on a high-priority stream forked from the
+// caller's and joined back at the end: when SMs free up, its blocks go before
+// those of the attraction, which runs beside it at the default priority.
+int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+            const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
+            float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
+            bool build_plan, int32_t G, const int64_t *koff) {
+    if (K <= 0) return BGV_OK;
+    cudaStream_t hp = priority_stream();
+    ForkJoin ev;
+    if (!hp || ev.make() != cudaSuccess) return BGV_ECUDA;
+    BGV_CUDA(cudaEventRecord(ev.fork, st));
+    BGV_CUDA(cudaStreamWaitEvent(hp, ev.fork, 0));
+    const int rc = run_fa2_body(mode, K, nnz, csr_off, csr_adj, csr_w, mass, p, pos_f, F_f, Fprev_f, speed, Fr, Fa, Fg,
+                                hdr, scratch, hp, marks, build_plan, G, koff);
+    BGV_CUDA(cudaEventRecord(ev.join, hp));
+    BGV_CUDA(cudaStreamWaitEvent(st, ev.join, 0));
+    return rc;
 }
 
 }  // namespace bgv
