@@ -21,7 +21,14 @@
  * Streams.    `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *             default stream).  Calls only enqueue work; they do not
  *             synchronise, except bgv_status, bgv_fa2_read_stats and the
- *             bgv_layout* pipeline calls (documented there).
+ *             bgv_layout* pipeline calls (documented there).  A ForceAtlas2
+ *             step forks its work from `stream` onto two library streams of
+ *             the calling host thread and device (the main chain at the
+ *             device's highest stream priority, the attraction beside it)
+ *             and joins them back into `stream` before it returns, so its
+ *             work is ordered on `stream` like any other call.  Those
+ *             streams are made on first use and live until the process
+ *             ends; each step makes and destroys four CUDA events.
  * Scratch.    The library allocates no memory.  Each stage takes a caller
  *             workspace `ws` of `ws_bytes` bytes (256-byte aligned), sized by
  *             the matching *_ws_size query.  The first 256 bytes of every
@@ -323,12 +330,14 @@ int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *c
                 float *pos, float *F, float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
 
 /* Profiling form of bgv_fa2_run: `iterations` steps launched one by one
- * (no graph) with CUDA events recorded on `stream` at the boundaries of the
- * BGV_FA2_STAGES stages of each step; synchronises `stream` and returns in
- * stage_ms[BGV_FA2_STAGES] the summed milliseconds per stage:
- *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order,
- *   3 moments, radix tree and quadtree cells, 4 pre-order layout, 5 Barnes-Hut repulsion,
- *   6 attraction + gravity + swing/traction + speed, 7 displacement.
+ * (no graph) with CUDA events recorded at the boundaries of the
+ * BGV_FA2_STAGES stages of each step (on the library stream that runs the
+ * main chain); synchronises `stream` and returns in stage_ms[BGV_FA2_STAGES]
+ * the summed milliseconds per stage:
+ *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order and
+ *   moment prefix sums, 3 radix tree and quadtree cells, 4 pre-order layout,
+ *   5 Barnes-Hut repulsion, 6 gravity + swing/traction + speed (after the
+ *   attraction, which runs beside stages 0-5), 7 displacement.
  * Creates and destroys (BGV_FA2_STAGES + 1) * iterations CUDA events. */
 #define BGV_FA2_STAGES 8
 int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
