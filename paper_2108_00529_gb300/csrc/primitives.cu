@@ -213,8 +213,14 @@ constexpr int kCountItems = 8;
 constexpr int kCountTile = kSortThreads * kCountItems;
 __global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long long *__restrict__ keys, int64_t cap,
                                                              const int64_t *d_count, int first, int passes,
-                                                             uint32_t *__restrict__ counts) {
+                                                             uint32_t *__restrict__ counts,
+                                                             unsigned long long *__restrict__ status, int64_t tiles,
+                                                             uint32_t *__restrict__ zero_words, int n_zero) {
     __shared__ uint32_t h[kMaxPasses][kBins];
+    // clears what the passes after it start from: the look-back words of the
+    // tiles (one tile's kBins words per block) and a few counters
+    if (blockIdx.x < tiles) status[int64_t(blockIdx.x) * kBins + threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x < n_zero) zero_words[threadIdx.x] = 0u;
     for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kSortThreads) (&h[0][0])[i] = 0;
     const int64_t n = load_count(d_count, cap);
     const int64_t base = int64_t(blockIdx.x) * kCountTile;
@@ -234,16 +240,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long
     for (int i = first * kBins + threadIdx.x; i < passes * kBins; i += kSortThreads) {
         const uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&counts[i], c);
-    }
-}
-
-// Exclusive scan of each pass's 256 digit counts, in place.
-__global__ void __launch_bounds__(kSortThreads) k_sort_offsets(uint32_t *counts, int passes) {
-    for (int p = 0; p < passes; ++p) {
-        const uint32_t c = counts[p * kBins + threadIdx.x];
-        uint32_t tot;
-        const uint32_t ex = block_exclusive(c, &tot);
-        counts[p * kBins + threadIdx.x] = ex;
     }
 }
 
@@ -299,7 +295,7 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
                                                                 const uint32_t *__restrict__ vin,
                                                                 uint32_t *__restrict__ vout, int64_t cap,
                                                                 const int64_t *d_count, int shift,
-                                                                const uint32_t *__restrict__ digit_base,
+                                                                const uint32_t *__restrict__ pass_counts,
                                                                 unsigned int *tile_counter,
                                                                 unsigned long long *status, uint32_t *dev_status,
                                                                 unsigned long long tag) {
@@ -370,6 +366,10 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
     }
     volatile unsigned long long *st = status;
     st[tile * kBins + d] = (tile == 0 ? kFlagIncl : kFlagAgg) | tag | total;
+    // where digit d starts in the output: the exclusive scan of the pass's
+    // digit counts (every block scans the 256 counts itself)
+    uint32_t all_keys;
+    const uint32_t digit_start = block_exclusive(pass_counts[d], &all_keys);
     if (kStage) {
         // keys go to their place in the tile before the look-back, which
         // frees their registers for a wider look-back window
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
             if (kVals) sval[slot] = val[k];
         }
     }
-    tile_base[d] = digit_base[d] + uint32_t(look_back<kStage ? kLookBackWide : kLookBack>(st, tile, d, tag, total,
+    tile_base[d] = digit_start + uint32_t(look_back<kStage ? kLookBackWide : kLookBack>(st, tile, d, tag, total,
                                                                                          dev_status));
     __syncthreads();
     if (kStage) {
@@ -465,13 +465,11 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
-    const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;
+    const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;  // >= tiles
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
-        b.keys[0], cap, d_count, 0, passes, b.counts);
-    note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
+        b.keys[0], cap, d_count, 0, passes, b.counts, b.status, tiles, nullptr, 0);
     BGV_TRY(launch_status());
     int cur = 0;
-    BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles), s));
     for (int p = 0; p < passes; ++p) {
         BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p),
                               items, s, dev_status));
@@ -751,13 +749,10 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_b
     const int items = sort_items(n);
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
-    BGV_CUDA(cudaMemsetAsync(r.counts, 0, 2 * sizeof(uint32_t), s));
-    const int64_t count_blocks = (n + kCountTile - 1) / kCountTile;
+    const int64_t count_blocks = (n + kCountTile - 1) / kCountTile;  // >= tiles
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
-        b.keys[0], n, nullptr, 2, passes, b.counts);
-    note_launch(), k_sort_offsets<<<1, kSortThreads, 0, s>>>(b.counts, passes);
+        b.keys[0], n, nullptr, 2, passes, b.counts, b.status, tiles_for(n, items), r.counts, 2);
     BGV_TRY(launch_status());
-    BGV_CUDA(cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * size_t(kBins) * size_t(tiles_for(n, items)), s));
     int cur = 0;
     for (int p = 2; p < passes; ++p) {
         BGV_TRY(onesweep_pass(b, n, nullptr, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p), items,
