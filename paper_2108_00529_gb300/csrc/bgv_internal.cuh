@@ -145,8 +145,11 @@ struct RunFixBuffers {
     uint32_t *counts;   // [0] runs, [1] big
 };
 void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r);
+// Words of SortBuffers::counts (digit counts and tile counters): cleared
+// before a sort, by the sort itself unless its caller cleared them.
+int64_t sort_counter_words();
 int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
-                    int *result_buffer, uint32_t *dev_status);
+                    int *result_buffer, uint32_t *dev_status, bool counters_cleared = false);
 
 // Sort autotuner: times 8 against 16 keys per thread for 2^14, 2^16, ...
 // up to max_keys and sets the cutoff between them for the whole process.

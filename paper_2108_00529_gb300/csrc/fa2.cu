@@ -174,12 +174,23 @@ __device__ __forceinline__ uint2 fixed_point(float2 p, float4 fr) {
 // Morton key of the body's fixed-point position in its graph's frame; in the
 // batched form the graph id sits above the 2L Morton bits, so each graph's
 // bodies stay together and form their own subtree.
+// Also clears, for the kernels after it, the step's counters (2 words), the
+// moment look-back flags and the sort's digit counters: the launches that
+// would otherwise clear them sit on the step's dependency chain.
 __global__ void __launch_bounds__(kThreads) k_keys(const float2 *__restrict__ pos, int64_t K,
                                                    const float4 *__restrict__ frames,
                                                    const int32_t *__restrict__ bgraph, int L,
                                                    unsigned long long *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals) {
+                                                   uint32_t *__restrict__ vals,
+                                                   unsigned long long *__restrict__ step_counters,
+                                                   uint32_t *__restrict__ clear_a, int64_t n_a,
+                                                   uint32_t *__restrict__ clear_b, int64_t n_b) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_a || t < n_b || t < 2; t += stride) {
+        if (t < 2) step_counters[t] = 0ull;
+        if (t < n_a) clear_a[t] = 0u;
+        if (t < n_b) clear_b[t] = 0u;
+    }
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
         const int g = bgraph ? bgraph[i] : 0;
         const uint2 U = fixed_point(pos[i], frames[g]);
@@ -1428,9 +1439,9 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         return BGV_OK;
     };
 
-    // per-step counters and last-block tickets
-    BGV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(hdr) + offsetof(WsHeader, interactions), 0,
-                             offsetof(WsHeader, reserved) - offsetof(WsHeader, interactions), st));
+    // The per-step counters are cleared by k_keys; S and T are written whole
+    // by the node kernels; the last-block tickets are reset by their last
+    // blocks (the header starts zeroed, see bgv_ws_init).
     BGV_TRY(mark(0));
     ForkJoin ev;
     cudaStream_t aux = nullptr;
@@ -1469,16 +1480,17 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
     const int gk = grid_for(K, kThreads, 152 * 16);
-    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0]);
+    const int64_t mom_tiles = (K + kMomTile - 1) / kMomTile;
+    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
+                                                   &hdr->interactions, s.mom_flags, mom_tiles + 1, s.sort.counts,
+                                                   sort_counter_words());
     BGV_TRY(launch_status());
     BGV_TRY(mark(1));
     int res = 0;
-    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, 2 * L + gbits, st, &res, &hdr->status));
+    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, 2 * L + gbits, st, &res, &hdr->status, true));
     BGV_TRY(mark(2));
     {
-        const int64_t tiles = (K + kMomTile - 1) / kMomTile;
-        BGV_CUDA(cudaMemsetAsync(s.mom_flags, 0, sizeof(uint32_t) * size_t(tiles + 1), st));
-        note_launch(), k_gather_moments<<<unsigned(tiles), kThreads, 0, st>>>(
+        note_launch(), k_gather_moments<<<unsigned(mom_tiles), kThreads, 0, st>>>(
             s.sort.vals[res], K, pos, mass, s.frame, s.bgraph, s.body, s.P, s.start_count,
             s.start_levels, s.mom_flags, s.mom_agg, s.mom_incl, &hdr->status);
         BGV_TRY(launch_status());

@@ -741,14 +741,17 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r) {
     r.counts = c.take<uint32_t>(2);
 }
 
+int64_t sort_counter_words() { return int64_t(kMaxPasses) * kBins + kMaxPasses; }
+
 int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
-                    int *result_buffer, uint32_t *dev_status) {
+                    int *result_buffer, uint32_t *dev_status, bool counters_cleared) {
     const int passes = (end_bit + 7) / 8;
     if (!b.vals[0] || end_bit <= 16 || passes > kMaxPasses || n >= (int64_t(1) << 32))
         return radix_sort(b, n, nullptr, end_bit, s, result_buffer, dev_status);
     const int items = sort_items(n);
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
-    BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
+    if (!counters_cleared)
+        BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
     const int64_t count_blocks = (n + kCountTile - 1) / kCountTile;  // >= tiles
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
         b.keys[0], n, nullptr, 2, passes, b.counts, b.status, tiles_for(n, items), r.counts, 2);
