@@ -2,7 +2,8 @@
 //
 // One iteration is a fixed chain of kernels with no host round trip:
 //   k_frame     bounding square of the positions (last-block finalise)
-//   k_keys      fixed-point coordinates U and 2L-bit Morton keys
+//   k_keys      fixed-point coordinates U and 2L-bit Morton keys; clears the
+//               step's counters (the captured step has no memset nodes)
 //   radix sort  (key, body) pairs -> Morton order: LSD passes on the bits
 //               above 16, then each run of equal high bits ordered locally
 //   k_gather_moments
