@@ -27,8 +27,9 @@
  *             device's highest stream priority, the attraction beside it)
  *             and joins them back into `stream` before it returns, so its
  *             work is ordered on `stream` like any other call.  Those
- *             streams are made on first use and live until the process
- *             ends; each step makes and destroys four CUDA events.
+ *             streams are made by the first such call of a host thread on a
+ *             device (make it outside any stream capture) and live until the
+ *             process ends; each step makes and destroys four CUDA events.
  * Scratch.    The library allocates no memory.  Each stage takes a caller
  *             workspace `ws` of `ws_bytes` bytes (256-byte aligned), sized by
  *             the matching *_ws_size query.  The first 256 bytes of every
