@@ -196,3 +196,51 @@ def test_speed_rise_is_capped_and_layout_separates_cliques():
     intra = np.mean([np.linalg.norm(x - y) for x in a for y in a] + [np.linalg.norm(x - y) for x in b for y in b])
     inter = np.mean([np.linalg.norm(x - y) for x in a for y in b])
     assert inter > 1.5 * intra
+
+
+def test_no_swing_keeps_speed_and_moves_by_the_cap_rule():
+    # Fprev equal to this step's force: every swing is 0, so S = 0 and the
+    # global speed stays as it was; traction is |F|; every node moves along F
+    # by ks * speed, or by ksmax / |F| where that is smaller.
+    n, off, adj, w = _two_cliques(6)
+    mass = (np.diff(off) + 1).astype(np.uint32)
+    p0 = oracle.fa2_init(n, 5)
+    F = oracle.fa2_step(oracle.FA2State(p0), off, adj, w, mass, FA2Params())["F"]
+    for ksmax in (10.0, 0.05):  # the cap binds for no node, then for some
+        params = FA2Params(ks=0.1, ksmax=ksmax)
+        st = oracle.FA2State(p0, Fprev=F, speed=0.7)
+        r = oracle.fa2_step(st, off, adj, w, mass, params)
+        assert np.array_equal(r["F"], F)
+        assert r["S"] == 0.0
+        nrm = np.linalg.norm(F, axis=1)
+        assert r["T"] == pytest.approx(float(np.sum(mass * nrm)), rel=1e-13)
+        assert st.speed == 0.7
+        s = np.minimum(params.ks * 0.7, params.ksmax / nrm)
+        if ksmax < 1.0:
+            assert np.any(s < params.ks * 0.7)
+        expected = p0.astype(np.float64) + s[:, None] * F
+        assert np.allclose(st.pos, expected, rtol=1e-12, atol=1e-12 * float(np.max(np.abs(expected))))
+        assert np.array_equal(st.Fprev, F)
+
+
+def test_half_previous_force_gives_closed_form_speed_and_steps():
+    # Fprev = F / 2: swing_i = |F_i| / 2 and traction_i = 3 |F_i| / 4, so
+    # T / S = 3 / 2.  With tau = 1 and speed 0.7 the target 1.5 is more than
+    # half above the speed: the rise is capped at 0.35 (new speed 1.05).
+    # Each node then moves along F by ks * speed / (1 + speed * sqrt(swing))
+    # at the new speed, capped at ksmax / |F|.
+    n, off, adj, w = _two_cliques(6)
+    mass = (np.diff(off) + 1).astype(np.uint32)
+    p0 = oracle.fa2_init(n, 6)
+    F = oracle.fa2_step(oracle.FA2State(p0), off, adj, w, mass, FA2Params())["F"]
+    params = FA2Params(ks=0.1, ksmax=10.0, tau=1.0)
+    st = oracle.FA2State(p0, Fprev=F / 2, speed=0.7)
+    r = oracle.fa2_step(st, off, adj, w, mass, params)
+    nrm = np.linalg.norm(F, axis=1)
+    assert r["S"] == pytest.approx(float(np.sum(mass * nrm / 2)), rel=1e-13)
+    assert r["T"] == pytest.approx(float(np.sum(mass * 3 * nrm / 4)), rel=1e-13)
+    assert st.speed == pytest.approx(1.05, rel=1e-14)
+    s = params.ks * 1.05 / (1 + 1.05 * np.sqrt(nrm / 2))
+    s = np.minimum(s, params.ksmax / nrm)
+    expected = p0.astype(np.float64) + s[:, None] * F
+    assert np.allclose(st.pos, expected, rtol=1e-12, atol=1e-12 * float(np.max(np.abs(expected))))
