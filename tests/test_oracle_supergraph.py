@@ -108,6 +108,8 @@ def test_modularity_two_triangles_closed_form():
     assert oracle.modularity(e, 6, np.array([0, 0, 0, 3, 3, 3], np.int32)) == pytest.approx(0.5, abs=1e-15)
     # everything in one community: Q = 1 - 1 = 0
     assert oracle.modularity(e, 6, np.zeros(6, np.int32)) == pytest.approx(0.0, abs=1e-15)
+    # every node alone: no edge inside, Q = -sum (d_i / 2m)^2 = -6 * (2/12)^2 = -1/6
+    assert oracle.modularity(e, 6, np.arange(6, dtype=np.int32)) == pytest.approx(-1.0 / 6.0, abs=1e-15)
 
 
 def test_modularity_matches_double_sum():
