@@ -137,9 +137,20 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        with open(self.path) as f:
+            out = self.summarise(f, self.gpus)
+        os.unlink(self.path)
+        return out
+
+    @staticmethod
+    def summarise(lines, gpus):
+        """Median SM clock, maximum clock and the throttle reasons seen active,
+        from nvidia-smi CSV rows (index, clocks.sm, clocks.max.sm, power,
+        active mask, then the four reason columns); rows of other GPUs and
+        malformed rows are skipped.  None when no row counts."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -147,7 +158,7 @@ class ClockSampler:
                 idx = int(parts[0])
             except ValueError:
                 continue
-            if self.gpus is not None and idx not in self.gpus:
+            if gpus is not None and idx not in gpus:
                 continue
             try:
                 sm.append(float(parts[1]))
@@ -157,7 +168,6 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
-        os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),

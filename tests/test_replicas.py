@@ -43,3 +43,4 @@ def test_two_gloo_ranks_share_barrier_and_max(tmp_path):
         assert x["ms_max"] == 20.0
         assert x["value"] == pytest.approx(1000.0 * 2 / 0.020)
     assert [x["reference_skipped"] for x in sorted(lines, key=lambda x: x["rank"])] == [None, True]
+
