@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
     tile_base[d] = digit_start + uint32_t(look_back<kStage ? kLookBackWide : kLookBack>(st, tile, d, tag, total,
                                                                                          dev_status));
     __syncthreads();
-    if (kStage) {
+    if constexpr (kStage) {
         const int64_t t0 = tile * kTileKeys;
         const int tile_n = n - t0 < kTileKeys ? int(n - t0) : kTileKeys;
         for (int slot = threadIdx.x; slot < tile_n; slot += kSortThreads) {
@@ -399,16 +399,16 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
             kout[pos] = k;
             if (kVals) vout[pos] = sval[slot];
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const int64_t i = base + int64_t(k) * 32 + lane;
-        if (i >= n) continue;
-        const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
-        const uint32_t pos = tile_base[d] + cnt[warp][d] + rank[k];
-        kout[pos] = key[k];
-        if (kVals) vout[pos] = kEarlyVals ? val[k] : vin[i];
+        for (int k = 0; k < kItems; ++k) {
+            const int64_t i = base + int64_t(k) * 32 + lane;
+            if (i >= n) continue;
+            const uint32_t d = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+            const uint32_t pos = tile_base[d] + cnt[warp][d] + rank[k];
+            kout[pos] = key[k];
+            if (kVals) vout[pos] = kEarlyVals ? val[k] : vin[i];
+        }
     }
 }
 }  // namespace
