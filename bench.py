@@ -10,7 +10,7 @@ slowest rank's mean step time).  `e2e` repeats the step through
 bgv_layout_host from pinned host memory (host-to-device copy of the edges and
 device-to-host copy of the layout inside the timed region).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22x]
     python bench.py --impl reference ...   # the CPU oracle, bounded sample
 
 Under torchrun (N > 1) every rank lays out its own replica of the workload on
@@ -37,15 +37,26 @@ if ROOT not in sys.path:
 import graphgen  # noqa: E402
 
 METRIC = "edges/s streamed (sketch+community), FA2 iters/s, % of HBM/FP32 peak"
-HBM_PEAK_GBS = 6798.2          # measured copy bandwidth of this machine's GB300
-SM_COUNT = 152
+FALLBACK_HBM_GBS = 6800.0      # the profiling recipe's fallback when no measured peak is on file
+FALLBACK_SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
 FLOPS_PER_INTERACTION = 12     # dx, dy, d2 (3), division, k*m*M (2), two FMAs (4)
-# DRAM bytes (read + write) of one k_repulse launch on the rmat20 supergraph,
-# from the ncu capture summarised in profiles/k_repulse_rmat20.md; valid only
-# while k_repulse is unchanged since that capture.
-REPULSE_TRAFFIC = {"rmat20": 51_802_880}
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth of
+    MEASURED_PEAKS.json at the repository root, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def fp32_peak_tflops(sms, mhz):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
 
 WORKLOADS = {
     "rmat20": dict(desc="R-MAT scale 20 (1,048,576 node ids), 10,000,000 unique edges, a,b,c,d=.57,.19,.19,.05, "
@@ -174,16 +185,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-
-
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(n, edges, cfg, fa2_iters_sample=1):
-    """Time the oracle (single-threaded C) on a bounded sample of one step:
-    the three edge stages on the full graph plus `fa2_iters_sample` FA2
-    iterations on the resulting supergraph.  Returns a dict with the
-    extrapolated step time (edge stages + iterations x FA2 iteration)."""
+def oracle_edge_stages(n, edges, cfg):
+    """The oracle's sketch, community rounds and supergraph on the whole
+    graph (single-threaded C); returns the supergraph and the seconds taken."""
     import oracle
     m = edges.shape[0]
     thr = cfg["threshold"] or (2 * m) // n
@@ -191,6 +196,16 @@ def oracle_sample(n, edges, cfg, fa2_iters_sample=1):
     _, dh = oracle.sketch_degrees(edges, n, cfg["rows"], cfg["width"], 1)
     lab, _ = oracle.communities(edges, n, dh, cfg["passes"], thr, cfg["growth"], 0)
     sg = oracle.supergraph(edges, n, lab, dh, cfg["rows"], cfg["width"], 1)
+    return sg, time.perf_counter() - t0
+
+
+def oracle_sample(n, edges, cfg, fa2_iters_sample=1):
+    """Time the oracle on a bounded sample of one step: the three edge stages
+    on the full graph plus `fa2_iters_sample` FA2 iterations on the resulting
+    supergraph.  Returns a dict with the extrapolated step time (edge stages
+    + iterations x FA2 iteration)."""
+    import oracle
+    sg, edge_s = oracle_edge_stages(n, edges, cfg)
     t1 = time.perf_counter()
     st = oracle.FA2State(oracle.fa2_init(sg["K"], 1))
     p = oracle.FA2Params()
@@ -198,8 +213,8 @@ def oracle_sample(n, edges, cfg, fa2_iters_sample=1):
         oracle.fa2_step(st, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p)
     t2 = time.perf_counter()
     t_fa2 = (t2 - t1) / max(fa2_iters_sample, 1)
-    step = (t1 - t0) + cfg["iterations"] * t_fa2
-    return dict(edge_s=t1 - t0, fa2_iter_s=t_fa2, step_s=step, wall_s=t2 - t0, K=sg["K"], Es=sg["Es"])
+    step = edge_s + cfg["iterations"] * t_fa2
+    return dict(edge_s=edge_s, fa2_iter_s=t_fa2, step_s=step, wall_s=edge_s + (t2 - t1), K=sg["K"], Es=sg["Es"])
 
 
 def cpu_info():
@@ -212,6 +227,34 @@ def cpu_info():
     except OSError:
         pass
     return model, os.cpu_count()
+
+
+# ------------------------------------------------------- shared reporting
+def workload_config(workload, n, m, world):
+    """The config dict of a single-graph workload, the same in both arms."""
+    cfg = WORKLOADS[workload]
+    thr = cfg["threshold"] or (2 * m) // n
+    return {"workload": f"{workload}: {cfg['desc']}", "n": n, "m": m, "sketch": f"{cfg['rows']}x{cfg['width']}",
+            "passes": cfg["passes"], "threshold": thr, "growth": cfg["growth"], "fa2_iterations": cfg["iterations"],
+            "theta": 1.2, "kr": 2.0, "kg": 1.0, "l2": "flushed before every timed step (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def repulse_roofline(inter_per_launch, launch_ms, dev, clk):
+    """FP32 roofline of the Barnes-Hut traversal: interactions x 12 flops per
+    launch over the launch's event-timed duration, against the FMA peak of
+    this GPU's SM count at its maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or FALLBACK_SM_MAX_MHZ
+    peak = fp32_peak_tflops(sms, mhz)
+    achieved = inter_per_launch * FLOPS_PER_INTERACTION / (launch_ms * 1e-3) / 1e12
+    return {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(achieved, 3),
+            "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "interactions_per_launch": int(inter_per_launch), "launch_ms": round(launch_ms, 4),
+            "peak_note": f"FP32 FMA peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz:.0f} MHz "
+                         "(unit counts of this GPU, maximum SM clock)",
+            "traffic_note": "DRAM bytes per launch come from an ncu capture of the current kernel, not from this run"}
 
 
 # --------------------------------------------------------------- GPU arm
@@ -330,22 +373,24 @@ def gpu_arm(args, dist: Dist):
     steps_run = st1.steps_total - st0.steps_total
     inter_per_launch = (st1.interactions_total - st0.interactions_total) / max(steps_run, 1)
     rep_launch_ms = fa2_stage_ms["repulsion"]  # per iteration = per launch
-    achieved_tf = inter_per_launch * FLOPS_PER_INTERACTION / (rep_launch_ms * 1e-3) / 1e12
-    peak_tf = fp32_peak_tflops()
-    roofline = {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(achieved_tf, 3),
-                "peak": round(peak_tf, 2), "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
-                "traffic": REPULSE_TRAFFIC.get(args.workload), "interactions_per_launch": int(inter_per_launch),
-                "launch_ms": round(rep_launch_ms, 4),
-                "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe unit counts, max clock)"}
+    roofline = repulse_roofline(inter_per_launch, rep_launch_ms, dev, clk)
 
     # edge stages against HBM
     sort_passes = math.ceil(2 * max(1, math.ceil(math.log2(max(n, 2)))) / 8)
     edge_bytes = (passes + 2) * 8 * m + sort_passes * 16 * m_cut
     edge_ms = stage_ms["sketch"] + stage_ms["communities"] + stage_ms["supergraph"]
     edge_gbs = edge_bytes / (edge_ms * 1e-3) / 1e9
-    edge_roofline = {"bound": "hbm", "achieved": round(edge_gbs, 1), "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                     "frac": round(edge_gbs / HBM_PEAK_GBS, 4), "algorithmic_bytes": int(edge_bytes),
+    hbm, hbm_src = hbm_peak()
+    edge_roofline = {"bound": "hbm", "achieved": round(edge_gbs, 1), "peak": hbm, "peak_source": hbm_src,
+                     "unit": "GB/s", "frac": round(edge_gbs / hbm, 4), "algorithmic_bytes": int(edge_bytes),
                      "edges_per_s": round(m / (edge_ms * 1e-3), 1), "ms": round(edge_ms, 4)}
+
+    # what the community stage made of the graph (outside the timed region)
+    ws_q = B.alloc_ws(B.bgv_modularity_ws_size(n), dev)
+    q = B.bgv_modularity(E, m, n, labels, ws_q, stream=s)
+    compression = {"isolated_ids": int(np.count_nonzero(np.bincount(edges_np.ravel(), minlength=n) == 0)),
+                   "K_over_n": round(K / n, 4), "m_cut_over_m": round(m_cut / max(m, 1), 4),
+                   "modularity_of_labels": round(q, 4)}
 
     # end to end through the host-buffer entry point
     lp = B.bgv_layout_default_params()
@@ -380,11 +425,8 @@ def gpu_arm(args, dist: Dist):
         "vs_baseline": None,
         "dtype": "i32+f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m, "sketch": f"{rows}x{width}",
-                   "passes": passes, "threshold": thr, "growth": growth, "fa2_iterations": iters, "theta": 1.2,
-                   "kr": 2.0, "kg": 1.0, "l2": "flushed before every timed step (256 MiB write)",
-                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-        "K": K, "Es": Es, "m_cut": m_cut,
+        "config": workload_config(args.workload, n, m, dist.world),
+        "K": K, "Es": Es, "m_cut": m_cut, "compression": compression,
         "fa2_iters_per_s": round(iters / (stage_ms["fa2"] * 1e-3), 2),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "fa2_stage_us_per_iteration": {k: round(1000 * v, 2) for k, v in fa2_stage_ms.items()},
@@ -515,7 +557,6 @@ def gpu_arm_whole(args, dist: Dist):
     stage = {nm: float(np.mean([r["fa2_stages"][i] for r in results])) for i, nm in enumerate(B.FA2_STAGE_NAMES)}
     inter = (st1.interactions_total - st0.interactions_total) / max(st1.steps_total - st0.steps_total, 1)
     rep_ms = stage["repulsion"]  # per iteration = per launch
-    ach = inter * FLOPS_PER_INTERACTION / (rep_ms * 1e-3) / 1e12
     out = {
         "metric": METRIC, "value": round(aggregate_throughput(m, dist.world, ms), 1), "unit": "edges/s",
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -527,10 +568,7 @@ def gpu_arm_whole(args, dist: Dist):
         "stage_ms": {k: round(float(np.mean([r[k] for r in results])), 4)
                      for k in ("communities", "graph_csr", "fa2")},
         "fa2_stage_us_per_iteration": {k: round(1000 * v, 2) for k, v in stage.items()},
-        "roofline": {"kernel": "k_repulse (Barnes-Hut traversal)", "bound": "alu", "achieved": round(ach, 3),
-                     "peak": round(fp32_peak_tflops(), 2), "unit": "TFLOP/s",
-                     "frac": round(ach / fp32_peak_tflops(), 4), "traffic": None,
-                     "interactions_per_launch": int(inter), "launch_ms": round(rep_ms, 4)},
+        "roofline": repulse_roofline(inter, rep_ms, dev, clk),
         "gpu_launches": int(launches), "clocks": clk,
     }
     if args.precision_sample:
@@ -774,31 +812,39 @@ def reference_arm_batched(args, dist: Dist):
 
 
 def reference_arm(args, dist: Dist):
-    """The oracle as the reference implementation, on the host cores."""
+    """The oracle as the reference implementation, on the host cores.  Its
+    edge stages run once on the full graph (timed), then every warm-up and
+    timed step is one oracle FA2 iteration on the resulting supergraph; a
+    step's time is the edge stages plus the workload's iterations x the
+    iteration time, so the run stays within a few minutes at full size."""
     if dist.rank != 0:
         return None
     if WORKLOADS[args.workload].get("batched"):
         return reference_arm_batched(args, dist)
+    import oracle
     cfg = WORKLOADS[args.workload]
     n, edges_np, _ = graphgen.load(args.workload)
     m = edges_np.shape[0]
-    steps = []
+    sg, edge_s = oracle_edge_stages(n, edges_np, cfg)
+    st = oracle.FA2State(oracle.fa2_init(sg["K"], 1))
+    p = oracle.FA2Params()
+    iters = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(n, edges_np, cfg)
+        t0 = time.perf_counter()
+        oracle.fa2_step(st, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], p)
         if i >= args.warmup:
-            steps.append(r)
-    step_s = float(np.mean([r["step_s"] for r in steps]))
+            iters.append(time.perf_counter() - t0)
+    fa2_iter_s = float(np.mean(iters))
+    step_s = edge_s + cfg["iterations"] * fa2_iter_s
     model, ncpu = cpu_info()
     value = round(m / step_s, 1)
-    sample = (f"each step: the three edge stages on the full {args.workload} graph plus 1 FA2 iteration on its "
-              f"supergraph; step time = edge stages + {cfg['iterations']} x FA2 iteration")
+    sample = (f"the three edge stages once on the full {args.workload} graph ({edge_s:.2f} s), then per step one "
+              f"FA2 iteration on its {sg['K']}-node supergraph (mean {fa2_iter_s:.2f} s); step time = edge stages "
+              f"+ {cfg['iterations']} x FA2 iteration = {step_s:.1f} s")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64",
-            "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {cfg['desc']}", "n": n, "m": m,
-                       "sketch": f"{cfg['rows']}x{cfg['width']}", "passes": cfg["passes"],
-                       "fa2_iterations": cfg["iterations"]},
+            "data": "synthetic", "config": workload_config(args.workload, n, m, dist.world),
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample,
                              "cpu": model, "host_cpus": ncpu},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -810,7 +856,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat22x", choices=sorted(WORKLOADS))
     ap.add_argument("--fa2-iterations", type=int, default=0,
                     help="override the workload's FA2 iteration count (short profiling runs only)")
     ap.add_argument("--stage-iterations", type=int, default=10,

@@ -39,9 +39,9 @@
  * Status.     Every call returns an int: BGV_OK, or an error detected on the
  *             host before any work is enqueued (BGV_EINVAL, BGV_ENOSPC), or
  *             BGV_ECUDA when a launch fails.  Errors found on the device (an
- *             edge endpoint outside [0, n), a label outside [0, n), a tree
- *             deeper than the traversal stack) are OR-ed into the status word
- *             in the workspace as BGV_DEV_* bits; read them with bgv_status.
+ *             edge endpoint outside [0, n), a label outside [0, n), a bounded
+ *             wait that gave up) are OR-ed into the status word in the
+ *             workspace as BGV_DEV_* bits; read them with bgv_status.
  *             Outputs of a call whose status word is non-zero are undefined.
  * Sizes.      Data-dependent sizes (K communities, Es superedges) are written
  *             to device int64 scalars, so a chain of calls needs no host
@@ -123,8 +123,10 @@ int bgv_sketch_degrees(const int32_t *edges, int64_t m, int32_t n, int32_t rows,
  * address (make it before any stream capture); every call clears the
  * counters, and all calls on a device share them, so calls whose work can
  * overlap on the GPU race and must be ordered on one stream.  Device-detected
- * bad edges are OR-ed into *status (device uint32, may be NULL).
- * Arguments otherwise as bgv_sketch_degrees. */
+ * bad edges are OR-ed into *status (device uint32).  status may be NULL:
+ * the call then uses a status word of its own (cleared on every call),
+ * synchronises `stream` at its end and returns BGV_EDEVICE if the device
+ * found a bad edge.  Arguments otherwise as bgv_sketch_degrees. */
 int bgv_sketch_degrees_noalloc(const int32_t *edges, int64_t m, int32_t n, int32_t rows, int32_t width,
                                uint64_t seed, uint32_t *sketch, uint32_t *deg_est, uint32_t *status,
                                void *stream);
@@ -260,9 +262,10 @@ int bgv_render(int64_t K, const float *xy, const float *radius, const uint8_t *g
  *   attraction -sum_j w_ij (p_i - p_j) over CSR neighbours;
  *   gravity    -kg m_i p_i / |p_i| (strong_gravity: -kg m_i p_i).
  * Step: swing_i = |F_i - Fprev_i|, traction_i = |F_i + Fprev_i| / 2;
- * S = sum m_i swing_i, T = sum m_i traction_i in FP64, added in a fixed
- * order (per thread, per block, then the block sums; batched: compensated
- * where a graph's threads meet); if S > 0,
+ * S = sum m_i swing_i, T = sum m_i traction_i over the FP32 per-node
+ * products, summed exactly (integer fixed-point accumulation) and rounded
+ * once to FP64, so they are the correctly rounded sums whatever the thread
+ * order (batched: per graph); if S > 0,
  * speed += min(tau T / S - speed, speed / 2); then
  * s_i = ks speed / (1 + speed sqrt(swing_i)), capped at ksmax / |F_i|;
  * p_i += s_i F_i; Fprev = F.
@@ -337,8 +340,9 @@ int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *c
  * the summed milliseconds per stage:
  *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order and
  *   moment prefix sums, 3 radix tree and quadtree cells, 4 pre-order layout,
- *   5 Barnes-Hut repulsion, 6 gravity + swing/traction + speed (after the
- *   attraction, which runs beside stages 0-5), 7 displacement.
+ *   5 Barnes-Hut repulsion, 6 the wait for the attraction (which runs beside
+ *   stages 0-5), 7 total force, swing/traction, speed and displacement (one
+ *   persistent kernel).
  * Creates and destroys (BGV_FA2_STAGES + 1) * iterations CUDA events. */
 #define BGV_FA2_STAGES 8
 int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
@@ -445,27 +449,88 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
                         float *Fprev, double *speed, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
- * 7. Autotuner.  The radix sort of the supergraph and ForceAtlas2 stages
- *    runs 8 keys per thread up to a size cutoff and 16 above it (one CTA
- *    wave of small tiles against fewer, larger tiles).  bgv_autotune_sort
- *    times both on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
- *    keys with 32-bit values, SplitMix64 of the index) and sets the cutoff
- *    to the largest size at which 8 was not slower.  The cutoff is process
- *    wide and starts at 2^22; workspaces stay valid whatever it is.
+ * 7. Autotuners.  The radix sort of the supergraph and ForceAtlas2 stages
+ *    runs either as one cooperative kernel for all its passes (method 1,
+ *    the default: per pass, digit counts per block chunk, a scan over the
+ *    chunks, then a stable scatter; no look-back) or as one onesweep kernel
+ *    per pass with decoupled look-back (method 0), which takes 8 keys per
+ *    thread up to a size cutoff and 16 above it.  bgv_autotune_sort times
+ *    all three forms on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
+ *    keys with 32-bit values, SplitMix64 of the index), sets the cutoff to
+ *    the largest size at which 8 was not slower and the method to the one
+ *    that summed less time.  Both are process wide; the cutoff starts at
+ *    2^40 (8 keys per thread at every size, which measured faster on GB300);
+ *    workspaces stay valid whatever they are.  bgv_set_sort_cutoff and
+ *    bgv_set_sort_method set them directly and return the previous value.
  *    Synchronises `stream` once per timed sort.  The paper has no
  *    counterpart.
  * ---------------------------------------------------------------------- */
 typedef struct bgv_tune_report {
     int32_t count;          /* sizes timed */
     int32_t sizes_log2[9];  /* log2 of each size */
-    float ms8[9];           /* median milliseconds, 8 keys per thread */
-    float ms16[9];          /* median milliseconds, 16 keys per thread */
+    float ms8[9];           /* median milliseconds, onesweep, 8 keys per thread */
+    float ms16[9];          /* median milliseconds, onesweep, 16 keys per thread */
+    float ms_coop[9];       /* median milliseconds, cooperative sort */
+    int32_t method;         /* the method now in force: 1 cooperative, 0 onesweep */
     int64_t cutoff;         /* the cutoff now in force */
 } bgv_tune_report;
+
+/* bgv_autotune_fa2 picks the launch shapes of the ForceAtlas2 step on the
+ * caller's supergraph: the CSR entries per warp range of the attraction
+ * (256, 512, 1024), the threads per block of the Barnes-Hut traversal (128,
+ * 256) and the blocks per SM of the persistent tail kernel (2, 4, 8; capped
+ * at what stays resident).  One shape at a time, it times whole steps (the
+ * median of three after a warm-up step) from positions `pos` (device, not
+ * changed: steps run on a copy in `ws`, with Fprev = 0 and speed 1), keeps
+ * the fastest, and leaves the choice in force for the process.  The traversal
+ * and tail shapes do not change any result; the attraction range changes the
+ * grouping of its FP32 row sums (within rounding).  Synchronises `stream`.
+ * bgv_set_fa2_tune sets the shapes directly (BGV_EINVAL for other values). */
+typedef struct bgv_fa2_tune_report {
+    int32_t att_range;          /* chosen CSR entries per attraction warp range */
+    int32_t repulse_threads;    /* chosen threads per block of the traversal */
+    int32_t tail_blocks_per_sm; /* chosen blocks per SM of the step's tail */
+    int32_t reserved;
+    float ms_att_range[3];      /* median step ms at 256, 512, 1024 entries */
+    float ms_repulse_threads[2];/* at 128, 256 threads */
+    float ms_tail_blocks[3];    /* at 2, 4, 8 blocks per SM */
+} bgv_fa2_tune_report;
+
+size_t bgv_autotune_fa2_ws_size(int64_t K, int64_t nnz);
+int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                     const uint32_t *mass, const bgv_fa2_params *p, const float *pos, bgv_fa2_tune_report *out,
+                     void *ws, size_t ws_bytes, void *stream);
+int bgv_set_fa2_tune(int32_t att_range, int32_t repulse_threads, int32_t tail_blocks_per_sm);
 
 size_t bgv_autotune_sort_ws_size(int64_t max_keys);
 int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t ws_bytes, void *stream);
 int64_t bgv_sort_cutoff(void);
+int64_t bgv_set_sort_cutoff(int64_t cutoff);
+int32_t bgv_set_sort_method(int32_t method);
+
+/* ------------------------------------------------------------------------
+ * 8. Bounded waits.  Every decoupled look-back wait in the library (radix
+ *    sort passes, the ForceAtlas2 moment pass, the CSR pass of the
+ *    supergraph) polls at most `limit` rounds for a predecessor tile, then
+ *    sets BGV_DEV_TIMEOUT in the status word and lets its block finish, so a
+ *    wait that cannot end is reported instead of hanging the GPU.  The paper
+ *    has no counterpart: this is the library's own failure detection.
+ *
+ * bgv_set_spin_limit sets the bound for the process (limit >= 0; default
+ * 2^22 rounds, a few seconds) and returns the previous one (-1 and no
+ * change for a negative limit).  A CUDA graph captured earlier keeps the
+ * bound it was captured with.
+ *
+ * bgv_check_wait_timeout runs one block of look-back kernel `which` (0 a
+ * radix-sort pass, 1 the moment pass, 2 the CSR pass) as the second tile of
+ * a two-tile input whose first tile never runs, so its wait cannot end and
+ * must give up at the bound: afterwards the status word of `ws` holds
+ * BGV_DEV_TIMEOUT.  Synchronises `stream`.  ws: a workspace of
+ * bgv_check_wait_timeout_ws_size() bytes (header zeroed, see bgv_ws_init).
+ * ---------------------------------------------------------------------- */
+int32_t bgv_set_spin_limit(int32_t limit);
+size_t bgv_check_wait_timeout_ws_size(void);
+int bgv_check_wait_timeout(int32_t which, void *ws, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,7 @@ class bgv_fa2_stats(C.Structure):
 
 class bgv_tune_report(C.Structure):
     _fields_ = [("count", i32), ("sizes_log2", i32 * 9), ("ms8", C.c_float * 9), ("ms16", C.c_float * 9),
-                ("cutoff", i64)]
+                ("ms_coop", C.c_float * 9), ("method", i32), ("cutoff", i64)]
 
 
 class bgv_layout_params(C.Structure):
@@ -104,9 +104,24 @@ _sig("bgv_fa2_forces_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_
 _sig("bgv_fa2_run_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_fa2_params), i32, i32, P, P, P, P, P,
                                       sz, P])
 
+class bgv_fa2_tune_report(C.Structure):
+    _fields_ = [("att_range", i32), ("repulse_threads", i32), ("tail_blocks_per_sm", i32), ("reserved", i32),
+                ("ms_att_range", C.c_float * 3), ("ms_repulse_threads", C.c_float * 2),
+                ("ms_tail_blocks", C.c_float * 3)]
+
+
+_sig("bgv_autotune_fa2_ws_size", sz, [i64, i64])
+_sig("bgv_autotune_fa2", C.c_int, [i64, i64, P, P, P, P, C.POINTER(bgv_fa2_params), P,
+                                   C.POINTER(bgv_fa2_tune_report), P, sz, P])
+_sig("bgv_set_fa2_tune", C.c_int, [i32, i32, i32])
 _sig("bgv_autotune_sort_ws_size", sz, [i64])
 _sig("bgv_autotune_sort", C.c_int, [i64, C.POINTER(bgv_tune_report), P, sz, P])
 _sig("bgv_sort_cutoff", i64, [])
+_sig("bgv_set_sort_cutoff", i64, [i64])
+_sig("bgv_set_sort_method", i32, [i32])
+_sig("bgv_set_spin_limit", i32, [i32])
+_sig("bgv_check_wait_timeout_ws_size", sz, [])
+_sig("bgv_check_wait_timeout", C.c_int, [i32, P, sz, P])
 
 #: every symbol this binding resolves from the library
 EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sketch_degrees_ws_size", "bgv_sketch_degrees", "bgv_sketch_degrees_noalloc",
@@ -119,7 +134,9 @@ EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sket
            "bgv_fa2_run", "bgv_fa2_run_timed", "bgv_launch_count", "bgv_fa2_read_stats", "bgv_layout_default_params", "bgv_layout_ws_size", "bgv_layout",
            "bgv_layout_host_ws_size", "bgv_layout_host", "bgv_layout_batched_ws_size", "bgv_layout_batched",
            "bgv_fa2_ws_size_batched", "bgv_fa2_init_batched", "bgv_fa2_forces_batched", "bgv_fa2_run_batched",
-           "bgv_autotune_sort_ws_size", "bgv_autotune_sort", "bgv_sort_cutoff"]
+           "bgv_autotune_fa2_ws_size", "bgv_autotune_fa2", "bgv_set_fa2_tune",
+           "bgv_autotune_sort_ws_size", "bgv_autotune_sort", "bgv_sort_cutoff", "bgv_set_sort_cutoff", "bgv_set_sort_method",
+           "bgv_set_spin_limit", "bgv_check_wait_timeout_ws_size", "bgv_check_wait_timeout"]
 
 
 class BgvError(RuntimeError):
@@ -316,7 +333,7 @@ def bgv_fa2_run(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, use_g
 
 
 BGV_FA2_STAGES = 8
-FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "preorder", "repulsion", "node_speed", "update"]
+FA2_STAGE_NAMES = ["frame_keys", "sort", "gather", "tree", "preorder", "repulsion", "attraction_wait", "node_speed_update"]
 
 
 def bgv_fa2_run_timed(K, nnz, csr_off, csr_adj, csr_w, mass, params, iterations, pos, F, Fprev, speed, ws,
@@ -433,3 +450,49 @@ def bgv_autotune_sort(max_keys, ws, ws_bytes=None, stream=None) -> bgv_tune_repo
 
 def bgv_sort_cutoff() -> int:
     return _lib.bgv_sort_cutoff()
+
+
+def bgv_set_sort_cutoff(cutoff: int) -> int:
+    """Keys per thread of the radix sort: 8 up to `cutoff` keys, 16 above;
+    returns the previous cutoff."""
+    return int(_lib.bgv_set_sort_cutoff(cutoff))
+
+
+def bgv_set_spin_limit(limit: int) -> int:
+    """Bound of every look-back wait (polling rounds); returns the previous."""
+    return int(_lib.bgv_set_spin_limit(limit))
+
+
+def bgv_check_wait_timeout_ws_size() -> int:
+    return _lib.bgv_check_wait_timeout_ws_size()
+
+
+def bgv_check_wait_timeout(which, ws, ws_bytes=None, stream=None):
+    """Run look-back kernel `which` (0 sort pass, 1 moment pass, 2 CSR pass)
+    on an input whose predecessor tile never publishes; its wait must give
+    up at the spin limit (BGV_DEV_TIMEOUT in the workspace status word)."""
+    _chk(_lib.bgv_check_wait_timeout(which, _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_check_wait_timeout")
+
+
+def bgv_autotune_fa2_ws_size(K: int, nnz: int) -> int:
+    return _lib.bgv_autotune_fa2_ws_size(K, nnz)
+
+
+def bgv_autotune_fa2(K, nnz, csr_off, csr_adj, csr_w, mass, params, pos, ws, ws_bytes=None,
+                     stream=None) -> bgv_fa2_tune_report:
+    """Time FA2 steps on this supergraph for each launch shape and keep the
+    fastest (process wide); returns the report."""
+    r = bgv_fa2_tune_report()
+    _chk(_lib.bgv_autotune_fa2(K, nnz, _p(csr_off), _p(csr_adj), _p(csr_w), _p(mass), C.byref(params), _p(pos),
+                               C.byref(r), _p(ws), _nbytes(ws, ws_bytes), _s(stream)), "bgv_autotune_fa2")
+    return r
+
+
+def bgv_set_fa2_tune(att_range: int, repulse_threads: int, tail_blocks_per_sm: int):
+    _chk(_lib.bgv_set_fa2_tune(att_range, repulse_threads, tail_blocks_per_sm), "bgv_set_fa2_tune")
+
+
+def bgv_set_sort_method(method: int) -> int:
+    """1: all radix passes in one cooperative kernel, 0: onesweep passes with
+    decoupled look-back; returns the previous method."""
+    return int(_lib.bgv_set_sort_method(method))

@@ -3,6 +3,7 @@
 // Host-side validation, workspace sizing and carving, and the pipeline that
 // chains the stages (Algorithm 3 end to end).  Everything on the data path
 // runs in the kernels of sketch.cu, communities.cu, supergraph.cu and fa2.cu.
+#include <algorithm>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -257,7 +258,7 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
         CommScratch s;
         carve_comm(c, m, n, s);
         BGV_TRY(run_communities(edges, m, n, b.deg_est, p->passes, D, p->growth, p->tie_mode, p->jumps, b.labels,
-                                nullptr, s, status, st));
+                                nullptr, s, status, st, nullptr, hdr));
     }
     {
         Carver c(b.scratch, 0);
@@ -281,7 +282,7 @@ int layout_device(const int32_t *edges, int64_t m, int32_t n, const bgv_layout_p
     BGV_TRY(fa2_loop(K, 2 * KE[1], b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
                      b.Fprev, b.speed, hdr, b.scratch, st));
     if (radius) {
-        note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
+        note_launch(), k_radius<<<grid_for(K, 256, sm_count() * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
         BGV_TRY(launch_status());
     }
     return BGV_OK;
@@ -416,10 +417,10 @@ int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, c
     BGV_CUDA(cudaMemcpyAsync(bb.node_off, node_off, sizeof(int32_t) * (size_t(G) + 1), cudaMemcpyHostToDevice, st));
     BGV_CUDA(cudaMemcpyAsync(bb.edge_off, edge_off, sizeof(int64_t) * (size_t(G) + 1), cudaMemcpyHostToDevice, st));
     BGV_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
-    note_launch(), k_batch_nodes<<<grid_for(N, 256, 152 * 8), 256, 0, st>>>(N, G, bb.node_off, bb.node_graph);
+    note_launch(), k_batch_nodes<<<grid_for(N, 256, sm_count() * 8), 256, 0, st>>>(N, G, bb.node_off, bb.node_graph);
     BGV_TRY(launch_status());
     if (m > 0) {
-        note_launch(), k_batch_edges<<<grid_for(m, 256, 152 * 16), 256, 0, st>>>(edges_local, m, G, bb.edge_off,
+        note_launch(), k_batch_edges<<<grid_for(m, 256, sm_count() * 16), 256, 0, st>>>(edges_local, m, G, bb.edge_off,
                                                                                   bb.node_off, bb.edges);
         BGV_TRY(launch_status());
     }
@@ -441,8 +442,7 @@ int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, c
         CommScratch s;
         carve_comm(sc, m, N, s, true);
         BGV_TRY(run_communities(bb.edges, m, N, b.deg_est, p->passes, 0, p->growth, p->tie_mode, p->jumps, b.labels,
-                                nullptr, s,
-                                status, st, &view));
+                                nullptr, s, status, st, &view, hdr));
     }
     {
         Carver sc(b.scratch, 0);
@@ -451,11 +451,11 @@ int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, c
         BGV_TRY(run_supergraph(bb.edges, m, N, b.labels, b.deg_est, h, bb.node_map, b.K_dev, b.ssrc, b.sdst, b.sw,
                                b.Es_dev, b.mass, b.csr_off, b.csr_adj, b.csr_w, nullptr, nullptr, nullptr, s, status,
                                st, &view));
-        note_launch(), k_batch_offsets<<<grid_for(int64_t(G) + 1, 256, 152), 256, 0, st>>>(
+        note_launch(), k_batch_offsets<<<grid_for(int64_t(G) + 1, 256, sm_count()), 256, 0, st>>>(
             G, bb.node_off, s.rank, b.K_dev, b.ssrc, b.Es_dev, bb.koff, bb.Es_off);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_batch_local_map<<<grid_for(N, 256, 152 * 8), 256, 0, st>>>(N, bb.node_map, bb.node_graph,
+    note_launch(), k_batch_local_map<<<grid_for(N, 256, sm_count() * 8), 256, 0, st>>>(N, bb.node_map, bb.node_graph,
                                                                                   bb.koff, node_map);
     BGV_TRY(launch_status());
     uint32_t dev_status = 0;
@@ -469,7 +469,7 @@ int layout_batched_device(const int32_t *edges_local, const int64_t *edge_off, c
     BGV_TRY(fa2_loop(K, 2 * Es, b.csr_off, b.csr_adj, b.csr_w, b.mass, p->fa2, p->iterations, p->use_graph, xy, b.F,
                      b.Fprev, b.speed, hdr, b.scratch, st, G, bb.koff));
     if (radius) {
-        note_launch(), k_radius<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
+        note_launch(), k_radius<<<grid_for(K, 256, sm_count() * 8), 256, 0, st>>>(b.mass, b.K_dev, radius);
         BGV_TRY(launch_status());
     }
     return BGV_OK;
@@ -565,7 +565,7 @@ int bgv_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *
     carve_comm(c, m, n, s);
     const uint32_t D = threshold ? threshold : uint32_t((2 * m) / n);
     return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, 0, labels, deg_out, s, status_ptr(ws),
-                           as_stream(stream));
+                           as_stream(stream), nullptr, header(ws));
 }
 
 size_t bgv_communities_ex_ws_size(int64_t m, int32_t n) {
@@ -607,7 +607,7 @@ int bgv_communities_ex(const int32_t *edges, int64_t m, int32_t n, const uint32_
     CommScratch s;
     carve_comm(rc, m, n, s);
     return run_communities(edges, m, n, deg_est, passes, D, growth, tie_mode, jumps, labels, deg_out, s,
-                           status_ptr(ws), st);
+                           status_ptr(ws), st, nullptr, header(ws));
 }
 
 size_t bgv_mode_degree_ws_size(int32_t n) {
@@ -666,12 +666,12 @@ int bgv_graph_csr(const int32_t *edges, int64_t m, int32_t n, int32_t *csr_off, 
     GraphCsrBuffers b;
     carve_graph_csr(c, m, n, b);
     cudaStream_t st = as_stream(stream);
-    note_launch(), k_identity_labels<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, b.labels, b.zero);
+    note_launch(), k_identity_labels<<<grid_for(n, 256, sm_count() * 8), 256, 0, st>>>(n, b.labels, b.zero);
     BGV_TRY(launch_status());
     const HashFamily h = make_hash_family(1, 1, 1);
     BGV_TRY(run_supergraph(edges, m, n, b.labels, b.zero, h, b.node_map, b.K_dev, b.ssrc, b.sdst, b.sw, b.Es_dev,
                            b.mass_tmp, csr_off, csr_adj, csr_w, nullptr, nullptr, nullptr, b.super, status_ptr(ws), st));
-    note_launch(), k_mass_from_degree<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, csr_off, mass, nnz_dev);
+    note_launch(), k_mass_from_degree<<<grid_for(n, 256, sm_count() * 8), 256, 0, st>>>(n, csr_off, mass, nnz_dev);
     return launch_status();
 }
 
@@ -965,6 +965,103 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
                     header(ws), scratch, st, G, dkoff);
 }
 
+size_t bgv_autotune_fa2_ws_size(int64_t K, int64_t nnz) {
+    Carver c(nullptr, kHeaderBytes);
+    const size_t k = size_t(K > 0 ? K : 1);
+    c.take<float>(2 * k);  // positions
+    c.take<float>(2 * k);  // F
+    c.take<float>(2 * k);  // Fprev
+    c.take<double>(1);     // speed
+    c.take<char>(fa2_scratch_bytes(K, nnz));
+    return c.used();
+}
+
+int bgv_set_fa2_tune(int32_t att_range, int32_t repulse_threads, int32_t tail_blocks_per_sm) {
+    return set_fa2_tune(Fa2Tune{att_range, repulse_threads, tail_blocks_per_sm});
+}
+
+int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
+                     const uint32_t *mass, const bgv_fa2_params *p, const float *pos, bgv_fa2_tune_report *out,
+                     void *ws, size_t ws_bytes, void *stream) {
+    if (K < 1 || K >= 0x7FFFFFFF || nnz < 0 || !csr_off || !mass || !pos || (nnz > 0 && (!csr_adj || !csr_w)))
+        return BGV_EINVAL;
+    BGV_TRY(fa2_check_params(p));
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_autotune_fa2_ws_size(K, nnz)));
+    cudaStream_t st = as_stream(stream);
+    Carver c(ws, kHeaderBytes);
+    const size_t k = size_t(K);
+    float *P = c.take<float>(2 * k), *F = c.take<float>(2 * k), *Fprev = c.take<float>(2 * k);
+    double *speed = c.take<double>(1);
+    void *scratch = c.take<char>(0);
+    WsHeader *hdr = header(ws);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BGV_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BGV_ECUDA;
+    }
+    const double one = 1.0;
+    // median of three timed steps (after one warm-up step that builds the
+    // attraction plan) from the caller's positions
+    auto time_steps = [&](float *ms) -> int {
+        BGV_CUDA(cudaMemcpyAsync(P, pos, sizeof(float) * 2 * k, cudaMemcpyDeviceToDevice, st));
+        BGV_CUDA(cudaMemsetAsync(Fprev, 0, sizeof(float) * 2 * k, st));
+        BGV_CUDA(cudaMemcpyAsync(speed, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        float t[3];
+        for (int r = 0; r < 4; ++r) {
+            BGV_CUDA(cudaEventRecord(e0, st));
+            BGV_TRY(run_fa2(1, K, nnz, csr_off, csr_adj, csr_w, mass, *p, P, F, Fprev, speed, nullptr, nullptr,
+                            nullptr, hdr, scratch, st, nullptr, r == 0));
+            BGV_CUDA(cudaEventRecord(e1, st));
+            BGV_CUDA(cudaEventSynchronize(e1));
+            float x = 0.0f;
+            BGV_CUDA(cudaEventElapsedTime(&x, e0, e1));
+            if (r > 0) t[r - 1] = x;
+        }
+        std::sort(t, t + 3);
+        *ms = t[1];
+        return BGV_OK;
+    };
+    bgv_fa2_tune_report r;
+    memset(&r, 0, sizeof(r));
+    Fa2Tune best = fa2_tune();
+    const int ranges[3] = {256, 512, 1024}, threads[2] = {128, 256}, tails[3] = {2, 4, 8};
+    int rc = BGV_OK;
+    float best_ms = 0.0f;
+    for (int i = 0; i < 3 && rc == BGV_OK; ++i) {
+        Fa2Tune t = best;
+        t.att_range = ranges[i];
+        set_fa2_tune(t);
+        rc = time_steps(&r.ms_att_range[i]);
+        if (rc == BGV_OK && (i == 0 || r.ms_att_range[i] < best_ms)) best_ms = r.ms_att_range[i], best.att_range = ranges[i];
+    }
+    for (int i = 0; i < 2 && rc == BGV_OK; ++i) {
+        Fa2Tune t = best;
+        t.repulse_threads = threads[i];
+        set_fa2_tune(t);
+        rc = time_steps(&r.ms_repulse_threads[i]);
+        if (rc == BGV_OK && (i == 0 || r.ms_repulse_threads[i] < best_ms))
+            best_ms = r.ms_repulse_threads[i], best.repulse_threads = threads[i];
+    }
+    for (int i = 0; i < 3 && rc == BGV_OK; ++i) {
+        Fa2Tune t = best;
+        t.tail_blocks_per_sm = tails[i];
+        set_fa2_tune(t);
+        rc = time_steps(&r.ms_tail_blocks[i]);
+        if (rc == BGV_OK && (i == 0 || r.ms_tail_blocks[i] < best_ms))
+            best_ms = r.ms_tail_blocks[i], best.tail_blocks_per_sm = tails[i];
+    }
+    set_fa2_tune(best);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BGV_TRY(rc);
+    r.att_range = best.att_range;
+    r.repulse_threads = best.repulse_threads;
+    r.tail_blocks_per_sm = best.tail_blocks_per_sm;
+    if (out) *out = r;
+    return BGV_OK;
+}
+
 size_t bgv_autotune_sort_ws_size(int64_t max_keys) {
     Carver c(nullptr, kHeaderBytes);
     SortBuffers b;
@@ -981,13 +1078,53 @@ int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t w
     bgv_tune_report r;
     memset(&r, 0, sizeof(r));
     int32_t count = 0;
-    BGV_TRY(autotune_sort(max_keys, b, as_stream(stream), status_ptr(ws), r.ms8, r.ms16, r.sizes_log2, &count));
+    int32_t method = 0;
+    BGV_TRY(autotune_sort(max_keys, b, as_stream(stream), status_ptr(ws), r.ms8, r.ms16, r.ms_coop, r.sizes_log2,
+                          &count, &method));
     r.count = count;
+    r.method = method;
     r.cutoff = sort_cutoff();
     if (out) *out = r;
     return BGV_OK;
 }
 
 int64_t bgv_sort_cutoff(void) { return sort_cutoff(); }
+
+int64_t bgv_set_sort_cutoff(int64_t cutoff) {
+    if (cutoff < 0) return -1;
+    return set_sort_cutoff(cutoff);
+}
+
+int32_t bgv_set_sort_method(int32_t method) {
+    if (method != 0 && method != 1) return -1;
+    return set_sort_method(method);
+}
+
+int32_t bgv_set_spin_limit(int32_t limit) {
+    if (limit < 0) return -1;
+    return set_spin_limit(limit);
+}
+
+size_t bgv_check_wait_timeout_ws_size(void) {
+    size_t need = wait_check_sort_bytes();
+    need = wait_check_moments_bytes() > need ? wait_check_moments_bytes() : need;
+    need = wait_check_reduce_bytes() > need ? wait_check_reduce_bytes() : need;
+    Carver c(nullptr, kHeaderBytes);
+    c.take<char>(need);
+    return c.used();
+}
+
+int bgv_check_wait_timeout(int32_t which, void *ws, size_t ws_bytes, void *stream) {
+    BGV_TRY(check_ws(ws, ws_bytes, bgv_check_wait_timeout_ws_size()));
+    Carver c(ws, kHeaderBytes);
+    void *scratch = c.take<char>(0);
+    cudaStream_t st = as_stream(stream);
+    switch (which) {
+        case 0: return wait_check_sort(scratch, status_ptr(ws), st);
+        case 1: return wait_check_moments(scratch, status_ptr(ws), st);
+        case 2: return wait_check_reduce(scratch, status_ptr(ws), st);
+        default: return BGV_EINVAL;
+    }
+}
 
 }  // extern "C"

@@ -14,6 +14,13 @@
 namespace bgv {
 
 // ---------------------------------------------------------------- workspace
+// Grid barrier words of a persistent kernel: arrivals (back to 0 after each
+// barrier), generation, and an abort word set when a wait gave up (it stays
+// set, and the barriers using these words fail at once, until cleared).
+struct GridBar {
+    unsigned int count, gen, abort, pad;
+};
+
 // Every public workspace starts with this header (kHeaderBytes bytes).
 struct WsHeader {
     uint32_t status;        // BGV_DEV_* bits
@@ -27,7 +34,9 @@ struct WsHeader {
     double S, T;                      // FA2: swing and traction of the last step
     unsigned int bbox_ticket;         // last-block tickets (reset by the last block)
     unsigned int node_ticket;
-    unsigned long long reserved[22];
+    // grid barrier of the persistent kernels (see GridBar)
+    GridBar bar;
+    unsigned long long reserved[20];
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit in 256 bytes");
 constexpr size_t kHeaderBytes = 256;
@@ -72,7 +81,20 @@ void note_launch();
 void add_launches(unsigned long long n);
 unsigned long long launches_issued();
 
-inline int grid_for(int64_t work, int threads, int64_t cap_blocks = 152 * 16) {
+// Polling rounds after which a decoupled look-back wait gives up and sets
+// BGV_DEV_TIMEOUT (passed to the kernels at launch; process wide).
+int spin_limit();
+int set_spin_limit(int limit);  // returns the previous limit
+
+// Multiprocessors of the current device (queried once per device and
+// cached; 1 if the query fails, which keeps every grid-stride launch valid).
+int sm_count();
+
+// Blocks for `work` items of `threads` each, at most `cap_blocks` (default:
+// 16 per multiprocessor); every kernel launched this way strides over the
+// grid, so the cap only sets how many blocks share the work.
+inline int grid_for(int64_t work, int threads, int64_t cap_blocks = -1) {
+    if (cap_blocks < 1) cap_blocks = int64_t(sm_count()) * 16;
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > cap_blocks) b = cap_blocks;
@@ -134,10 +156,10 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out);
 int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit, cudaStream_t s,
                int *result_buffer, uint32_t *dev_status, int items = 0);
 
-// The same order for n (key, value) pairs (host-known count) when the keys
+// The same order (keys, with values when b.vals[0] is set) when the keys
 // are nearly always told apart above their low 16 bits: LSD passes on bits
 // 16.. only, then every run of equal high bits sorted locally on its low
-// bits.
+// bits.  Count = *d_count if given, else cap.
 struct RunFixBuffers {
     uint8_t *descent;   // per 32-key chunk: holds a key below its predecessor in the same run
     uint32_t *runs;     // starts of runs too long for one thread
@@ -148,17 +170,24 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r);
 // Words of SortBuffers::counts (digit counts and tile counters): cleared
 // before a sort, by the sort itself unless its caller cleared them.
 int64_t sort_counter_words();
-int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
-                    int *result_buffer, uint32_t *dev_status, bool counters_cleared = false);
+int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const int64_t *d_count, int end_bit,
+                    cudaStream_t s, int *result_buffer, uint32_t *dev_status, bool counters_cleared = false);
 
-// Sort autotuner: times 8 against 16 keys per thread for 2^14, 2^16, ...
-// up to max_keys and sets the cutoff between them for the whole process.
-// Per size k (count of them in *count): ms8[k], ms16[k], sizes_log2[k]
-// (host arrays, may be NULL; 9 entries suffice).  b must hold max_keys
-// pairs.
+// Sort autotuner: times the onesweep passes at 8 and at 16 keys per thread
+// and the cooperative sort for 2^14, 2^16, ... up to max_keys; sets the
+// cutoff between 8 and 16 (the largest size at which 8 was not slower) and
+// the method that summed less time, for the whole process.  Per size k
+// (count of them in *count): ms8[k], ms16[k], ms_coop[k], sizes_log2[k]
+// (host arrays, may be NULL; 9 entries suffice); *method: 1 cooperative, 0
+// onesweep.  b must hold max_keys pairs.
 int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
-                  int32_t *sizes_log2, int32_t *count);
+                  float *ms_coop, int32_t *sizes_log2, int32_t *count, int32_t *method);
 int64_t sort_cutoff();
+int64_t set_sort_cutoff(int64_t cutoff);  // returns the previous cutoff
+// 1: all passes in one cooperative kernel (default), 0: onesweep passes with
+// decoupled look-back.  Process wide; returns the previous method.
+int set_sort_method(int method);
+int sort_method();
 
 
 
@@ -168,6 +197,55 @@ inline int bits_for(int64_t n) {
     while (b < 62 && (int64_t(1) << b) < n) ++b;
     return b;
 }
+
+// ------------------------------------------------- persistent kernels
+// Grid-wide barrier for kernels launched cooperatively (all blocks resident
+// at once).  The last block to arrive resets the count and advances the
+// generation; the others poll the generation for at most spin_limit rounds,
+// then set BGV_DEV_TIMEOUT and the abort word, and every later barrier of the
+// workspace returns false at once.  Returns true when all blocks arrived.
+__device__ __forceinline__ bool grid_barrier(GridBar *h, int spin_limit, uint32_t *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &h->gen, *abort = &h->abort;
+        const unsigned int g = *gen;  // read before arriving
+        __threadfence();
+        int good = *abort == 0u;
+        if (good) {
+            if (atomicAdd(&h->count, 1u) + 1u == gridDim.x) {
+                h->count = 0u;
+                __threadfence();
+                atomicAdd(&h->gen, 1u);
+            } else {
+                int spins = 0;
+                while (*gen == g) {
+                    if (*abort != 0u) {
+                        good = 0;
+                        break;
+                    }
+                    if (++spins > spin_limit) {
+                        atomicOr(status, BGV_DEV_TIMEOUT);
+                        atomicExch(&h->abort, 1u);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Blocks of `threads` threads that a cooperative launch of `kernel` can keep
+// resident at once, at most `want` (at least 1).
+int coop_blocks(const void *kernel, int threads, int want);
+// Cooperative launch on `st` (all blocks resident together).
+int launch_coop(const void *kernel, int blocks, int threads, void **args, cudaStream_t st);
 
 // --------------------------------------------------------- stage internals
 // Enqueue-only stage bodies used by the public entry points and the
@@ -203,10 +281,12 @@ void carve_comm(Carver &c, int64_t m, int32_t n, CommScratch &s, bool batched = 
 // delta^i schedule).  `jumps` pointer-jumping steps follow every round.
 // With `batch`, the threshold of every node starts at its graph's D0 and
 // `threshold` is ignored.
+// All rounds run in one persistent kernel whose grid barrier lives in `hdr`
+// (the workspace header); its waits are bounded (BGV_DEV_TIMEOUT).
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t jumps, int32_t *labels,
                     uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st,
-                    const BatchView *batch = nullptr);
+                    const BatchView *batch, WsHeader *hdr);
 
 // Mode degree: the most frequent nonzero value of deg (ties: the smaller),
 // 0 if none; with `batch`, one per graph.  mode_dev: device, 1 or G values.
@@ -219,19 +299,18 @@ int run_mode_degree(const uint32_t *deg, int32_t n, const BatchView *batch, uint
                     const ModeScratch &s, uint32_t *status, cudaStream_t st);
 
 struct SuperScratch {
-    uint32_t *flags;        // [n] label present / CSR counts
+    uint32_t *flags;        // [n+1] label present
     uint32_t *rank;         // [n+1]
     int32_t *label_of;      // [n]
-    uint32_t *src_first, *src_end;  // [n] runs of each supernode in (src, dst) order
-    uint32_t *dst_first, *dst_end;  // [n] runs in (dst, src) order
-    int64_t *m_cut;         // device scalar
+    unsigned long long *nkeys;  // device count of (row, col) keys
+    int64_t *nnz;           // device count of CSR entries
     unsigned long long *sketch;  // [rows * width], batched form: one per graph
-    uint32_t *heads;        // [m]
-    uint32_t *segidx;       // [m + 1]
-    uint32_t *segstart;     // [m]
+    uint32_t *start;        // [2m + 1] first sorted key of every CSR entry
+    int32_t *supidx;        // [2m] superedge of every CSR entry, -1 for col < row
+    uint32_t *red_flags;    // look-back flags of the CSR pass, then its tile counter
+    unsigned long long *red_agg, *red_incl;
     void *scan_tmp;
-    SortBuffers sort_cut;   // m keys
-    SortBuffers sort_dst;   // m keys + values
+    SortBuffers sort_pairs;   // 2m keys
 };
 void carve_super(Carver &c, int64_t m, int32_t n, int32_t rows, int32_t width, SuperScratch &s, int32_t G = 1);
 // With `batch`, community labels are node ids of their own graph, so the
@@ -242,6 +321,16 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
                    uint32_t *sw, int64_t *Es_dev, uint32_t *mass, int32_t *csr_off, int32_t *csr_adj,
                    uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
                    const SuperScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch = nullptr);
+
+// Launch shapes of a FA2 step (process wide; chosen by the autotuner):
+// CSR entries per attraction warp range (256, 512, 1024), threads per block
+// of the Barnes-Hut traversal (128, 256), blocks per SM of the persistent
+// tail kernel (1..8, at most what stays resident).
+struct Fa2Tune {
+    int att_range, repulse_threads, tail_blocks_per_sm;
+};
+Fa2Tune fa2_tune();
+int set_fa2_tune(const Fa2Tune &t);
 
 // Scratch for one FA2 step over G graphs (G = 1: a single layout), carved
 // from `scratch` (not counting a header).
@@ -263,5 +352,15 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
             cudaEvent_t *marks = nullptr, bool build_plan = true, int32_t G = 1, const int64_t *koff = nullptr);
+
+// Bounded-wait self checks: one block of a look-back kernel whose
+// predecessor tile never publishes (sort pass, FA2 moment pass, CSR pass).
+// Each synchronises `s`; the wait's timeout lands in *dev_status.
+size_t wait_check_sort_bytes();
+int wait_check_sort(void *scratch, uint32_t *dev_status, cudaStream_t s);
+size_t wait_check_moments_bytes();
+int wait_check_moments(void *scratch, uint32_t *dev_status, cudaStream_t s);
+size_t wait_check_reduce_bytes();
+int wait_check_reduce(void *scratch, uint32_t *dev_status, cudaStream_t s);
 
 }  // namespace bgv

@@ -22,15 +22,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr unsigned long long kNone = ~0ull;
 
-__global__ void __launch_bounds__(kThreads) k_comm_init(const uint32_t *__restrict__ deg_est, int32_t n,
-                                                        uint2 *__restrict__ state,
-                                                        unsigned long long *__restrict__ best) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        state[v] = make_uint2(deg_est[v], uint32_t(v));
-        best[v] = kNone;
-    }
-}
 
 // The rule of one edge on the round's snapshot: returns the joining node w
 // and the label it is offered, or -1 when the edge moves nothing.
@@ -63,14 +54,15 @@ __device__ __forceinline__ void offer(unsigned long long *best, int32_t w, uint3
     const unsigned long long cand = (static_cast<unsigned long long>(e) << 32) | lab;
     // The slot only decreases, so a stale read can only be larger than the
     // current value: skipping when cand is not below it is always safe.
-    if (cand < best[w]) atomicMin(&best[w], cand);
+    if (cand < __ldcg(&best[w])) atomicMin(&best[w], cand);
 }
 
 __device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, int32_t n, const uint2 *state,
                                              unsigned long long *best, uint32_t D, int tie_mode,
                                              uint32_t *status) {
     if (!endpoints_ok(u, v, n, status)) return;
-    const uint2 su = state[u], sv = state[v];  // (degree, label)
+    // from L2: within the persistent kernel other blocks wrote them
+    const uint2 su = __ldcg(&state[u]), sv = __ldcg(&state[v]);  // (degree, label)
     uint32_t lab;
     const int32_t w = edge_rule(u, v, su.x, su.y, sv.x, sv.y, D, tie_mode, &lab);
     if (w >= 0) offer(best, w, e, lab);
@@ -81,127 +73,115 @@ __device__ __forceinline__ void propose_edge(int32_t u, int32_t v, uint32_t e, i
 __device__ __forceinline__ void propose_edge_b(int32_t u, int32_t v, uint32_t e, int32_t n, const uint4 *state,
                                                unsigned long long *best, int tie_mode, uint32_t *status) {
     if (!endpoints_ok(u, v, n, status)) return;
-    const uint4 su = state[u], sv = state[v];  // (degree, label, threshold, first threshold)
+    const uint4 su = __ldcg(&state[u]), sv = __ldcg(&state[v]);  // (degree, label, threshold, first threshold)
     uint32_t lab;
     const int32_t w = edge_rule(u, v, su.x, su.y, sv.x, sv.y, su.z, tie_mode, &lab);
     if (w >= 0) offer(best, w, e, lab);
 }
 
-__global__ void __launch_bounds__(kThreads) k_comm_init_b(const uint32_t *__restrict__ deg_est, int32_t n,
+
+
+
+
+
+
+
+
+
+// All rounds in one persistent kernel (cooperative launch, every block
+// resident): initial state, then per round the proposals over the edge
+// list, a grid barrier, the winning proposals applied (and the thresholds
+// advanced), a barrier, the pointer-jumping steps (read, barrier, write,
+// barrier), and at the end the labels.  The same per-edge and per-node rules
+// as the kernels above, so the labels are the same bit for bit; the barrier
+// waits are bounded and report BGV_DEV_TIMEOUT.  kB: the batched form (per
+// node (degree, label, threshold, first threshold)).
+template <bool kB>
+__global__ void __launch_bounds__(kThreads) k_comm_rounds(const int32_t *__restrict__ edges, int64_t m, int32_t n,
+                                                          const uint32_t *__restrict__ deg_est,
                                                           const int32_t *__restrict__ node_graph,
-                                                          const uint32_t *__restrict__ D0, uint4 *__restrict__ state,
-                                                          unsigned long long *__restrict__ best) {
+                                                          const uint32_t *__restrict__ D0, int32_t passes,
+                                                          uint32_t threshold, uint32_t growth, int tie_mode,
+                                                          int32_t jumps, uint2 *state, uint4 *bstate,
+                                                          unsigned long long *best, uint32_t *jump,
+                                                          int32_t *__restrict__ labels, uint32_t *__restrict__ deg_out,
+                                                          uint32_t *status, WsHeader *hdr, int spin_limit) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint32_t d0 = D0[node_graph[v]];
-        state[v] = make_uint4(deg_est[v], uint32_t(v), d0, d0);
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t v = t0; v < n; v += stride) {
+        if (kB) {
+            const uint32_t d0 = D0[node_graph[v]];
+            bstate[v] = make_uint4(deg_est[v], uint32_t(v), d0, d0);
+        } else {
+            state[v] = make_uint2(deg_est[v], uint32_t(v));
+        }
         best[v] = kNone;
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_comm_propose_b(const int32_t *__restrict__ edges, int64_t m, int32_t n,
-                                                             const uint4 *__restrict__ state,
-                                                             unsigned long long *best, int tie_mode,
-                                                             uint32_t *status) {
+    if (!grid_barrier(&hdr->bar, spin_limit, status)) return;
     const int4 *e2 = reinterpret_cast<const int4 *>(edges);
     const int64_t pairs = m >> 1;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
-        const int4 e = __ldcs(e2 + p);
-        propose_edge_b(e.x, e.y, uint32_t(2 * p), n, state, best, tie_mode, status);
-        propose_edge_b(e.z, e.w, uint32_t(2 * p + 1), n, state, best, tie_mode, status);
-    }
-    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-        propose_edge_b(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, state, best, tie_mode, status);
-}
-
-// Applies the winning proposals and moves every node's threshold to the
-// next round's (times growth, or times its graph's first threshold when
-// growth is 0; saturating at 2^32 - 1).
-__global__ void __launch_bounds__(kThreads) k_comm_apply_b(int32_t n, uint4 *__restrict__ state,
-                                                           unsigned long long *__restrict__ best, uint32_t growth) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const unsigned long long b = best[v];
-        uint4 s = state[v];
-        if (b != kNone) {
-            s.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
-            if (s.x != 0xFFFFFFFFu) s.x += 1;
-            best[v] = kNone;
+    unsigned long long D = threshold;
+    const unsigned long long factor = growth ? growth : threshold;
+    for (int32_t p = 0; p < passes; ++p) {
+        for (int64_t q = t0; q < pairs; q += stride) {
+            const int4 e = __ldcs(e2 + q);
+            if (kB) {
+                propose_edge_b(e.x, e.y, uint32_t(2 * q), n, bstate, best, tie_mode, status);
+                propose_edge_b(e.z, e.w, uint32_t(2 * q + 1), n, bstate, best, tie_mode, status);
+            } else {
+                propose_edge(e.x, e.y, uint32_t(2 * q), n, state, best, uint32_t(D), tie_mode, status);
+                propose_edge(e.z, e.w, uint32_t(2 * q + 1), n, state, best, uint32_t(D), tie_mode, status);
+            }
         }
-        const unsigned long long D = static_cast<unsigned long long>(s.z) * (growth ? growth : s.w);
-        s.z = D > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(D);
-        state[v] = s;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_comm_out_b(int32_t n, const uint4 *__restrict__ state,
-                                                         int32_t *__restrict__ labels, uint32_t *__restrict__ deg_out) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint4 s = state[v];
-        labels[v] = int32_t(s.y);
-        if (deg_out) deg_out[v] = s.x;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_comm_propose(const int32_t *__restrict__ edges, int64_t m, int32_t n,
-                                                           const uint2 *__restrict__ state,
-                                                           unsigned long long *best, uint32_t D, int tie_mode,
-                                                           uint32_t *status) {
-    const int4 *e2 = reinterpret_cast<const int4 *>(edges);
-    const int64_t pairs = m >> 1;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
-        const int4 e = __ldcs(e2 + p);
-        propose_edge(e.x, e.y, uint32_t(2 * p), n, state, best, D, tie_mode, status);
-        propose_edge(e.z, e.w, uint32_t(2 * p + 1), n, state, best, D, tie_mode, status);
-    }
-    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-        propose_edge(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, state, best, D, tie_mode,
-                     status);
-}
-
-__global__ void __launch_bounds__(kThreads) k_comm_apply(int32_t n, uint2 *__restrict__ state,
-                                                         unsigned long long *__restrict__ best) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const unsigned long long b = best[v];
-        if (b != kNone) {
-            uint2 s = state[v];
-            s.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
-            if (s.x != 0xFFFFFFFFu) s.x += 1;
-            state[v] = s;
-            best[v] = kNone;
+        if ((m & 1) && t0 == 0) {
+            if (kB)
+                propose_edge_b(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, bstate, best, tie_mode,
+                               status);
+            else
+                propose_edge(edges[2 * (m - 1)], edges[2 * (m - 1) + 1], uint32_t(m - 1), n, state, best, uint32_t(D),
+                             tie_mode, status);
         }
+        if (!grid_barrier(&hdr->bar, spin_limit, status)) return;
+        for (int64_t v = t0; v < n; v += stride) {
+            const unsigned long long b = __ldcg(&best[v]);
+            if (kB) {
+                uint4 st = bstate[v];
+                if (b != kNone) {
+                    st.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
+                    if (st.x != 0xFFFFFFFFu) st.x += 1;
+                    best[v] = kNone;
+                }
+                const unsigned long long nd = static_cast<unsigned long long>(st.z) * (growth ? growth : st.w);
+                st.z = nd > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(nd);
+                bstate[v] = st;
+            } else if (b != kNone) {
+                uint2 st = state[v];
+                st.y = static_cast<uint32_t>(b & 0xFFFFFFFFull);
+                if (st.x != 0xFFFFFFFFu) st.x += 1;
+                state[v] = st;
+                best[v] = kNone;
+            }
+        }
+        if (!grid_barrier(&hdr->bar, spin_limit, status)) return;
+        for (int32_t j = 0; j < jumps; ++j) {
+            for (int64_t v = t0; v < n; v += stride)
+                jump[v] = kB ? __ldcg(&bstate[__ldcg(&bstate[v].y)].y) : __ldcg(&state[__ldcg(&state[v].y)].y);
+            if (!grid_barrier(&hdr->bar, spin_limit, status)) return;
+            for (int64_t v = t0; v < n; v += stride) {
+                if (kB) bstate[v].y = __ldcg(&jump[v]);
+                else state[v].y = __ldcg(&jump[v]);
+            }
+            if (!grid_barrier(&hdr->bar, spin_limit, status)) return;
+        }
+        D *= factor;
+        if (D > 0xFFFFFFFFull) D = 0xFFFFFFFFull;
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_comm_out(int32_t n, const uint2 *__restrict__ state,
-                                                       int32_t *__restrict__ labels, uint32_t *__restrict__ deg_out) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const uint2 s = state[v];
-        labels[v] = int32_t(s.y);
-        if (deg_out) deg_out[v] = s.x;
+    for (int64_t v = t0; v < n; v += stride) {
+        const uint32_t d = kB ? __ldcg(&bstate[v].x) : __ldcg(&state[v].x);
+        const uint32_t l = kB ? __ldcg(&bstate[v].y) : __ldcg(&state[v].y);
+        labels[v] = int32_t(l);
+        if (deg_out) deg_out[v] = d;
     }
-}
-
-// Pointer jumping (one synchronous step): every label becomes its label's
-// label, read from the state before the step.
-template <class S>
-__global__ void __launch_bounds__(kThreads) k_comm_jump_read(int32_t n, const S *__restrict__ state,
-                                                             uint32_t *__restrict__ next) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride)
-        next[v] = state[state[v].y].y;
-}
-
-template <class S>
-__global__ void __launch_bounds__(kThreads) k_comm_jump_write(int32_t n, S *__restrict__ state,
-                                                              const uint32_t *__restrict__ next) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) state[v].y = next[v];
 }
 
 // Mode degree (Section 4.2.2): the keys (graph << 32 | degree) are sorted;
@@ -257,7 +237,7 @@ void carve_mode(Carver &c, int32_t n, int32_t G, ModeScratch &s) {
 int run_mode_degree(const uint32_t *deg, int32_t n, const BatchView *batch, uint32_t *mode_dev,
                     const ModeScratch &s, uint32_t *status, cudaStream_t st) {
     const int32_t G = batch ? batch->G : 1;
-    const int gn = grid_for(n, kThreads, 152 * 8);
+    const int gn = grid_for(n, kThreads, sm_count() * 8);
     BGV_CUDA(cudaMemsetAsync(s.best, 0, sizeof(unsigned long long) * size_t(G), st));
     note_launch(), k_mode_keys<<<gn, kThreads, 0, st>>>(deg, n, batch ? batch->node_graph : nullptr,
                                                         s.sort.keys[0]);
@@ -266,59 +246,27 @@ int run_mode_degree(const uint32_t *deg, int32_t n, const BatchView *batch, uint
     int res = 0;
     BGV_TRY(radix_sort(sb, n, nullptr, 32 + (batch ? bits_for(G) : 0), st, &res, status));
     note_launch(), k_mode_runs<<<gn, kThreads, 0, st>>>(sb.keys[res], n, s.best);
-    note_launch(), k_mode_out<<<grid_for(G, kThreads, 152), kThreads, 0, st>>>(s.best, G, mode_dev);
+    note_launch(), k_mode_out<<<grid_for(G, kThreads, sm_count()), kThreads, 0, st>>>(s.best, G, mode_dev);
     return launch_status();
 }
 
 int run_communities(const int32_t *edges, int64_t m, int32_t n, const uint32_t *deg_est, int32_t passes,
                     uint32_t threshold, uint32_t growth, int32_t tie_mode, int32_t jumps, int32_t *labels,
                     uint32_t *deg_out, const CommScratch &s, uint32_t *status, cudaStream_t st,
-                    const BatchView *batch) {
-    const int gn = grid_for(n, kThreads, 152 * 8);
-    if (batch) {
-        const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
-        note_launch(), k_comm_init_b<<<gn, kThreads, 0, st>>>(deg_est, n, batch->node_graph, batch->D0, s.bstate,
-                                                              s.best);
-        BGV_TRY(launch_status());
-        for (int32_t p = 0; p < passes; ++p) {
-            if (m > 0) {
-                note_launch(), k_comm_propose_b<<<ge, kThreads, 0, st>>>(edges, m, n, s.bstate, s.best, tie_mode,
-                                                                         status);
-                BGV_TRY(launch_status());
-            }
-            note_launch(), k_comm_apply_b<<<gn, kThreads, 0, st>>>(n, s.bstate, s.best, growth);
-            BGV_TRY(launch_status());
-            for (int32_t j = 0; j < jumps; ++j) {
-                note_launch(), k_comm_jump_read<<<gn, kThreads, 0, st>>>(n, s.bstate, s.jump);
-                note_launch(), k_comm_jump_write<<<gn, kThreads, 0, st>>>(n, s.bstate, s.jump);
-                BGV_TRY(launch_status());
-            }
-        }
-        note_launch(), k_comm_out_b<<<gn, kThreads, 0, st>>>(n, s.bstate, labels, deg_out);
-        return launch_status();
-    }
-    note_launch(), k_comm_init<<<gn, kThreads, 0, st>>>(deg_est, n, s.state, s.best);
-    BGV_TRY(launch_status());
-    unsigned long long D = threshold;
-    const unsigned long long factor = growth ? growth : threshold;
-    const int ge = grid_for((m + 1) / 2, kThreads, 152 * 8);
-    for (int32_t p = 0; p < passes; ++p) {
-        if (m > 0) {
-            note_launch(), k_comm_propose<<<ge, kThreads, 0, st>>>(edges, m, n, s.state, s.best, uint32_t(D), tie_mode, status);
-            BGV_TRY(launch_status());
-        }
-        note_launch(), k_comm_apply<<<gn, kThreads, 0, st>>>(n, s.state, s.best);
-        BGV_TRY(launch_status());
-        for (int32_t j = 0; j < jumps; ++j) {
-            note_launch(), k_comm_jump_read<<<gn, kThreads, 0, st>>>(n, s.state, s.jump);
-            note_launch(), k_comm_jump_write<<<gn, kThreads, 0, st>>>(n, s.state, s.jump);
-            BGV_TRY(launch_status());
-        }
-        D *= factor;
-        if (D > 0xFFFFFFFFull) D = 0xFFFFFFFFull;
-    }
-    note_launch(), k_comm_out<<<gn, kThreads, 0, st>>>(n, s.state, labels, deg_out);
-    return launch_status();
+                    const BatchView *batch, WsHeader *hdr) {
+    const int32_t *node_graph = batch ? batch->node_graph : nullptr;
+    const uint32_t *D0 = batch ? batch->D0 : nullptr;
+    uint2 *state = s.state;
+    uint4 *bstate = s.bstate;
+    unsigned long long *best = s.best;
+    uint32_t *jump = s.jump;
+    int tmode = tie_mode, limit = spin_limit();
+    void *args[] = {&edges, &m, &n, &deg_est, &node_graph, &D0, &passes, &threshold, &growth, &tmode, &jumps,
+                    &state, &bstate, &best, &jump, &labels, &deg_out, &status, &hdr, &limit};
+    const void *kernel = batch ? reinterpret_cast<const void *>(k_comm_rounds<true>)
+                               : reinterpret_cast<const void *>(k_comm_rounds<false>);
+    const int blocks = coop_blocks(kernel, kThreads, sm_count() * 8);
+    return launch_coop(kernel, blocks, kThreads, args, st);
 }
 
 }  // namespace bgv

@@ -27,23 +27,29 @@
 //               row, row pieces kept per range; k_long_rows sums the rows
 //               spread over many ranges.  Both run on a second stream while
 //               the tree is built and walked.
-//   k_node      per node: attraction pieces in range order, gravity, total
-//               force, swing and traction (FP64 sums in a fixed order); the
-//               last block adds the block sums and updates the global speed
-//   k_update    local speed, displacement, Fprev = F
+//   k_tail      one persistent kernel (cooperative launch, bounded grid
+//               barriers): per node gravity, total force, swing and
+//               traction, summed exactly (integer accumulation); the global
+//               speed (per graph in the batched form); per node the local
+//               speed, the displacement and Fprev = F
+//   (k_node gives the forces alone, without a step)
 //
 // The opening test and the centre it uses are computed with explicit
 // round-to-nearest FP32 operations (no contraction) from the exact integer
 // moments, so the decisions do not depend on thread scheduling and equal
 // the oracle's decisions on the same positions.
+#include <atomic>
+
 #include "bgv_internal.cuh"
 
 namespace bgv {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kFrameBlocks = 304;      // 2 x 152 SMs
-constexpr int kNodeBlocks = 152 * 4;  // node-kernel grid (rows are grid-strided; measured best)
+constexpr int kMaxFrameBlocks = 1024;  // frame-kernel grid: 2 blocks per SM, at most this many
+constexpr int kMaxNodeBlocks = 2048;   // node-kernel grid: 4 blocks per SM (measured best), at most this many
+inline int frame_blocks() { return sm_count() * 2 < kMaxFrameBlocks ? sm_count() * 2 : kMaxFrameBlocks; }
+inline int node_blocks() { return sm_count() * 4 < kMaxNodeBlocks ? sm_count() * 4 : kMaxNodeBlocks; }
 
 typedef unsigned __int128 u128;
 
@@ -322,7 +328,6 @@ struct MomTile {
     unsigned long long M, xl, xh, yl, yh, pad;
 };
 enum : uint32_t { kMomAgg = 1u, kMomIncl = 2u };  // look-back flags (0: nothing published)
-constexpr int kMomSpinLimit = 1 << 22;
 constexpr int kMomLBItems = 4;                          // predecessors per thread and round
 constexpr int kMomLookBack = kThreads * kMomLBItems;    // predecessors per round
 
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
     const uint32_t *__restrict__ perm, int64_t K, const float2 *__restrict__ pos, const uint32_t *__restrict__ mass,
     const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
     MomP *__restrict__ P, uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
-    MomTile *incl, uint32_t *dev_status) {
+    MomTile *incl, uint32_t *dev_status, int spin_limit) {
     __shared__ uint4 stage[2 * (kMomTile + kMomTile / 8)];  // bodies, then two halves per prefix record
     __shared__ unsigned tile_sh;
     __shared__ int near_sh;
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
                 pending |= idx >= lo && f[r] == 0u;
             }
             if (__syncthreads_or(pending)) {
-                if (++spins > kMomSpinLimit) {
+                if (++spins > spin_limit) {
                     if (threadIdx.x == 0) raise_status(dev_status, BGV_DEV_TIMEOUT);
                     break;
                 }
@@ -526,16 +531,16 @@ __device__ __forceinline__ int node_level(int delta, int kb, int L, int gbits) {
 // opening test (+inf for a leaf that is never accepted); cells are counted
 // per first body, and their levels recorded there, for the pre-order
 // layout.
-__global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__restrict__ keys, int64_t K, int L,
-                                                   int gbits, int leaf_cap, const float4 *__restrict__ frames,
-                                                   const int32_t *__restrict__ bgraph,
-                                                   const MomP *__restrict__ P, int2 *__restrict__ range,
-                                                   int8_t *__restrict__ cell_level, float4 *__restrict__ cell,
-                                                   uint32_t *__restrict__ start_count,
-                                                   uint32_t *__restrict__ start_levels,
-                                                   unsigned long long *tree_nodes) {
+// A binary node can only be a quadtree cell if the split inside its range
+// lies at a deeper 2-bit level than the split just outside it; both follow
+// from the keys of the node and its two neighbours.  The test runs over all
+// nodes (three coalesced key loads each) and lists the candidates, one
+// atomic per block; the range searches then run densely over the list.
+__global__ void __launch_bounds__(kThreads) k_tree_mark(const unsigned long long *__restrict__ keys, int64_t K,
+                                                        int L, int gbits, int8_t *__restrict__ cell_level,
+                                                        uint32_t *__restrict__ cand, uint32_t *cand_count) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool top = false;
+    bool is_cand = false;
     if (i < K - 1) {
         const int kb = 2 * L + gbits;
         const unsigned long long ki = __ldg(&keys[i]);
@@ -545,50 +550,99 @@ __global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__r
         // The node's split lies between its parent's (dmin) and that of the
         // pair (i, i + d) inside its range: when those two share a level,
         // the node shares it with its parent and is no cell.
-        const bool may_be_cell =
-            node_level(d > 0 ? dnext : dprev, kb, L, gbits) != node_level(dmin, kb, L, gbits);
-        if (!may_be_cell) cell_level[i] = -1;
-        if (may_be_cell) {
-            int64_t lmax = 2;
-            while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
-            int64_t l = 0;
-            for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-                if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
-            const int64_t j = i + l * d;
-            const int dnode = key_delta(keys, K, kb, i, ki, j);
-            const int64_t first = i < j ? i : j, last = i < j ? j : i;
-            const int lev = node_level(dnode, kb, L, gbits);
-            const int par_lev = node_level(dmin, kb, L, gbits);
-            top = par_lev < lev;
-            cell_level[i] = static_cast<int8_t>(top ? lev : -1);
-            if (top) {
-                range[i] = make_int2(int32_t(first), int32_t(last));
-                const int cnt = int(last - first) + 1;
-                const bool leaf = cnt <= leaf_cap || lev >= L;
-                // A leaf made by the depth limit (coincident keys, more than
-                // leaf_cap bodies) hides a chain of non-leaf cells with the same
-                // bodies between its parent's level and L; the deepest of them,
-                // at level L - 1, takes the opening test for the whole chain.
-                const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
-                // positions of graph g in Morton order are its index range too
-                const float4 fr = frames[bgraph ? bgraph[first] : 0];
-                const Mom hi = momp_load(P, last + 1), lo = momp_load(P, first);
-                const unsigned long long M = hi.M - lo.M;
-                const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
-                const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
-                const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
-                const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), two_m32)));
-                const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), two_m32)));
-                const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
-                const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
-                cell[i] = make_float4(cx, cy, __ull2float_rn(M), side2);
-                atomicAdd(&start_count[first], 1u);
-                atomicOr(&start_levels[first], 1u << lev);
-            }
+        is_cand = node_level(d > 0 ? dnext : dprev, kb, L, gbits) != node_level(dmin, kb, L, gbits);
+        if (!is_cand) cell_level[i] = -1;
+    }
+    // block-wide compaction: one atomic per block on the shared counter
+    __shared__ uint32_t warp_n[kThreads / 32], block_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, is_cand);
+    if (lane == 0) warp_n[warp] = uint32_t(__popc(mask));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const uint32_t c = warp_n[w];
+            warp_n[w] = t;
+            t += c;
+        }
+        block_base = t ? atomicAdd(cand_count, t) : 0u;
+    }
+    __syncthreads();
+    if (is_cand) cand[block_base + warp_n[warp] + __popc(mask & ((1u << lane) - 1u))] = uint32_t(i);
+}
+
+// Binary radix tree and quadtree cells, one thread per listed candidate
+// (Karras, HPG 2012): the node's range and split prefix length come from an
+// exponential and a binary search on key prefixes.  Its parent's split is
+// the nearer of the two pairs just outside the range (the far one shares a
+// shorter prefix), so the node knows its parent's level without waiting for
+// anyone.  A node is a quadtree cell when its level exceeds its parent's (a
+// chain of single-child cells collapses into its deepest cell, which takes
+// the opening test for the whole chain).  For each cell: FP32 centre from
+// the exact moments, mass, and the squared side used by the opening test
+// (+inf for a leaf that is never accepted); cells are counted per first
+// body, and their levels recorded there, for the pre-order layout.
+__global__ void __launch_bounds__(kThreads) k_tree(const unsigned long long *__restrict__ keys, int64_t K, int L,
+                                                   int gbits, int leaf_cap, const float4 *__restrict__ frames,
+                                                   const int32_t *__restrict__ bgraph,
+                                                   const MomP *__restrict__ P, int2 *__restrict__ range,
+                                                   int8_t *__restrict__ cell_level, float4 *__restrict__ cell,
+                                                   uint32_t *__restrict__ start_count,
+                                                   uint32_t *__restrict__ start_levels,
+                                                   unsigned long long *tree_nodes, const uint32_t *__restrict__ cand,
+                                                   const uint32_t *cand_count) {
+    const int64_t count = *cand_count;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int kb = 2 * L + gbits;
+    uint32_t tops = 0;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const int64_t i = cand[q];
+        const unsigned long long ki = __ldg(&keys[i]);
+        const int dnext = key_delta(keys, K, kb, i, ki, i + 1), dprev = key_delta(keys, K, kb, i, ki, i - 1);
+        const int d = dnext > dprev ? 1 : -1;
+        const int dmin = d > 0 ? dprev : dnext;
+        int64_t lmax = 2;
+        while (key_delta(keys, K, kb, i, ki, i + lmax * d) > dmin) lmax <<= 1;
+        int64_t l = 0;
+        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+            if (key_delta(keys, K, kb, i, ki, i + (l + t) * d) > dmin) l += t;
+        const int64_t j = i + l * d;
+        const int dnode = key_delta(keys, K, kb, i, ki, j);
+        const int64_t first = i < j ? i : j, last = i < j ? j : i;
+        const int lev = node_level(dnode, kb, L, gbits);
+        const int par_lev = node_level(dmin, kb, L, gbits);
+        const bool top = par_lev < lev;
+        cell_level[i] = static_cast<int8_t>(top ? lev : -1);
+        if (top) {
+            ++tops;
+            range[i] = make_int2(int32_t(first), int32_t(last));
+            const int cnt = int(last - first) + 1;
+            const bool leaf = cnt <= leaf_cap || lev >= L;
+            // A leaf made by the depth limit (coincident keys, more than
+            // leaf_cap bodies) hides a chain of non-leaf cells with the same
+            // bodies between its parent's level and L; the deepest of them,
+            // at level L - 1, takes the opening test for the whole chain.
+            const bool testable = leaf && cnt > leaf_cap && par_lev + 1 <= L - 1;
+            // positions of graph g in Morton order are its index range too
+            const float4 fr = frames[bgraph ? bgraph[first] : 0];
+            const Mom hi = momp_load(P, last + 1), lo = momp_load(P, first);
+            const unsigned long long M = hi.M - lo.M;
+            const u128 X = hi.X - lo.X, Y = hi.Y - lo.Y;
+            const uint32_t qx = M ? uint32_t(X / M) : 0u, qy = M ? uint32_t(Y / M) : 0u;
+            const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+            const float cx = __fadd_rn(fr.x, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qx), two_m32)));
+            const float cy = __fadd_rn(fr.y, __fmul_rn(fr.z, __fmul_rn(__uint2float_rn(qy), two_m32)));
+            const float sl = __fmul_rn(fr.z, pow2_neg(testable ? L - 1 : lev));
+            const float side2 = (leaf && !testable) ? INFINITY : __fmul_rn(sl, sl);
+            cell[i] = make_float4(cx, cy, __ull2float_rn(M), side2);
+            atomicAdd(&start_count[first], 1u);
+            atomicOr(&start_levels[first], 1u << lev);
         }
     }
-    const unsigned mask = __ballot_sync(0xFFFFFFFFu, top);
-    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(tree_nodes, static_cast<unsigned long long>(__popc(mask)));
+#pragma unroll
+    for (int dd = 16; dd > 0; dd >>= 1) tops += __shfl_xor_sync(0xFFFFFFFFu, tops, dd);
+    if ((threadIdx.x & 31) == 0 && tops) atomicAdd(tree_nodes, static_cast<unsigned long long>(tops));
 }
 
 // Pre-order layout of cells and bodies.  With T[s] = number of cells whose
@@ -636,7 +690,8 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t K, const int2 *__
 // other cell is accepted by the FP32 opening test of the definition.  Each
 // body sees exactly its own interaction set in depth-first order; threads of
 // a warp are Morton neighbours, so they mostly read the same elements.
-__global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
+template <int kRT>
+__global__ void __launch_bounds__(kRT) k_repulse(const float4 *__restrict__ geo, const int32_t *__restrict__ skip,
                                                       const uint32_t *__restrict__ T,
                                                       const int64_t *__restrict__ koff,
                                                       const int32_t *__restrict__ bgraph,
@@ -684,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
 }
 
 // ------------------------------------------------------------ attraction
-// The CSR entries are cut into fixed ranges of kRange consecutive entries,
+// The CSR entries are cut into fixed ranges of `range` consecutive entries,
 // one warp per range whatever the row lengths (a hub row spreads over many
 // warps, short rows share one).  The warp takes its range kStep entries at a
 // time, 4 consecutive entries per lane: 16-byte loads of the neighbours and
@@ -696,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) k_repulse(const float4 *__restrict__
 // piece of a row that began before it to head[range].  k_node adds a row's
 // pieces in range order, so every sum has a fixed order.
 constexpr int kChunk = 8;     // entries per plan record
-constexpr int kRange = 512;   // entries per warp range
+constexpr int kRangeMin = 256;   // entries per warp range: 256, 512 or 1024 (process-wide, tuned)
 constexpr int kLaneEntries = 4;                 // consecutive entries per lane and step
 constexpr int kStep = 32 * kLaneEntries;
 
@@ -712,7 +767,8 @@ constexpr int kStep = 32 * kLaneEntries;
 constexpr int kLongRowRanges = 8;
 constexpr unsigned kMetaWalk = 4u;
 
-__global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, int range,
+                                                         const int32_t *__restrict__ off,
                                                          int32_t *__restrict__ chunk_row, int32_t *__restrict__ long_rows,
                                                          int32_t *long_count) {
     const int lane = threadIdx.x & 31;
@@ -725,7 +781,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz,
             const int64_t b = off[r], e = off[r + 1] < nnz ? off[r + 1] : nnz;
             g0 = (b + kChunk - 1) / kChunk;
             g1 = (e + kChunk - 1) / kChunk;
-            spread = e > b && (e - 1) / kRange - b / kRange > kLongRowRanges;
+            spread = e > b && (e - 1) / range - b / range > kLongRowRanges;
         }
         if (spread) long_rows[atomicAdd(long_count, 1)] = int32_t(r);
         const bool longrow = g1 - g0 > 32;
@@ -834,7 +890,7 @@ __device__ __forceinline__ void load_lane(int64_t b, int64_t e1, int lane, int64
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, int range, const int32_t *__restrict__ off,
                                                       const int32_t *__restrict__ chunk_row,
                                                       const unsigned long long *__restrict__ chunk_meta,
                                                       const int32_t *__restrict__ adj,
@@ -842,11 +898,11 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
                                                       float2 *__restrict__ full, float2 *__restrict__ head,
                                                       float2 *__restrict__ tail) {
     const int lane = threadIdx.x & 31;
-    const int64_t ranges = (nnz + kRange - 1) / kRange;
+    const int64_t ranges = (nnz + range - 1) / range;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const bool vec = ((reinterpret_cast<uintptr_t>(adj) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
     for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < ranges; q += warps) {
-        const int64_t e0 = q * kRange, e1 = e0 + kRange < nnz ? e0 + kRange : nnz;
+        const int64_t e0 = q * range, e1 = e0 + range < nnz ? e0 + range : nnz;
         const int32_t row_first = entry_row(e0, K, off, chunk_row, chunk_meta);
         const int32_t row_last = entry_row(e1 - 1, K, off, chunk_row, chunk_meta);
         const bool began = off[row_first] < e0;
@@ -958,7 +1014,7 @@ __global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, co
 // full[].
 constexpr int kLongThreads = 128;
 
-__global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kLongThreads) k_long_rows(int range, const int32_t *__restrict__ off,
                                                             const int32_t *__restrict__ long_rows,
                                                             const int32_t *__restrict__ long_count,
                                                             const float2 *__restrict__ head,
@@ -969,7 +1025,7 @@ __global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__res
     const int64_t count = *long_count;
     for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int32_t r = long_rows[q];
-        const int64_t a = off[r] / kRange, z = (off[r + 1] - 1) / kRange;
+        const int64_t a = off[r] / range, z = (off[r + 1] - 1) / range;
         float px = 0.0f, py = 0.0f;
         for (int64_t g = a + 1 + threadIdx.x; g <= z; g += kLongThreads) {
             const float2 v = head[g];
@@ -996,232 +1052,295 @@ __global__ void __launch_bounds__(kLongThreads) k_long_rows(const int32_t *__res
 }
 
 // --------------------------------------------- node forces, swing, speed
-// Neumaier-compensated FP64 accumulation (the batched form's per-graph
-// sums); merging two partial sums keeps both compensations.  Used in a fixed
-// order, so results are reproducible.
-struct Comp {
-    double s, c;
+// Global swing and traction (the sums that set the adaptive speed):
+// S = sum m_i swing_i and T = sum m_i traction_i over FP32 per-node products,
+// which are non-negative.  They are summed EXACTLY: each product f * 2^q
+// (f its 24-bit significand) is added as a fixed-point integer into a
+// 128-bit accumulator V whose unit 2^q0 sits kXHead binary places below the
+// largest term seen so far (q0 moves up, with V shifted down, when a larger
+// term arrives).  A term below the unit loses only its bits under 2^q0, less
+// than 2^-95 of the largest term, so the accumulated value equals the exact
+// sum to about 2^-64 relative even over 2^31 terms; integer addition does not
+// depend on the order of the merges.  The total is rounded once to FP64, so S
+// and T are the correctly rounded sums of the products (Kahan or Neumaier
+// compensation in FP64 would leave about two units in the last place, and
+// FP64 arithmetic runs at a small fraction of the integer rate on this GPU).
+constexpr int kXHead = 72;          // each term < 2^(24 + 72): 2^31 terms fit in 127 bits
+constexpr int kXNoAnchor = -100000; // anchor of an empty accumulator
+struct XSum {
+    u128 V;
+    int q0;
+    int bad;  // 1: an infinite term, 2: a NaN term
 };
-__device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
-    const double t = a.s + b.s;
-    const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
-    return Comp{t, a.c + b.c + e};
-}
-__device__ __forceinline__ Comp comp_shfl_down(Comp a, int d) {
-    return Comp{__shfl_down_sync(0xFFFFFFFFu, a.s, d), __shfl_down_sync(0xFFFFFFFFu, a.c, d)};
+__device__ __forceinline__ XSum xsum_zero() { return XSum{0, kXNoAnchor, 0}; }
+
+__device__ __forceinline__ void xsum_add(XSum &a, float x) {
+    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;  // terms are >= 0 (a -0 adds nothing)
+    const int e = int(b >> 23);
+    if (e == 255) {
+        a.bad |= (b & 0x7FFFFFu) ? 2 : 1;
+        return;
+    }
+    const uint32_t f = e ? ((b & 0x7FFFFFu) | 0x800000u) : b;
+    const int q = (e ? e : 1) - 150;  // x = f * 2^q
+    if (f == 0u) return;
+    if (q - kXHead > a.q0) {  // a new largest term: move the anchor up
+        const int d = q - kXHead - a.q0;
+        a.V = d >= 128 ? u128(0) : (a.V >> d);
+        a.q0 = q - kXHead;
+    }
+    const int sh = q - a.q0;  // <= kXHead
+    if (sh >= 0)
+        a.V += u128(f) << sh;
+    else if (sh > -24)
+        a.V += u128(f >> -sh);
 }
 
-// Block-wide merge of one (S, T) pair per thread, in a fixed tree; thread 0
+__device__ __forceinline__ XSum xsum_merge(XSum a, XSum b) {
+    if (b.q0 > a.q0) {
+        const XSum t = a;
+        a = b;
+        b = t;
+    }
+    const int d = a.q0 - b.q0;
+    if (d < 128) a.V += b.V >> d;
+    a.bad |= b.bad;
+    return a;
+}
+
+__device__ __forceinline__ XSum xsum_shfl_down(const XSum &a, int d) {
+    XSum r;
+    r.V = (u128(__shfl_down_sync(0xFFFFFFFFu, static_cast<unsigned long long>(a.V >> 64), d)) << 64) |
+          __shfl_down_sync(0xFFFFFFFFu, static_cast<unsigned long long>(a.V), d);
+    r.q0 = __shfl_down_sync(0xFFFFFFFFu, a.q0, d);
+    r.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, d);
+    return r;
+}
+
+// The accumulated value rounded once to FP64 (round to nearest even): the top
+// 64 bits of V, with a sticky bit for the rest, converted, then scaled.
+__device__ __forceinline__ double xsum_value(const XSum &a) {
+    if (a.bad) return (a.bad & 2) ? __longlong_as_double(0x7FF8000000000000ll) : __longlong_as_double(0x7FF0000000000000ll);
+    const unsigned long long hi = static_cast<unsigned long long>(a.V >> 64);
+    if (!hi) return ldexp(__ull2double_rn(static_cast<unsigned long long>(a.V)), a.q0);
+    const int sh = 64 - __clzll(static_cast<long long>(hi));  // bits of V above its top 64
+    unsigned long long t = static_cast<unsigned long long>(a.V >> sh);
+    if (a.V & ((u128(1) << sh) - 1)) t |= 1ull;  // sticky: far below the rounding position
+    return ldexp(__ull2double_rn(t), a.q0 + sh);
+}
+
+// Stored form of one accumulator (per-block partials).
+struct XPart {
+    unsigned long long lo, hi;
+    int q0, bad;
+};
+__device__ __forceinline__ XPart xsum_pack(const XSum &a) {
+    return XPart{static_cast<unsigned long long>(a.V), static_cast<unsigned long long>(a.V >> 64), a.q0, a.bad};
+}
+__device__ __forceinline__ XSum xsum_unpack(const XPart *p) {  // from L2: written by other blocks
+    const unsigned long long lo = __ldcg(&p->lo), hi = __ldcg(&p->hi);
+    return XSum{(u128(hi) << 64) | lo, __ldcg(&p->q0), __ldcg(&p->bad)};
+}
+
+// Block-wide merge of one (S, T) pair per thread in a fixed tree; thread 0
 // receives the result.
-__device__ __forceinline__ void block_merge(Comp &S, Comp &T) {
-    __shared__ Comp sS[kThreads / 32], sT[kThreads / 32];
+__device__ __forceinline__ void xsum_block(XSum &S, XSum &T) {
+    __shared__ XPart sS[kThreads / 32], sT[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        const Comp oS = comp_shfl_down(S, d), oT = comp_shfl_down(T, d);
-        S = comp_merge(S, oS);
-        T = comp_merge(T, oT);
+        const XSum oS = xsum_shfl_down(S, d), oT = xsum_shfl_down(T, d);
+        S = xsum_merge(S, oS);
+        T = xsum_merge(T, oT);
     }
     if (lane == 0) {
-        sS[warp] = S;
-        sT[warp] = T;
+        sS[warp] = xsum_pack(S);
+        sT[warp] = xsum_pack(T);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < kThreads / 32; ++k) {
-            S = comp_merge(S, sS[k]);
-            T = comp_merge(T, sT[k]);
+            S = xsum_merge(S, XSum{(u128(sS[k].hi) << 64) | sS[k].lo, sS[k].q0, sS[k].bad});
+            T = xsum_merge(T, XSum{(u128(sT[k].hi) << 64) | sT[k].lo, sT[k].q0, sT[k].bad});
         }
     }
     __syncthreads();
 }
 
-// Block sum of one (S, T) pair per thread in plain FP64 (fixed tree);
-// thread 0 receives it.  Compensation is applied where the block sums meet.
-__device__ __forceinline__ void block_sum_plain(double &S, double &T) {
-    __shared__ double sS[kThreads / 32], sT[kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        S += __shfl_down_sync(0xFFFFFFFFu, S, d);
-        T += __shfl_down_sync(0xFFFFFFFFu, T, d);
+__device__ __forceinline__ double speed_update(double sp, double Ssum, double Tsum, float tau) {
+    if (Ssum > 0.0) {
+        const double target = double(tau) * Tsum / Ssum;
+        const double rise = target - sp, cap = 0.5 * sp;
+        sp += rise < cap ? rise : cap;
     }
-    if (lane == 0) {
-        sS[warp] = S;
-        sT[warp] = T;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < kThreads / 32; ++k) {
-            S += sS[k];
-            T += sT[k];
-        }
-    }
-    __syncthreads();
+    return sp;
 }
 
-__global__ void __launch_bounds__(kThreads) k_node(int mode, int64_t K, const int32_t *__restrict__ off,
-                                                   const float2 *__restrict__ full, const float2 *__restrict__ head,
-                                                   const float2 *__restrict__ tail,
+// Per-node swing and traction products, FP32 with every rounding explicit
+// (no contraction), so they can be recomputed bit for bit from F, Fprev and
+// the mass: m |F - Fprev| and (m / 2) |F + Fprev|.
+__device__ __forceinline__ float2 swing_traction(float m, float fx, float fy, float px, float py) {
+    const float sx = __fsub_rn(fx, px), sy = __fsub_rn(fy, py), tx = __fadd_rn(fx, px), ty = __fadd_rn(fy, py);
+    const float sw = sqrtf(__fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy)));
+    const float tr = sqrtf(__fadd_rn(__fmul_rn(tx, tx), __fmul_rn(ty, ty)));
+    return make_float2(__fmul_rn(m, sw), __fmul_rn(__fmul_rn(0.5f, m), tr));
+}
+
+// The step's tail in one persistent kernel (all blocks resident at once,
+// cooperative launch): per node the total force and the swing and traction
+// products; a grid barrier; the global speed (every block merges the block
+// partials in block order, so all blocks hold the same value; batched: one
+// block per graph sums that graph's rows, then a second barrier); then per
+// node the local speed and the displacement, Fprev = F.  The barrier waits
+// are bounded and report BGV_DEV_TIMEOUT.
+// The attraction of row i from the pieces k_attract / k_long_rows left:
+// rows over many ranges (or inside one) in full[], the others as the tail
+// piece of their first range plus the head pieces of the next ones, added in
+// range order.  off == nullptr: no CSR entries, no attraction.
+struct AttPieces {
+    const int32_t *off;
+    const float2 *full, *head, *tail;
+    int range;
+};
+__device__ __forceinline__ float2 attraction_of(int64_t i, const AttPieces &a) {
+    if (!a.off) return make_float2(0.0f, 0.0f);
+    const int64_t b = a.off[i], e = a.off[i + 1];
+    if (e <= b) return make_float2(0.0f, 0.0f);
+    const int64_t g1 = b / a.range, g2 = (e - 1) / a.range;
+    if (g1 == g2 || g2 - g1 > kLongRowRanges) return a.full[i];
+    float2 v = a.tail[g1];
+    for (int64_t g = g1 + 1; g <= g2; ++g) {
+        const float2 h = a.head[g];
+        v.x += h.x;
+        v.y += h.y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ float2 node_force(int64_t i, const AttPieces &att, float m, float2 pi, float2 fr, float kg,
+                                             int strong) {
+    const float2 fa = attraction_of(i, att);
+    float gx, gy;
+    if (strong) {
+        gx = -kg * m * pi.x;
+        gy = -kg * m * pi.y;
+    } else {
+        const float rr = sqrtf(pi.x * pi.x + pi.y * pi.y);
+        gx = rr > 0.0f ? -kg * m * pi.x / rr : 0.0f;
+        gy = rr > 0.0f ? -kg * m * pi.y / rr : 0.0f;
+    }
+    return make_float2(fr.x + fa.x + gx, fr.y + fa.y + gy);
+}
+
+__device__ __forceinline__ float2 displaced(float2 p, float2 f, float2 fp, float sp, float ks, float ksmax) {
+    const float sx = f.x - fp.x, sy = f.y - fp.y;
+    const float swing = sqrtf(sx * sx + sy * sy);
+    float s = ks * sp / (1.0f + sp * sqrtf(swing));
+    const float fn = sqrtf(f.x * f.x + f.y * f.y);
+    if (fn > 0.0f && s * fn > ksmax) s = ksmax / fn;
+    p.x += s * f.x;
+    p.y += s * f.y;
+    return p;
+}
+
+// Forces only (no state change): repulsion, attraction and gravity per node.
+__global__ void __launch_bounds__(kThreads) k_node(int64_t K, const AttPieces att,
                                                    const uint32_t *__restrict__ mass, const float2 *__restrict__ pos,
                                                    const float2 *__restrict__ Frep, float kg, int strong,
-                                                   float2 *__restrict__ F, const float2 *__restrict__ Fprev,
                                                    float2 *__restrict__ Fr_out, float2 *__restrict__ Fa_out,
-                                                   float2 *__restrict__ Fg_out, double2 *part, double *speed,
-                                                   float tau, WsHeader *hdr, float2 *__restrict__ rowst) {
-    Comp S{0.0, 0.0}, T{0.0, 0.0};
-    const int lane = threadIdx.x & 31;
+                                                   float2 *__restrict__ Fg_out) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); base < K; base += stride) {
-        const int64_t i = base + lane;
-        const bool valid = i < K;
-        int64_t g1 = 0, g2 = -1;
-        float ax = 0.0f, ay = 0.0f;
-        // independent per-node loads first, so they overlap the piece sums
-        float2 pi = make_float2(0.f, 0.f), fr = pi, fp = pi;
-        uint32_t mi = 0;
-        if (valid) {
-            const int64_t b = off[i], e = off[i + 1];
-            pi = pos[i];
-            mi = mass[i];
-            fr = Frep[i];
-            if (mode != 0) fp = Fprev[i];
-            if (e > b) {
-                g1 = b / kRange;
-                g2 = (e - 1) / kRange;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const float m = __uint2float_rn(mass[i]);
+        const float2 pi = pos[i];
+        if (Fr_out) Fr_out[i] = Frep[i];
+        if (Fa_out) Fa_out[i] = attraction_of(i, att);
+        if (Fg_out) {
+            const AttPieces none = {nullptr, nullptr, nullptr, nullptr, 0};
+            Fg_out[i] = node_force(i, none, m, pi, make_float2(0.0f, 0.0f), kg, strong);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const AttPieces att,
+                                                   const uint32_t *__restrict__ mass, float2 *__restrict__ pos,
+                                                   const float2 *__restrict__ Frep, float kg, int strong,
+                                                   float2 *__restrict__ F, float2 *__restrict__ Fprev, XPart *part,
+                                                   double *speed, float tau, float ks, float ksmax, WsHeader *hdr,
+                                                   float2 *__restrict__ rowst, const int64_t *__restrict__ koff,
+                                                   const int32_t *__restrict__ bgraph, int32_t G, int spin_limit) {
+    __shared__ double sp_sh;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool batched = rowst != nullptr;
+    const double sp_old = batched ? 0.0 : *speed;  // read by every block before anyone writes it
+    XSum S = xsum_zero(), T = xsum_zero();
+    for (int64_t i = t0; i < K; i += stride) {
+        const float m = __uint2float_rn(mass[i]);
+        const float2 f = node_force(i, att, m, pos[i], Frep[i], kg, strong);
+        F[i] = f;
+        const float2 fp = Fprev[i];
+        const float2 st = swing_traction(m, f.x, f.y, fp.x, fp.y);
+        if (batched) {
+            rowst[i] = st;
+        } else {
+            xsum_add(S, st.x);
+            xsum_add(T, st.y);
+        }
+    }
+    if (!batched) {
+        xsum_block(S, T);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = xsum_pack(S);
+            part[2 * blockIdx.x + 1] = xsum_pack(T);
+        }
+        if (!grid_barrier(&hdr->bar, spin_limit, &hdr->status)) return;
+        S = xsum_zero();
+        T = xsum_zero();
+        for (unsigned bk = threadIdx.x; bk < gridDim.x; bk += blockDim.x) {
+            S = xsum_merge(S, xsum_unpack(&part[2 * bk]));
+            T = xsum_merge(T, xsum_unpack(&part[2 * bk + 1]));
+        }
+        xsum_block(S, T);
+        if (threadIdx.x == 0) {
+            const double Ssum = xsum_value(S), Tsum = xsum_value(T);
+            sp_sh = speed_update(sp_old, Ssum, Tsum, tau);
+            if (blockIdx.x == 0) {
+                *speed = sp_sh;
+                hdr->S = Ssum;
+                hdr->T = Tsum;
+                hdr->steps_total += 1;
             }
         }
-        // rows over many ranges were summed by k_long_rows into full[]
-        if (valid && g2 >= g1) {
-            if (g1 == g2 || g2 - g1 > kLongRowRanges) {
-                const float2 v = full[i];
-                ax = v.x;
-                ay = v.y;
-            } else {
-                float2 v = tail[g1];
-                ax = v.x;
-                ay = v.y;
-                for (int64_t g = g1 + 1; g <= g2; ++g) {
-                    v = head[g];
-                    ax += v.x;
-                    ay += v.y;
+        __syncthreads();
+    } else {
+        if (!grid_barrier(&hdr->bar, spin_limit, &hdr->status)) return;
+        for (int32_t g = blockIdx.x; g < G; g += gridDim.x) {  // one block per graph
+            const int64_t a = koff[g], b = koff[g + 1];
+            XSum Sg = xsum_zero(), Tg = xsum_zero();
+            for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+                const float2 v = __ldcg(&rowst[i]);
+                xsum_add(Sg, v.x);
+                xsum_add(Tg, v.y);
+            }
+            xsum_block(Sg, Tg);
+            if (threadIdx.x == 0) {
+                const double Ssum = xsum_value(Sg), Tsum = xsum_value(Tg);
+                speed[g] = speed_update(speed[g], Ssum, Tsum, tau);
+                if (g == 0) {
+                    hdr->S = Ssum;
+                    hdr->T = Tsum;
+                    hdr->steps_total += 1;
                 }
             }
         }
-        if (!valid) continue;
-        const float m = __uint2float_rn(mi);
-        float gx, gy;
-        if (strong) {
-            gx = -kg * m * pi.x;
-            gy = -kg * m * pi.y;
-        } else {
-            const float rr = sqrtf(pi.x * pi.x + pi.y * pi.y);
-            gx = rr > 0.0f ? -kg * m * pi.x / rr : 0.0f;
-            gy = rr > 0.0f ? -kg * m * pi.y / rr : 0.0f;
-        }
-        if (mode == 0) {
-            if (Fr_out) Fr_out[i] = fr;
-            if (Fa_out) Fa_out[i] = make_float2(ax, ay);
-            if (Fg_out) Fg_out[i] = make_float2(gx, gy);
-        } else {
-            const float fx = fr.x + ax + gx, fy = fr.y + ay + gy;
-            F[i] = make_float2(fx, fy);
-            const float sx = fx - fp.x, sy = fy - fp.y, tx = fx + fp.x, ty = fy + fp.y;
-            // per-node products in FP32; the sums over nodes are FP64
-            const float msw = m * sqrtf(sx * sx + sy * sy), mtr = 0.5f * m * sqrtf(tx * tx + ty * ty);
-            if (rowst) {
-                rowst[i] = make_float2(msw, mtr);  // batched: summed per graph
-            } else {
-                S.s += double(msw);
-                T.s += double(mtr);
-            }
-        }
+        if (!grid_barrier(&hdr->bar, spin_limit, &hdr->status)) return;
     }
-    if (mode == 0 || rowst) return;
-    __shared__ bool last;
-    block_sum_plain(S.s, T.s);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = make_double2(S.s, T.s);
-        __threadfence();
-        last = atomicAdd(&hdr->node_ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // The last block adds the block partials: each thread a strided subset
-    // in block order, then the fixed block tree (plain FP64: a few hundred
-    // terms, each already a block's sum).
-    double aS = 0.0, aT = 0.0;
-    for (unsigned bk = threadIdx.x; bk < gridDim.x; bk += blockDim.x) {
-        const double2 v = __ldcg(&part[bk]);
-        aS += v.x;
-        aT += v.y;
-    }
-    block_sum_plain(aS, aT);
-    if (threadIdx.x != 0) return;
-    const double Ssum = aS, Tsum = aT;
-    double sp = *speed;
-    if (Ssum > 0.0) {
-        const double target = double(tau) * Tsum / Ssum;
-        const double rise = target - sp, cap = 0.5 * sp;
-        sp += rise < cap ? rise : cap;
-    }
-    *speed = sp;
-    hdr->S = Ssum;
-    hdr->T = Tsum;
-    hdr->steps_total += 1;
-    hdr->node_ticket = 0u;
-}
-
-// Batched form: one block per graph sums its rows' swing and traction (FP64
-// in a fixed order, compensated across threads) and updates that graph's
-// speed.
-__global__ void __launch_bounds__(kThreads) k_speed_seg(const float2 *__restrict__ rowst,
-                                                        const int64_t *__restrict__ koff, double *speed, float tau,
-                                                        WsHeader *hdr) {
-    const int g = blockIdx.x;
-    const int64_t a = koff[g], b = koff[g + 1];
-    // plain FP64 per thread, compensated where the threads' sums meet
-    double s = 0.0, t = 0.0;
-    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
-        const float2 v = rowst[i];
-        s += double(v.x);
-        t += double(v.y);
-    }
-    Comp S{s, 0.0}, T{t, 0.0};
-    block_merge(S, T);
-    if (threadIdx.x != 0) return;
-    const double Ssum = S.s + S.c, Tsum = T.s + T.c;
-    double sp = speed[g];
-    if (Ssum > 0.0) {
-        const double target = double(tau) * Tsum / Ssum;
-        const double rise = target - sp, cap = 0.5 * sp;
-        sp += rise < cap ? rise : cap;
-    }
-    speed[g] = sp;
-    if (g == 0) {
-        hdr->S = Ssum;
-        hdr->T = Tsum;
-        hdr->steps_total += 1;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_update(int64_t K, const float2 *__restrict__ F, float2 *__restrict__ Fprev,
-                                                     float2 *__restrict__ pos, const double *__restrict__ speed,
-                                                     const int32_t *__restrict__ bgraph, float ks, float ksmax) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
-        const float sp = float(speed[bgraph ? bgraph[i] : 0]);
+    const float sp_all = float(sp_sh);
+    for (int64_t i = t0; i < K; i += stride) {
+        const float sp = batched ? float(__ldcg(&speed[bgraph[i]])) : sp_all;
         const float2 f = F[i], fp = Fprev[i];
-        const float sx = f.x - fp.x, sy = f.y - fp.y;
-        const float swing = sqrtf(sx * sx + sy * sy);
-        float s = ks * sp / (1.0f + sp * sqrtf(swing));
-        const float fn = sqrtf(f.x * f.x + f.y * f.y);
-        if (fn > 0.0f && s * fn > ksmax) s = ksmax / fn;
-        float2 p = pos[i];
-        p.x += s * f.x;
-        p.y += s * f.y;
-        pos[i] = p;
+        pos[i] = displaced(pos[i], f, fp, sp, ks, ksmax);
         Fprev[i] = f;
     }
 }
@@ -1290,7 +1409,8 @@ struct Fa2Scratch {
     int2 *range;           // per binary node that is a cell: its bodies
     int8_t *cell_level;    // per binary node: its level if a cell, else -1
     MomP *P;               // moment prefix sums, K + 1 records
-    uint32_t *mom_flags;   // look-back flags per tile, then the tile counter
+    uint32_t *mom_flags;   // look-back flags per tile, the tile counter, the tree candidate count
+    uint32_t *cand;        // binary nodes that may be quadtree cells
     MomTile *mom_agg, *mom_incl;
     float4 *cell;          // per binary node: centre, mass, side^2 (cells only)
     uint32_t *start_count; // cells per first body
@@ -1305,16 +1425,16 @@ struct Fa2Scratch {
     unsigned long long *chunk_meta;  // plan: rows of the chunk's entries, flags
     int32_t *long_rows;   // plan: rows over more than kLongRowRanges ranges
     int32_t *long_count;
-    double2 *part;  // per block: (S, T)
+    XPart *part;  // per node-kernel block: exact S and T partials
 };
 
 static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
     const size_t k = size_t(K > 0 ? K : 1);
     const size_t chunks = size_t((nnz > 0 ? nnz : 1) + kChunk - 1) / kChunk;
-    const size_t ranges = size_t((nnz > 0 ? nnz : 1) + kRange - 1) / kRange;
+    const size_t ranges = size_t((nnz > 0 ? nnz : 1) + kRangeMin - 1) / kRangeMin;
     const bool batched = G > 1;
     s.frame = c.take<float4>(size_t(G > 1 ? G : 1));
-    s.frame_part = c.take<float4>(kFrameBlocks);
+    s.frame_part = c.take<float4>(kMaxFrameBlocks);
     s.bgraph = batched ? c.take<int32_t>(k) : nullptr;
     s.rowst = batched ? c.take<float2>(k) : nullptr;
     carve_sort(c, int64_t(k), true, s.sort);
@@ -1324,10 +1444,11 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.range = c.take<int2>(k);
     s.cell_level = c.take<int8_t>(k);
     s.P = c.take<MomP>(k + 1);
-    s.mom_flags = c.take<uint32_t>(tiles + 1);
+    s.mom_flags = c.take<uint32_t>(tiles + 2);  // look-back flags, tile counter, tree candidate count
     s.mom_agg = c.take<MomTile>(tiles);
     s.mom_incl = c.take<MomTile>(tiles);
     s.cell = c.take<float4>(k);
+    s.cand = c.take<uint32_t>(k);
     s.start_count = c.take<uint32_t>(k + 1);
     s.start_levels = c.take<uint32_t>(k);
     s.T = c.take<uint32_t>(k + 1);
@@ -1342,7 +1463,7 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.chunk_meta = c.take<unsigned long long>(chunks);
     s.long_rows = c.take<int32_t>(ranges / kLongRowRanges + 1);
     s.long_count = c.take<int32_t>(1);
-    s.part = c.take<double2>(kNodeBlocks);
+    s.part = c.take<XPart>(2 * size_t(kMaxNodeBlocks));
 }
 
 size_t fa2_scratch_bytes(int64_t K, int64_t nnz, int32_t G) {
@@ -1371,12 +1492,82 @@ int run_fa2_init(int64_t K, const bgv_fa2_params &p, float *pos, float *Fprev, d
     }
     if (K > 0) {
         const float R = __builtin_sqrtf(float(K));
-        note_launch(), k_init<<<grid_for(K, kThreads, 152 * 8), kThreads, 0, st>>>(
+        note_launch(), k_init<<<grid_for(K, kThreads, sm_count() * 8), kThreads, 0, st>>>(
             K, p.seed, R, reinterpret_cast<float2 *>(pos), reinterpret_cast<float2 *>(Fprev));
         BGV_TRY(launch_status());
     }
     note_launch(), k_set_speed<<<1, 1, 0, st>>>(speed);
     return launch_status();
+}
+
+// Bounded-wait self check of the moment pass: one block as tile 1 of two
+// tiles of bodies (all at the origin, body 0 everywhere, mass 0, frame side
+// 1) whose tile 0 never runs, so its look-back must give up at the spin
+// limit.  Writes stay within the two tiles' bodies and prefix records.
+namespace {
+struct WaitCheckMoments {
+    uint32_t *perm, *mass, *start_count, *start_levels, *flags;
+    float2 *pos;
+    float4 *frame, *body;
+    MomP *P;
+    MomTile *agg, *incl;
+};
+void carve_wait_check_moments(Carver &c, WaitCheckMoments &w) {
+    const size_t K = 2 * kMomTile;
+    w.perm = c.take<uint32_t>(K);
+    w.mass = c.take<uint32_t>(K);
+    w.start_count = c.take<uint32_t>(K);
+    w.start_levels = c.take<uint32_t>(K);
+    w.flags = c.take<uint32_t>(3);
+    w.pos = c.take<float2>(K);
+    w.frame = c.take<float4>(1);
+    w.body = c.take<float4>(K);
+    w.P = c.take<MomP>(K + 1);
+    w.agg = c.take<MomTile>(2);
+    w.incl = c.take<MomTile>(2);
+}
+}  // namespace
+
+size_t wait_check_moments_bytes() {
+    Carver c(nullptr, 0);
+    WaitCheckMoments w;
+    carve_wait_check_moments(c, w);
+    return c.used();
+}
+
+int wait_check_moments(void *scratch, uint32_t *dev_status, cudaStream_t st) {
+    Carver c(scratch, 0);
+    WaitCheckMoments w;
+    carve_wait_check_moments(c, w);
+    BGV_CUDA(cudaMemsetAsync(scratch, 0, wait_check_moments_bytes(), st));
+    const float4 frame = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    const uint32_t one = 1u;  // the tile counter (after the two tiles' flags)
+    BGV_CUDA(cudaMemcpyAsync(w.frame, &frame, sizeof(frame), cudaMemcpyHostToDevice, st));
+    BGV_CUDA(cudaMemcpyAsync(w.flags + 2, &one, sizeof(one), cudaMemcpyHostToDevice, st));
+    note_launch(), k_gather_moments<<<1, kThreads, 0, st>>>(w.perm, 2 * kMomTile, w.pos, w.mass, w.frame, nullptr,
+                                                            w.body, w.P, w.start_count, w.start_levels, w.flags,
+                                                            w.agg, w.incl, dev_status, spin_limit());
+    BGV_TRY(launch_status());
+    return cudaStreamSynchronize(st) == cudaSuccess ? BGV_OK : BGV_ECUDA;
+}
+
+// Launch shapes of the step, process wide (bgv_autotune_fa2 picks them):
+// CSR entries per attraction warp range, threads per block of the
+// traversal, blocks per SM of the persistent tail.  Packed in one word so a
+// step reads a consistent set.
+static std::atomic<uint32_t> g_fa2_tune{(512u << 16) | (256u << 4) | 4u};
+Fa2Tune fa2_tune() {
+    const uint32_t w = g_fa2_tune.load(std::memory_order_relaxed);
+    return Fa2Tune{int(w >> 16), int((w >> 4) & 0xFFFu), int(w & 0xFu)};
+}
+int set_fa2_tune(const Fa2Tune &t) {
+    if ((t.att_range != 256 && t.att_range != 512 && t.att_range != 1024) ||
+        (t.repulse_threads != 128 && t.repulse_threads != 256) || t.tail_blocks_per_sm < 1 ||
+        t.tail_blocks_per_sm > 8)
+        return BGV_EINVAL;
+    g_fa2_tune.store((uint32_t(t.att_range) << 16) | (uint32_t(t.repulse_threads) << 4) | uint32_t(t.tail_blocks_per_sm),
+                     std::memory_order_relaxed);
+    return BGV_OK;
 }
 
 // A second stream per host thread and device, made on first use.
@@ -1435,6 +1626,7 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
     float2 *Fprev = reinterpret_cast<float2 *>(Fprev_f);
     const int L = p.max_depth;
     const int gbits = batched ? bits_for(G) : 0;
+    const Fa2Tune tune = fa2_tune();
     auto mark = [&](int i) -> int {
         if (marks && cudaEventRecord(marks[i], st) != cudaSuccess) return BGV_ECUDA;
         return BGV_OK;
@@ -1450,59 +1642,80 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         aux = aux_stream();
         if (!aux || ev.make() != cudaSuccess) return BGV_ECUDA;
     }
+    // Once the second stream is forked, every way out of this function joins
+    // it back into `st` (so `st` stays ordered after the attraction, and a
+    // capture never ends with an unjoined fork).
+    struct JoinGuard {
+        cudaEvent_t ev = nullptr;
+        cudaStream_t from = nullptr, into = nullptr;
+        int join() {
+            if (!ev) return BGV_OK;
+            const cudaError_t a = cudaEventRecord(ev, from);
+            const cudaError_t b = cudaStreamWaitEvent(into, ev, 0);
+            ev = nullptr;
+            return a == cudaSuccess && b == cudaSuccess ? BGV_OK : BGV_ECUDA;
+        }
+        ~JoinGuard() { join(); }
+    } guard;
     // The attraction needs only the positions and the CSR: it runs on a
     // second stream while the tree is built and traversed, and k_node waits
     // for it.
     if (nnz > 0) {
         BGV_CUDA(cudaEventRecord(ev.fork, st));
         BGV_CUDA(cudaStreamWaitEvent(aux, ev.fork, 0));
+        guard.ev = ev.join;
+        guard.from = aux;
+        guard.into = st;
         if (build_plan) {
             BGV_CUDA(cudaMemsetAsync(s.long_count, 0, sizeof(int32_t), aux));
-            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, 152 * 16), kThreads, 0, aux>>>(
-                K, nnz, csr_off, s.chunk_row, s.long_rows, s.long_count);
+            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, sm_count() * 16), kThreads, 0, aux>>>(
+                K, nnz, tune.att_range, csr_off, s.chunk_row, s.long_rows, s.long_count);
             BGV_TRY(launch_status());
-            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, 152 * 16), kThreads, 0,
+            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, sm_count() * 16), kThreads, 0,
                                           aux>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
             BGV_TRY(launch_status());
         }
-        const int64_t nranges = (nnz + kRange - 1) / kRange;
+        const int64_t nranges = (nnz + tune.att_range - 1) / tune.att_range;
         note_launch(), k_attract<<<grid_for(nranges * 32, kThreads, (nranges * 32 + kThreads - 1) / kThreads), kThreads,
-                                   0, aux>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta, csr_adj, csr_w, pos, s.full,
-                                         s.head, s.tail);
+                                   0, aux>>>(K, nnz, tune.att_range, csr_off, s.chunk_row, s.chunk_meta, csr_adj,
+                                             csr_w, pos, s.full, s.head, s.tail);
         BGV_TRY(launch_status());
-        note_launch(), k_long_rows<<<152 * 16, kLongThreads, 0, aux>>>(csr_off, s.long_rows, s.long_count, s.head,
-                                                                       s.tail, s.full);
+        note_launch(), k_long_rows<<<sm_count() * 16, kLongThreads, 0, aux>>>(tune.att_range, csr_off, s.long_rows,
+                                                                              s.long_count, s.head, s.tail, s.full);
         BGV_TRY(launch_status());
-        BGV_CUDA(cudaEventRecord(ev.join, aux));
     }
     if (batched)
         note_launch(), k_frame_seg<<<G, kThreads, 0, st>>>(pos, koff, s.frame, s.bgraph);
     else
-        note_launch(), k_frame<<<kFrameBlocks, kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
+        note_launch(), k_frame<<<frame_blocks(), kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
-    const int gk = grid_for(K, kThreads, 152 * 16);
+    const int gk = grid_for(K, kThreads, sm_count() * 16);
     const int64_t mom_tiles = (K + kMomTile - 1) / kMomTile;
     note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
-                                                   &hdr->interactions, s.mom_flags, mom_tiles + 1, s.sort.counts,
+                                                   &hdr->interactions, s.mom_flags, mom_tiles + 2, s.sort.counts,
                                                    sort_counter_words());
     BGV_TRY(launch_status());
     BGV_TRY(mark(1));
     int res = 0;
-    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, 2 * L + gbits, st, &res, &hdr->status, true));
+    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, nullptr, 2 * L + gbits, st, &res, &hdr->status, true));
     BGV_TRY(mark(2));
     {
         note_launch(), k_gather_moments<<<unsigned(mom_tiles), kThreads, 0, st>>>(
             s.sort.vals[res], K, pos, mass, s.frame, s.bgraph, s.body, s.P, s.start_count,
-            s.start_levels, s.mom_flags, s.mom_agg, s.mom_incl, &hdr->status);
+            s.start_levels, s.mom_flags, s.mom_agg, s.mom_incl, &hdr->status, spin_limit());
         BGV_TRY(launch_status());
     }
     BGV_TRY(mark(3));
     if (K >= 2) {
         const unsigned gt = unsigned((K + kThreads - 1) / kThreads);
         const unsigned gi = unsigned((K - 1 + kThreads - 1) / kThreads);
-        note_launch(), k_tree<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph,
-                                                       s.P, s.range, s.cell_level, s.cell,
-                                                       s.start_count, s.start_levels, &hdr->tree_nodes);
+        uint32_t *cand_count = s.mom_flags + mom_tiles + 1;  // cleared by k_keys
+        note_launch(), k_tree_mark<<<gi, kThreads, 0, st>>>(s.sort.keys[res], K, L, gbits, s.cell_level, s.cand,
+                                                            cand_count);
+        BGV_TRY(launch_status());
+        note_launch(), k_tree<<<grid_for(K, kThreads, sm_count() * 8), kThreads, 0, st>>>(
+            s.sort.keys[res], K, L, gbits, p.leaf_cap, s.frame, s.bgraph, s.P, s.range, s.cell_level, s.cell,
+            s.start_count, s.start_levels, &hdr->tree_nodes, s.cand, cand_count);
         BGV_TRY(launch_status());
         BGV_TRY(mark(4));
         BGV_TRY(scan_exclusive(s.start_count, s.T, K, nullptr, nullptr, true, s.scan_tmp, st));
@@ -1511,10 +1724,17 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         BGV_TRY(launch_status());
         BGV_TRY(mark(5));
         const float theta2 = p.theta * p.theta;
-        const unsigned gr = unsigned((K + kThreads - 1) / kThreads);
-        note_launch(), k_repulse<<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, koff, s.bgraph, s.body, K, p.kr,
-                                                          theta2, s.Frep, &hdr->interactions,
-                                                          &hdr->interactions_total);
+        if (tune.repulse_threads == 128) {
+            const unsigned gr = unsigned((K + 127) / 128);
+            note_launch(), k_repulse<128><<<gr, 128, 0, st>>>(s.geo, s.skip, s.T, koff, s.bgraph, s.body, K, p.kr,
+                                                              theta2, s.Frep, &hdr->interactions,
+                                                              &hdr->interactions_total);
+        } else {
+            const unsigned gr = unsigned((K + kThreads - 1) / kThreads);
+            note_launch(), k_repulse<kThreads><<<gr, kThreads, 0, st>>>(s.geo, s.skip, s.T, koff, s.bgraph, s.body, K,
+                                                                        p.kr, theta2, s.Frep, &hdr->interactions,
+                                                                        &hdr->interactions_total);
+        }
         BGV_TRY(launch_status());
     } else {
         BGV_CUDA(cudaMemsetAsync(s.Frep, 0, sizeof(float2), st));
@@ -1522,22 +1742,29 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         BGV_TRY(mark(5));
     }
     BGV_TRY(mark(6));
-    if (nnz > 0) {  // the attraction ran alongside on the second stream
-        BGV_CUDA(cudaStreamWaitEvent(st, ev.join, 0));
-    }
-    note_launch(), k_node<<<grid_for(K, kThreads, kNodeBlocks), kThreads, 0, st>>>(
-        mode, K, csr_off, s.full, s.head, s.tail, mass, pos, s.Frep, p.kg, p.strong_gravity, F, Fprev,
-        reinterpret_cast<float2 *>(Fr), reinterpret_cast<float2 *>(Fa), reinterpret_cast<float2 *>(Fg), s.part, speed,
-        p.tau, hdr, (batched && mode == 1) ? s.rowst : nullptr);
-    BGV_TRY(launch_status());
-    if (batched && mode == 1) {
-        note_launch(), k_speed_seg<<<G, kThreads, 0, st>>>(s.rowst, koff, speed, p.tau, hdr);
-        BGV_TRY(launch_status());
-    }
+    BGV_TRY(guard.join());  // the attraction ran alongside on the second stream
     BGV_TRY(mark(7));
-    if (mode == 1) {
-        note_launch(), k_update<<<gk, kThreads, 0, st>>>(K, F, Fprev, pos, speed, s.bgraph, p.ks, p.ksmax);
+    AttPieces att = {nnz > 0 ? csr_off : nullptr, s.full, s.head, s.tail, tune.att_range};
+    if (mode == 0) {
+        note_launch(), k_node<<<grid_for(K, kThreads, node_blocks()), kThreads, 0, st>>>(
+            K, att, mass, pos, s.Frep, p.kg, p.strong_gravity, reinterpret_cast<float2 *>(Fr),
+            reinterpret_cast<float2 *>(Fa), reinterpret_cast<float2 *>(Fg));
         BGV_TRY(launch_status());
+    } else {
+        float2 *rowst = batched ? s.rowst : nullptr;
+        const int64_t *koff_d = batched ? koff : nullptr;
+        const int32_t *bgraph = s.bgraph;
+        int32_t g_count = G;
+        float kg = p.kg, tau = p.tau, ks = p.ks, ksmax = p.ksmax;
+        int strong = p.strong_gravity, limit = spin_limit();
+        int64_t k_count = K;
+        XPart *part = s.part;
+        const float2 *frep = s.Frep;
+        void *args[] = {&k_count, &att, &mass, &pos, &frep, &kg, &strong, &F, &Fprev, &part, &speed, &tau, &ks,
+                        &ksmax, &hdr, &rowst, &koff_d, &bgraph, &g_count, &limit};
+        const int blocks = coop_blocks(reinterpret_cast<const void *>(k_tail), kThreads,
+                                       sm_count() * tune.tail_blocks_per_sm);
+        BGV_TRY(launch_coop(reinterpret_cast<const void *>(k_tail), blocks, kThreads, args, st));
     }
     BGV_TRY(mark(8));
     return BGV_OK;

@@ -17,6 +17,49 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
 
+// Bound on the polling rounds of every decoupled look-back wait (process
+// wide; the default ends a wait that cannot finish after a few seconds).
+static std::atomic<int> g_spin_limit{1 << 22};
+int spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
+int set_spin_limit(int limit) { return g_spin_limit.exchange(limit, std::memory_order_relaxed); }
+
+int coop_blocks(const void *kernel, int threads, int want) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) per_sm = 1;
+    const int most = (per_sm > 0 ? per_sm : 1) * sm_count();
+    const int b = want < most ? want : most;
+    return b > 0 ? b : 1;
+}
+
+int launch_coop(const void *kernel, int blocks, int threads, void **args, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(blocks));
+    cfg.blockDim = dim3(unsigned(threads));
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelExC(&cfg, kernel, args) == cudaSuccess ? BGV_OK : BGV_ECUDA;
+}
+
+int sm_count() {
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cached[kMaxDevices];  // 0: not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDevices) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    if (dev < kMaxDevices) cached[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 // ------------------------------------------------------------------- scan
 namespace {
 constexpr int kScanThreads = 256;
@@ -183,11 +226,12 @@ int scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n_cap, const int64
 namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-// Keys per thread: 8 up to a cutoff, 16 above it.  The cutoff starts at
-// 2^22 keys (a million keys then make ~480 tiles, enough blocks for 152
-// SMs) and bgv_autotune_sort can set it from measurements on this GPU.
+// Keys per thread: 8 up to a cutoff, 16 above it.  Measured on GB300 with
+// 48-bit keys and values, 8 was faster at every size from 2^14 to 2^26
+// keys (4.4 against 11.7 ms at 2^26), so the cutoff starts above any
+// count; bgv_autotune_sort can set it from measurements on the GPU at hand.
 constexpr int kSortItemsBig = 16, kSortItemsSmall = 8;
-std::atomic<int64_t> g_small_sort_cutoff{int64_t(1) << 22};
+std::atomic<int64_t> g_small_sort_cutoff{int64_t(1) << 40};
 inline int sort_items(int64_t cap) {
     return cap <= g_small_sort_cutoff.load(std::memory_order_relaxed) ? kSortItemsSmall : kSortItemsBig;
 }
@@ -203,7 +247,6 @@ constexpr int kMaxPasses = 8;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFlagMask = 3ull << 62;
 constexpr unsigned long long kCountMask = (1ull << 40) - 1;
 constexpr int kTagShift = 40;
-constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookBack = 4;       // predecessors read per look-back round (16 keys per thread)
 constexpr int kLookBackWide = 16;  // the same with 8 keys per thread (keys staged first)
 
@@ -250,7 +293,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(const unsigned long
 // count and returns the exclusive one.
 template <int kW>
 __device__ __forceinline__ unsigned long long look_back(volatile unsigned long long *st, int64_t tile, int d,
-                                                        unsigned long long tag, uint32_t total, uint32_t *dev_status) {
+                                                        unsigned long long tag, uint32_t total, uint32_t *dev_status,
+                                                        int spin_limit) {
     if (tile == 0) return 0ull;
     unsigned long long excl = 0;
     int64_t j = tile - 1;
@@ -273,7 +317,7 @@ __device__ __forceinline__ unsigned long long look_back(volatile unsigned long l
         if (done) break;
         j -= q;
         if (q < kW) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 raise_status(dev_status, BGV_DEV_TIMEOUT);
                 break;
             }
@@ -298,8 +342,10 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
                                                                 const uint32_t *__restrict__ pass_counts,
                                                                 unsigned int *tile_counter,
                                                                 unsigned long long *status, uint32_t *dev_status,
-                                                                unsigned long long tag) {
-    constexpr bool kStage = kItems <= 8;
+                                                                unsigned long long tag, int spin_limit) {
+    // keys go through shared memory (coalesced digit runs on the way out)
+    // with 8 keys per thread, and with 16 when there are no values (42 KB)
+    constexpr bool kStage = kItems <= 8 || !kVals;
     constexpr int kTileKeys = kSortThreads * kItems;
     __shared__ uint32_t cnt[kSortWarps][kBins];
     __shared__ uint32_t tile_base[kBins];
@@ -387,7 +433,7 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
         }
     }
     tile_base[d] = digit_start + uint32_t(look_back<kStage ? kLookBackWide : kLookBack>(st, tile, d, tag, total,
-                                                                                         dev_status));
+                                                                                         dev_status, spin_limit));
     __syncthreads();
     if constexpr (kStage) {
         const int64_t t0 = tile * kTileKeys;
@@ -413,6 +459,178 @@ __global__ void __launch_bounds__(kSortThreads, kItems <= 8 ? 4 : 2) k_sort_ones
 }
 }  // namespace
 
+// ------------------------------------------------- cooperative radix sort
+// All LSD passes in one persistent kernel (cooperative launch: every block
+// resident), with no look-back.  Block b owns a contiguous chunk of tiles of
+// 2,048 keys.  Per pass on the 8-bit digit at `shift`:
+//   A  the block counts the digits of its chunk (shared-memory atomics);
+//   -  grid barrier;
+//   B  blocks 0..255 take one digit each and scan its counts over the chunks
+//      (exclusive, in block order) and total them;
+//   -  grid barrier;
+//   C  the block turns the 256 totals into digit starts, then takes its
+//      tiles in order: ranks each tile's keys stably (per-warp digit
+//      counters in (item, lane) order, as in the onesweep pass), stages them
+//      in shared memory in digit order and writes every digit's run at the
+//      digit start + the chunk's prefix + what its earlier tiles wrote;
+//   -  grid barrier before the next pass reads the output.
+// Chunks in block order and tiles in order keep the passes stable.  The
+// barrier waits are bounded (BGV_DEV_TIMEOUT).
+template <bool kVals>
+__global__ void __launch_bounds__(kSortThreads, kVals ? 3 : 4) k_sort_coop(unsigned long long *k0, unsigned long long *k1,
+                                                                 uint32_t *v0, uint32_t *v1, int64_t cap,
+                                                                 const int64_t *d_count, int first_pass, int passes,
+                                                                 uint32_t *chunk_hist, uint32_t *chunk_pre,
+                                                                 uint32_t *totals, GridBar *bar, uint32_t *dev_status,
+                                                                 int spin_limit) {
+    constexpr int kItems = kSortItemsSmall;
+    constexpr int kTileKeys = kSortThreads * kItems;
+    __shared__ uint32_t cnt[kSortWarps][kBins];
+    __shared__ uint32_t run[kBins];
+    __shared__ uint32_t local_start[kBins];
+    __shared__ unsigned long long skey[kTileKeys];
+    __shared__ uint32_t sval[kVals ? kTileKeys : 1];
+    const int64_t n = load_count(d_count, cap);
+    const int64_t T = (n + kTileKeys - 1) / kTileKeys;
+    const int64_t per = (T + gridDim.x - 1) / gridDim.x;
+    const int64_t t_lo = int64_t(blockIdx.x) * per < T ? int64_t(blockIdx.x) * per : T;
+    const int64_t t_hi = t_lo + per < T ? t_lo + per : T;
+    const int64_t i_hi = t_hi * kTileKeys < n ? t_hi * kTileKeys : n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int d = threadIdx.x;  // the digit this thread owns in per-digit steps
+    for (int p = first_pass; p < passes; ++p) {
+        const int shift = 8 * p;
+        const bool odd = ((p - first_pass) & 1) != 0;
+        const unsigned long long *kin = odd ? k1 : k0;
+        unsigned long long *kout = odd ? k0 : k1;
+        const uint32_t *vin = odd ? v1 : v0;
+        uint32_t *vout = odd ? v0 : v1;
+        // A: digit counts of the chunk
+        run[d] = 0u;
+        __syncthreads();
+        for (int64_t i = t_lo * kTileKeys + threadIdx.x; i < i_hi; i += kSortThreads)
+            atomicAdd(&run[uint32_t(__ldcg(&kin[i]) >> shift) & 0xFFu], 1u);
+        __syncthreads();
+        chunk_hist[size_t(blockIdx.x) * kBins + d] = run[d];
+        if (!grid_barrier(bar, spin_limit, dev_status)) return;
+        // B: one digit per block, scanned over the chunks
+        for (unsigned dd = blockIdx.x; dd < kBins; dd += gridDim.x) {
+            uint32_t carry = 0u;
+            for (unsigned b0 = 0; b0 < gridDim.x; b0 += kSortThreads) {
+                const unsigned b = b0 + threadIdx.x;
+                const uint32_t x = b < gridDim.x ? __ldcg(&chunk_hist[size_t(b) * kBins + dd]) : 0u;
+                uint32_t tot;
+                const uint32_t ex = block_exclusive(x, &tot);
+                if (b < gridDim.x) chunk_pre[size_t(b) * kBins + dd] = carry + ex;
+                carry += tot;
+            }
+            if (threadIdx.x == 0) totals[dd] = carry;
+        }
+        if (!grid_barrier(bar, spin_limit, dev_status)) return;
+        // C: digit starts, then the chunk's tiles in order
+        uint32_t all;
+        const uint32_t dstart = block_exclusive(__ldcg(&totals[d]), &all);
+        run[d] = dstart + __ldcg(&chunk_pre[size_t(blockIdx.x) * kBins + d]);
+        for (int64_t tile = t_lo; tile < t_hi; ++tile) {
+            for (int i = threadIdx.x; i < kSortWarps * kBins; i += kSortThreads) (&cnt[0][0])[i] = 0u;
+            __syncthreads();
+            const int64_t base = tile * kTileKeys + int64_t(warp) * (32 * kItems);
+            unsigned long long key[kItems];
+            uint32_t val[kItems], rank[kItems];
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const int64_t i = base + int64_t(k) * 32 + lane;
+                key[k] = i < n ? __ldcg(&kin[i]) : 0ull;
+                if (kVals) val[k] = i < n ? __ldcg(&vin[i]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const int64_t i = base + int64_t(k) * 32 + lane;
+                const bool valid = i < n;
+                const uint32_t dg = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+                uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+                if (!valid) peers = ~peers;
+#pragma unroll
+                for (int bit = 0; bit < 8; ++bit) {
+                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, (dg >> bit) & 1u);
+                    peers &= ((dg >> bit) & 1u) ? m : ~m;
+                }
+                const int leader = __ffs(peers) - 1;
+                uint32_t before = 0;
+                if (valid && lane == leader) {
+                    before = cnt[warp][dg];
+                    cnt[warp][dg] = before + __popc(peers);
+                }
+                before = __shfl_sync(0xFFFFFFFFu, before, leader);
+                rank[k] = before + __popc(peers & lt_mask);
+                __syncwarp();
+            }
+            __syncthreads();
+            uint32_t total = 0u;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = cnt[w][d];
+                cnt[w][d] = total;
+                total += c;
+            }
+            local_start[d] = block_exclusive(total, &all);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const int64_t i = base + int64_t(k) * 32 + lane;
+                if (i >= n) continue;
+                const uint32_t dk = static_cast<uint32_t>(key[k] >> shift) & 0xFFu;
+                const uint32_t slot = local_start[dk] + cnt[warp][dk] + rank[k];
+                skey[slot] = key[k];
+                if (kVals) sval[slot] = val[k];
+            }
+            __syncthreads();
+            const int64_t t0 = tile * kTileKeys;
+            const int tile_n = n - t0 < kTileKeys ? int(n - t0) : kTileKeys;
+            for (int slot = threadIdx.x; slot < tile_n; slot += kSortThreads) {
+                const unsigned long long k = skey[slot];
+                const uint32_t dk = static_cast<uint32_t>(k >> shift) & 0xFFu;
+                const uint32_t pos = run[dk] + uint32_t(slot) - local_start[dk];
+                kout[pos] = k;
+                if (kVals) vout[pos] = sval[slot];
+            }
+            __syncthreads();
+            run[d] += total;
+        }
+        if (p + 1 < passes && !grid_barrier(bar, spin_limit, dev_status)) return;
+    }
+}
+
+// Which sort runs the passes: the cooperative one (1, the default) or the
+// onesweep passes with decoupled look-back (0); process wide.
+std::atomic<int> g_sort_method{1};
+
+// Launches the cooperative sort over passes first..passes-1 from buffer
+// pair 0; the result is in pair (passes - first) % 2.  Its counter words
+// (totals, barrier) must be zero: radix_sort clears them, the FA2 step's
+// keys kernel clears them in its graph.
+int coop_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int first, int passes, cudaStream_t s,
+              uint32_t *dev_status) {
+    const int64_t tiles = tiles_for(cap, kSortItemsSmall);
+    const void *kernel = b.vals[0] ? reinterpret_cast<const void *>(k_sort_coop<true>)
+                                   : reinterpret_cast<const void *>(k_sort_coop<false>);
+    int blocks = coop_blocks(kernel, kSortThreads, sm_count() * 4);
+    if (blocks > tiles) blocks = int(tiles);
+    // per-chunk digit counts and prefixes live in the look-back words
+    // (256 u64 per tile >= 2 x 256 u32 per block, as blocks <= tiles)
+    uint32_t *chunk_hist = reinterpret_cast<uint32_t *>(b.status);
+    uint32_t *chunk_pre = chunk_hist + size_t(blocks) * kBins;
+    uint32_t *totals = b.counts;
+    GridBar *bar = reinterpret_cast<GridBar *>(b.counts + kMaxPasses * kBins + kMaxPasses);
+    unsigned long long *k0 = b.keys[0], *k1 = b.keys[1];
+    uint32_t *v0 = b.vals[0], *v1 = b.vals[1];
+    int limit = spin_limit();
+    void *args[] = {&k0, &k1, &v0, &v1, &cap, &d_count, &first, &passes, &chunk_hist, &chunk_pre, &totals,
+                    &bar, &dev_status, &limit};
+    return launch_coop(kernel, blocks, kSortThreads, args, s);
+}
+
 // The look-back words are sized for the smaller tiles, so a workspace stays
 // large enough whatever tile size the cutoff picks later.
 int64_t sort_tiles(int64_t cap) {
@@ -427,7 +645,7 @@ void carve_sort(Carver &c, int64_t cap, bool with_vals, SortBuffers &out) {
     out.vals[0] = with_vals ? c.take<uint32_t>(size_t(cap)) : nullptr;
     out.vals[1] = with_vals ? c.take<uint32_t>(size_t(cap)) : nullptr;
     out.status = c.take<unsigned long long>(size_t(kBins) * size_t(sort_tiles(cap)));
-    out.counts = c.take<uint32_t>(size_t(kMaxPasses) * kBins + kMaxPasses);
+    out.counts = c.take<uint32_t>(size_t(sort_counter_words()));
 }
 
 namespace {
@@ -441,16 +659,16 @@ int onesweep_pass(SortBuffers &b, int64_t cap, const int64_t *d_count, int cur, 
     uint32_t *vi = b.vals[cur], *vo = b.vals[cur ^ 1];
     if (b.vals[0] && small)
         note_launch(), k_sort_onesweep<true, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag, spin_limit());
     else if (b.vals[0])
         note_launch(), k_sort_onesweep<true, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+            ki, ko, vi, vo, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag, spin_limit());
     else if (small)
         note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<g, kSortThreads, 0, s>>>(
-            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag, spin_limit());
     else
         note_launch(), k_sort_onesweep<false, kSortItemsBig><<<g, kSortThreads, 0, s>>>(
-            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag);
+            ki, ko, nullptr, nullptr, cap, d_count, shift, base, tile_counter, b.status, dev_status, tag, spin_limit());
     return launch_status();
 }
 
@@ -464,7 +682,12 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     const int passes = (end_bit + 7) / 8;
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
-    BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * (size_t(kMaxPasses) * kBins + kMaxPasses), s));
+    BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
+    if (g_sort_method.load(std::memory_order_relaxed) == 1) {
+        BGV_TRY(coop_sort(b, cap, d_count, 0, passes, s, dev_status));
+        *result_buffer = passes & 1;
+        return BGV_OK;
+    }
     const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;  // >= tiles
     note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
         b.keys[0], cap, d_count, 0, passes, b.counts, b.status, tiles, nullptr, 0);
@@ -501,10 +724,18 @@ __device__ __forceinline__ unsigned long long run_key(unsigned long long k, int6
 }
 
 // End of the run of equal high bits that starts at `start` (the array is
-// sorted on the high bits).
+// sorted on the high bits): galloping from the start (probes at +1, +2, +4,
+// ... stay near the run), then a binary search inside the last step.
 __device__ __forceinline__ int64_t run_end(const unsigned long long *keys, int64_t n, int64_t start) {
     const unsigned long long hi = keys[start] >> 16;
-    int64_t lo = start, up = n;
+    int64_t step = 1, lo = start + 1;  // keys[lo - 1] is in the run
+    while (lo < n && (keys[lo] >> 16) == hi) {
+        lo += step;
+        step <<= 1;
+    }
+    int64_t up = lo < n ? lo : n;  // first index past the run lies in (lo - step/2, up]
+    lo = lo - (step >> 1);
+    if (lo < start + 1) lo = start + 1;
     while (lo < up) {
         const int64_t mid = (lo + up) >> 1;
         if ((keys[mid] >> 16) <= hi) lo = mid + 1; else up = mid;
@@ -513,9 +744,10 @@ __device__ __forceinline__ int64_t run_end(const unsigned long long *keys, int64
 }
 
 __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__restrict__ keys,
-                                                          uint32_t *__restrict__ vals, int64_t n,
-                                                          uint8_t *__restrict__ descent, uint32_t *__restrict__ runs,
-                                                          uint32_t *run_count) {
+                                                          uint32_t *__restrict__ vals, int64_t cap,
+                                                          const int64_t *d_count, uint8_t *__restrict__ descent,
+                                                          uint32_t *__restrict__ runs, uint32_t *run_count) {
+    const int64_t n = load_count(d_count, cap);
     const int lane = threadIdx.x & 31;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
@@ -548,7 +780,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__
 #pragma unroll
         for (int a = 0; a < kShortRun; ++a) {
             kk[a] = a < r ? run_key(keys[i + a], a) : ~0ull;
-            vv[a] = a < r ? vals[i + a] : 0u;
+            vv[a] = (vals && a < r) ? vals[i + a] : 0u;
             if (a > 0) ordered = ordered && kk[a - 1] < kk[a];
         }
         if (ordered) continue;
@@ -559,7 +791,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__
 #pragma unroll
                 for (int c = 0; c < kShortRun; ++c) rk += kk[c] < kk[a] ? 1u : 0u;
                 keys[i + rk] = (hi << 16) | (kk[a] >> 32);
-                vals[i + rk] = vv[a];
+                if (vals) vals[i + rk] = vv[a];
             }
         }
     }
@@ -570,12 +802,13 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__
 // 8 keys and counts the smaller ones through shuffles); longer ones go on
 // to the block kernel's list.
 __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__restrict__ keys,
-                                                          uint32_t *__restrict__ vals, int64_t n,
-                                                          const uint8_t *__restrict__ descent,
+                                                          uint32_t *__restrict__ vals, int64_t cap,
+                                                          const int64_t *d_count, const uint8_t *__restrict__ descent,
                                                           const uint32_t *__restrict__ runs,
                                                           const uint32_t *run_count, uint32_t *__restrict__ big,
                                                           uint32_t *big_count) {
     constexpr int kPer = kWarpRun / 32;
+    const int64_t n = load_count(d_count, cap);
     const int lane = threadIdx.x & 31;
     const uint32_t count = *run_count;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -609,7 +842,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__
         for (int j = 0; j < kPer; ++j) {
             const int64_t t = lane + 32 * j;
             kk[j] = t < len ? run_key(keys[start + t], t) : ~0ull;
-            vv[j] = t < len ? vals[start + t] : 0u;
+            vv[j] = (vals && t < len) ? vals[start + t] : 0u;
             rank[j] = 0;
         }
 #pragma unroll
@@ -626,7 +859,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__
             const int64_t t = lane + 32 * j;
             if (t < len) {
                 keys[start + rank[j]] = (hi << 16) | (kk[j] >> 32);
-                vals[start + rank[j]] = vv[j];
+                if (vals) vals[start + rank[j]] = vv[j];
             }
         }
     }
@@ -643,9 +876,10 @@ constexpr int kBlockItems = 8;
 __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *__restrict__ keys,
                                                            uint32_t *__restrict__ vals,
                                                            unsigned long long *__restrict__ alt_keys,
-                                                           uint32_t *__restrict__ alt_vals, int64_t n,
-                                                           const uint32_t *__restrict__ big,
+                                                           uint32_t *__restrict__ alt_vals, int64_t cap,
+                                                           const int64_t *d_count, const uint32_t *__restrict__ big,
                                                            const uint32_t *big_count) {
+    const int64_t n = load_count(d_count, cap);
     constexpr int kWarps = kFixThreads / 32;
     constexpr int kGroups = kBlockItems * kWarps;
     __shared__ uint32_t hist[4][16];
@@ -662,7 +896,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
         __syncthreads();
         const int64_t len = end_sh - start;
         unsigned long long *sk = keys + start, *dk = alt_keys + start;
-        uint32_t *sv = vals + start, *dv = alt_vals + start;
+        uint32_t *sv = vals ? vals + start : nullptr, *dv = alt_vals ? alt_vals + start : nullptr;
         for (int64_t t0 = 0; t0 < len; t0 += blockDim.x) {
             const int64_t t = t0 + threadIdx.x;
             const unsigned long long k = t < len ? sk[t] : 0ull;
@@ -691,7 +925,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
                 for (int j = 0; j < kBlockItems; ++j) {
                     const int64_t t = t0 + int64_t(j) * blockDim.x + threadIdx.x;
                     k[j] = t < len ? sk[t] : 0ull;
-                    v[j] = t < len ? sv[t] : 0u;
+                    v[j] = (sv && t < len) ? sv[t] : 0u;
                     d[j] = t < len ? int((k[j] >> shift) & 15) : 16;
                 }
                 for (int e = threadIdx.x; e < kGroups * 17; e += blockDim.x) (&wcount[0][0])[e] = 0;
@@ -718,7 +952,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
                     if (d[j] < 16) {
                         const uint32_t pos = wcount[j * kWarps + warp][d[j]] + __popc(peers[j] & lt_mask);
                         dk[pos] = k[j];
-                        dv[pos] = v[j];
+                        if (dv) dv[pos] = v[j];
                     }
                 }
                 __syncthreads();
@@ -741,38 +975,77 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r) {
     r.counts = c.take<uint32_t>(2);
 }
 
-int64_t sort_counter_words() { return int64_t(kMaxPasses) * kBins + kMaxPasses; }
+// digit counts of every pass, tile counters, then the grid-barrier words of
+// the cooperative sort
+int64_t sort_counter_words() { return int64_t(kMaxPasses) * kBins + kMaxPasses + 4; }
 
-int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t n, int end_bit, cudaStream_t s,
-                    int *result_buffer, uint32_t *dev_status, bool counters_cleared) {
+int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const int64_t *d_count, int end_bit,
+                    cudaStream_t s, int *result_buffer, uint32_t *dev_status, bool counters_cleared) {
     const int passes = (end_bit + 7) / 8;
-    if (!b.vals[0] || end_bit <= 16 || passes > kMaxPasses || n >= (int64_t(1) << 32))
-        return radix_sort(b, n, nullptr, end_bit, s, result_buffer, dev_status);
-    const int items = sort_items(n);
+    if (end_bit <= 16 || passes > kMaxPasses || cap >= (int64_t(1) << 32))
+        return radix_sort(b, cap, d_count, end_bit, s, result_buffer, dev_status);
+    const int items = sort_items(cap);
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     if (!counters_cleared)
         BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
-    const int64_t count_blocks = (n + kCountTile - 1) / kCountTile;  // >= tiles
-    note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0, s>>>(
-        b.keys[0], n, nullptr, 2, passes, b.counts, b.status, tiles_for(n, items), r.counts, 2);
-    BGV_TRY(launch_status());
     int cur = 0;
-    for (int p = 2; p < passes; ++p) {
-        BGV_TRY(onesweep_pass(b, n, nullptr, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p), items,
-                              s, dev_status));
-        cur ^= 1;
+    if (g_sort_method.load(std::memory_order_relaxed) == 1) {
+        BGV_CUDA(cudaMemsetAsync(r.counts, 0, 2 * sizeof(uint32_t), s));
+        BGV_TRY(coop_sort(b, cap, d_count, 2, passes, s, dev_status));
+        cur = (passes - 2) & 1;
+    } else {
+        const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;  // >= tiles
+        note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0,
+                                      s>>>(b.keys[0], cap, d_count, 2, passes, b.counts, b.status,
+                                           tiles_for(cap, items), r.counts, 2);
+        BGV_TRY(launch_status());
+        for (int p = 2; p < passes; ++p) {
+            BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p),
+                                  items, s, dev_status));
+            cur ^= 1;
+        }
     }
-    if (n > 1) {
-        note_launch(), k_fix_runs<<<grid_for(n, kFixThreads, 152 * 8), kFixThreads, 0, s>>>(
-            b.keys[cur], b.vals[cur], n, r.descent, r.runs, r.counts);
-        note_launch(), k_fix_warp<<<152 * 8, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], n, r.descent, r.runs,
-                                                                  r.counts, r.big, r.counts + 1);
-        note_launch(), k_fix_block<<<152 * 2, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
-                                                                   b.vals[cur ^ 1], n, r.big, r.counts + 1);
+    if (cap > 1) {
+        note_launch(), k_fix_runs<<<grid_for(cap, kFixThreads, sm_count() * 8), kFixThreads, 0, s>>>(
+            b.keys[cur], b.vals[cur], cap, d_count, r.descent, r.runs, r.counts);
+        note_launch(), k_fix_warp<<<sm_count() * 8, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], cap, d_count,
+                                                                         r.descent, r.runs, r.counts, r.big,
+                                                                         r.counts + 1);
+        note_launch(), k_fix_block<<<sm_count() * 2, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                                                          b.vals[cur ^ 1], cap, d_count, r.big,
+                                                                          r.counts + 1);
         BGV_TRY(launch_status());
     }
     *result_buffer = cur;
     return BGV_OK;
+}
+
+// ------------------------------------------------ bounded-wait self check
+// One onesweep block as tile 1 of a two-tile, all-zero key set whose tile 0
+// never runs: its look-back finds nothing published and must give up at the
+// spin limit (BGV_DEV_TIMEOUT).  Every digit offset is 0, so the block's
+// writes stay inside its own tile's slots.
+size_t wait_check_sort_bytes() {
+    Carver c(nullptr, 0);
+    SortBuffers b;
+    carve_sort(c, 2 * int64_t(kSortThreads) * kSortItemsSmall, false, b);
+    return c.used();
+}
+
+int wait_check_sort(void *scratch, uint32_t *dev_status, cudaStream_t s) {
+    const int64_t cap = 2 * int64_t(kSortThreads) * kSortItemsSmall;
+    Carver c(scratch, 0);
+    SortBuffers b;
+    carve_sort(c, cap, false, b);
+    BGV_CUDA(cudaMemsetAsync(scratch, 0, wait_check_sort_bytes(), s));
+    const uint32_t one = 1u;  // the tile counter: the launched block takes tile 1
+    uint32_t *tile_counter = b.counts + kMaxPasses * kBins;
+    BGV_CUDA(cudaMemcpyAsync(tile_counter, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+    note_launch(), k_sort_onesweep<false, kSortItemsSmall><<<1, kSortThreads, 0, s>>>(
+        b.keys[0], b.keys[1], nullptr, nullptr, cap, nullptr, 0, b.counts, tile_counter, b.status, dev_status,
+        pass_tag(0), spin_limit());
+    BGV_TRY(launch_status());
+    return cudaStreamSynchronize(s) == cudaSuccess ? BGV_OK : BGV_ECUDA;  // `one` lives on this stack
 }
 
 // ------------------------------------------------------------- autotuner
@@ -793,26 +1066,33 @@ __global__ void k_tune_keys(unsigned long long *keys, uint32_t *vals, int64_t n)
 }  // namespace
 
 int64_t sort_cutoff() { return g_small_sort_cutoff.load(std::memory_order_relaxed); }
+int64_t set_sort_cutoff(int64_t cutoff) { return g_small_sort_cutoff.exchange(cutoff, std::memory_order_relaxed); }
+int set_sort_method(int method) { return g_sort_method.exchange(method, std::memory_order_relaxed); }
+int sort_method() { return g_sort_method.load(std::memory_order_relaxed); }
 
 int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
-                  int32_t *sizes_log2, int32_t *count) {
+                  float *ms_coop, int32_t *sizes_log2, int32_t *count, int32_t *method) {
     cudaEvent_t e0, e1;
     BGV_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return BGV_ECUDA;
     }
+    const int method_before = g_sort_method.load(std::memory_order_relaxed);
     int rc = BGV_OK;
     int64_t cutoff = 0;
+    double sum_onesweep = 0.0, sum_coop = 0.0;
     int k = 0;
     for (int lg = 14; lg <= 30 && (int64_t(1) << lg) <= max_keys && rc == BGV_OK; lg += 2, ++k) {
         const int64_t n = int64_t(1) << lg;
-        float best[2] = {0.0f, 0.0f};
-        for (int v = 0; v < 2 && rc == BGV_OK; ++v) {
-            const int items = v == 0 ? kSortItemsSmall : kSortItemsBig;
+        float best[3] = {0.0f, 0.0f, 0.0f};
+        for (int v = 0; v < 3 && rc == BGV_OK; ++v) {
+            // v 0, 1: onesweep passes at 8 and 16 keys per thread; v 2: cooperative
+            const int items = v == 1 ? kSortItemsBig : kSortItemsSmall;
+            g_sort_method.store(v == 2 ? 1 : 0, std::memory_order_relaxed);
             float times[3];
             for (int r = 0; r < 4 && rc == BGV_OK; ++r) {
-                note_launch(), k_tune_keys<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(b.keys[0], b.vals[0], n);
+                note_launch(), k_tune_keys<<<grid_for(n, 256, sm_count() * 8), 256, 0, s>>>(b.keys[0], b.vals[0], n);
                 int res = 0;
                 if (cudaEventRecord(e0, s) != cudaSuccess) rc = BGV_ECUDA;
                 if (rc == BGV_OK) rc = radix_sort(b, n, nullptr, 48, s, &res, dev_status, items);
@@ -829,13 +1109,24 @@ int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *de
         if (rc != BGV_OK) break;
         if (ms8) ms8[k] = best[0];
         if (ms16) ms16[k] = best[1];
+        if (ms_coop) ms_coop[k] = best[2];
         if (sizes_log2) sizes_log2[k] = lg;
         if (best[0] <= best[1]) cutoff = n;
+        sum_onesweep += best[0] < best[1] ? best[0] : best[1];
+        sum_coop += best[2];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (count) *count = k;
-    if (rc == BGV_OK) g_small_sort_cutoff.store(cutoff, std::memory_order_relaxed);
+    if (rc == BGV_OK) {
+        // the cutoff of the onesweep passes, and whichever method summed less
+        // time over the sizes timed
+        g_small_sort_cutoff.store(cutoff, std::memory_order_relaxed);
+        g_sort_method.store(k > 0 && sum_coop > sum_onesweep ? 0 : 1, std::memory_order_relaxed);
+    } else {
+        g_sort_method.store(method_before, std::memory_order_relaxed);
+    }
+    if (method) *method = g_sort_method.load(std::memory_order_relaxed);
     return rc;
 }
 

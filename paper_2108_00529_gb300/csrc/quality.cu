@@ -12,7 +12,7 @@
 namespace bgv {
 namespace {
 constexpr int kThreads = 256;
-constexpr int kSqBlocks = 152 * 4;
+constexpr int kSqBlocks = 608;  // partial sums of vol^2 (a fixed count: sized into the workspace)
 typedef unsigned __int128 u128;
 
 __global__ void __launch_bounds__(kThreads) k_mod_count(const int32_t *__restrict__ edges, int64_t m, int32_t n,
@@ -90,7 +90,7 @@ extern "C" int bgv_modularity(const int32_t *edges, int64_t m, int32_t n, const 
     unsigned long long *part = c.take<unsigned long long>(2 * kSqBlocks);
     BGV_CUDA(cudaMemsetAsync(vol, 0, sizeof(uint32_t) * size_t(n), st));
     BGV_CUDA(cudaMemsetAsync(intra, 0, sizeof(unsigned long long), st));
-    note_launch(), k_mod_count<<<grid_for(m, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, labels, vol, intra,
+    note_launch(), k_mod_count<<<grid_for(m, kThreads, sm_count() * 8), kThreads, 0, st>>>(edges, m, n, labels, vol, intra,
                                                                                    status_ptr(ws));
     BGV_TRY(launch_status());
     note_launch(), k_mod_squares<<<kSqBlocks, kThreads, 0, st>>>(vol, n, part);

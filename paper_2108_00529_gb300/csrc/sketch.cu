@@ -3,8 +3,9 @@
 // Algorithm 2 adds 1 to M[i][h_i(x)] for every event x; the events here are
 // the 2m edge endpoints.  Integer addition commutes, so the same matrix is
 // built from exact per-node degrees: one edge pass counts degrees (L2
-// atomics on an n-entry array), then every node with degree d adds d to its
-// r cells.  That turns 2 r m scattered sketch updates into 2m + r n.
+// atomics on an n-entry array, aggregated per warp over equal node ids),
+// then every node with degree d adds d to its r cells.  That turns 2 r m
+// scattered sketch updates into at most 2m + r n.
 //
 // Edges are read as int4 (two edges per 16-byte load) with a grid-stride
 // loop over a grid sized to fill the GPU.
@@ -38,28 +39,49 @@ HashFamily make_hash_family(uint64_t seed, int rows, uint32_t width) {
 namespace {
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void count_endpoint(int32_t x, int32_t n, uint32_t *deg, uint32_t *status) {
-    if (static_cast<uint32_t>(x) < static_cast<uint32_t>(n))
-        atomicAdd(&deg[x], 1u);
-    else
-        raise_status(status, BGV_DEV_BADEDGE);
+// One endpoint per lane: lanes holding the same node id are found with
+// __match_any_sync and only the lowest of them adds their number, so a hub
+// that shows up several times in a warp's 32 endpoints costs one atomic.
+__device__ __forceinline__ void count_endpoints_warp(bool have, int32_t x, int32_t n, uint32_t *deg,
+                                                     uint32_t *status) {
+    const bool ok = have && static_cast<uint32_t>(x) < static_cast<uint32_t>(n);
+    if (have && !ok) raise_status(status, BGV_DEV_BADEDGE);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, ok ? x : -1);
+    const int lane = threadIdx.x & 31;
+    if (ok && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&deg[x], uint32_t(__popc(peers)));
 }
 
+// Whole warps iterate together (the exit test uses the warp's first index)
+// so every __match_any_sync sees all 32 lanes.  Each lane loads two int4
+// (four edges) before counting, so the loads are in flight together.
+constexpr int kDegLoads = 2;
 __global__ void __launch_bounds__(kThreads) k_degree_count(const int32_t *__restrict__ edges, int64_t m, int32_t n,
                                                            uint32_t *__restrict__ deg, uint32_t *status) {
     const int4 *e2 = reinterpret_cast<const int4 *>(edges);
     const int64_t pairs = m >> 1;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < pairs; p += stride) {
-        int4 e = __ldcs(e2 + p);
-        count_endpoint(e.x, n, deg, status);
-        count_endpoint(e.y, n, deg, status);
-        count_endpoint(e.z, n, deg, status);
-        count_endpoint(e.w, n, deg, status);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t base = warp * 32 * kDegLoads; base < pairs; base += warps * 32 * kDegLoads) {
+        int4 e[kDegLoads];
+        bool have[kDegLoads];
+#pragma unroll
+        for (int r = 0; r < kDegLoads; ++r) {
+            const int64_t p = base + int64_t(r) * 32 + lane;
+            have[r] = p < pairs;
+            e[r] = have[r] ? __ldcs(e2 + p) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int r = 0; r < kDegLoads; ++r) {
+            count_endpoints_warp(have[r], e[r].x, n, deg, status);
+            count_endpoints_warp(have[r], e[r].y, n, deg, status);
+            count_endpoints_warp(have[r], e[r].z, n, deg, status);
+            count_endpoints_warp(have[r], e[r].w, n, deg, status);
+        }
     }
-    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        count_endpoint(edges[2 * (m - 1)], n, deg, status);
-        count_endpoint(edges[2 * (m - 1) + 1], n, deg, status);
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x < 32) {  // the odd last edge, one warp
+        count_endpoints_warp(lane == 0, edges[2 * (m - 1)], n, deg, status);
+        count_endpoints_warp(lane == 0, edges[2 * (m - 1) + 1], n, deg, status);
     }
 }
 
@@ -123,13 +145,13 @@ int run_sketch(const int32_t *edges, int64_t m, int32_t n, const HashFamily &h, 
     BGV_CUDA(cudaMemsetAsync(s.deg, 0, sizeof(uint32_t) * size_t(n), st));
     BGV_CUDA(cudaMemsetAsync(sketch, 0, sizeof(uint32_t) * size_t(h.rows) * h.width * mats, st));
     if (m > 0) {
-        note_launch(), k_degree_count<<<grid_for((m + 1) / 2, kThreads, 152 * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
+        note_launch(), k_degree_count<<<grid_for((m / 2 + kDegLoads - 1) / kDegLoads, kThreads, sm_count() * 8), kThreads, 0, st>>>(edges, m, n, s.deg, status);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_sketch_fill<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(s.deg, n, h, sketch, node_graph,
+    note_launch(), k_sketch_fill<<<grid_for(n, kThreads, sm_count() * 8), kThreads, 0, st>>>(s.deg, n, h, sketch, node_graph,
                                                                                        node_off);
     BGV_TRY(launch_status());
-    note_launch(), k_sketch_query<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(sketch, n, h, deg_est, node_graph,
+    note_launch(), k_sketch_query<<<grid_for(n, kThreads, sm_count() * 8), kThreads, 0, st>>>(sketch, n, h, deg_est, node_graph,
                                                                                         node_off);
     return launch_status();
 }
@@ -161,7 +183,7 @@ constexpr int32_t kNoAllocMaxNodes = 1 << 22;
 constexpr int kNoAllocMaxDevices = 64;
 
 // Degree counters followed by one status word used when the caller passes
-// no status pointer.
+// no status pointer (cleared by every such call and read back at its end).
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxNodes + 64];
 
 std::mutex g_noalloc_mutex;
@@ -198,8 +220,17 @@ extern "C" int bgv_sketch_degrees_noalloc(const int32_t *edges, int64_t m, int32
     BGV_TRY(noalloc_scratch(&scratch));
     SketchScratch s;
     s.deg = scratch;
-    uint32_t *st = status ? status : scratch + kNoAllocMaxNodes;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     const HashFamily h = make_hash_family(seed, rows, uint32_t(width));
-    return run_sketch(edges, m, n, h, sketch, deg_est, s, st, static_cast<cudaStream_t>(stream));
+    if (status) return run_sketch(edges, m, n, h, sketch, deg_est, s, status, cs);
+    // No status word from the caller: use the one after the counters, cleared
+    // on every call, and report what the device found before returning.
+    uint32_t *own = scratch + kNoAllocMaxNodes;
+    BGV_CUDA(cudaMemsetAsync(own, 0, sizeof(uint32_t), cs));
+    BGV_TRY(run_sketch(edges, m, n, h, sketch, deg_est, s, own, cs));
+    uint32_t seen = 0;
+    BGV_CUDA(cudaMemcpyAsync(&seen, own, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
+    BGV_CUDA(cudaStreamSynchronize(cs));
+    return seen ? BGV_EDEVICE : BGV_OK;
 }
 

@@ -109,14 +109,14 @@ extern "C" int bgv_colour_groups(int64_t K, const uint32_t *sizes, uint8_t *grou
     Carver c(ws, kHeaderBytes);
     SortBuffers sort;
     carve_style(c, K, sort);
-    note_launch(), k_size_keys<<<grid_for(K, 256, 152 * 8), 256, 0, st>>>(sizes, K, sort.keys[0], sort.vals[0]);
+    note_launch(), k_size_keys<<<grid_for(K, 256, sm_count() * 8), 256, 0, st>>>(sizes, K, sort.keys[0], sort.vals[0]);
     BGV_TRY(launch_status());
     int res = 0;
     BGV_TRY(radix_sort(sort, K, nullptr, 32, st, &res, status_ptr(ws)));
     note_launch(), k_colour_groups<<<1, kStyleThreads, 0, st>>>(sort.keys[res], sort.vals[res], K, group);
     BGV_TRY(launch_status());
     if (node_colour && n > 0) {
-        note_launch(), k_node_colours<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, node_map, K, group, node_colour);
+        note_launch(), k_node_colours<<<grid_for(n, 256, sm_count() * 8), 256, 0, st>>>(n, node_map, K, group, node_colour);
         BGV_TRY(launch_status());
     }
     return BGV_OK;
@@ -240,11 +240,11 @@ extern "C" int bgv_render(int64_t K, const float *xy, const float *radius, const
     note_launch(), k_render_frame<<<1, kStyleThreads, 0, st>>>(p, radius, K, W, H, frame);
     BGV_TRY(launch_status());
     if (K > 0) {
-        note_launch(), k_render_splat<<<grid_for(K * 32, kStyleThreads, 152 * 16), kStyleThreads, 0, st>>>(
+        note_launch(), k_render_splat<<<grid_for(K * 32, kStyleThreads, sm_count() * 16), kStyleThreads, 0, st>>>(
             p, radius, K, W, H, frame, zbuf);
         BGV_TRY(launch_status());
     }
-    note_launch(), k_render_shade<<<grid_for(pixels, kStyleThreads, 152 * 8), kStyleThreads, 0, st>>>(
+    note_launch(), k_render_shade<<<grid_for(pixels, kStyleThreads, sm_count() * 8), kStyleThreads, 0, st>>>(
         zbuf, pixels, K, group, reinterpret_cast<uchar4 *>(rgba));
     return launch_status();
 }

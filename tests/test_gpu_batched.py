@@ -118,7 +118,7 @@ def _oracle_batch(graphs):
 def test_batched_forces_equal_separate_calls():
     # Same positions, same tree per graph: repulsion and gravity are bit
     # identical to the single-graph call; attraction differs only in the
-    # grouping of its FP32 sums.
+    # grouping of its FP32 sums (its ranges start at other offsets).
     graphs = _mixed_batch()
     sgs, koff, off, adj, w, mass = _oracle_batch(graphs)
     Gn, K = len(graphs), int(koff[-1])
@@ -184,3 +184,60 @@ def test_batch_set_integer_stages_equal_separate_calls():
         nm1, _, _, K, Es = _single(e, n, p)
         assert (K_off[g + 1] - K_off[g], Es_off[g + 1] - Es_off[g]) == (K, Es), g
         assert np.array_equal(nm[no[g]:no[g + 1]], nm1), g
+
+
+@pytest.mark.slow
+def test_batched_forces_match_oracle_above_the_sort_cutoff():
+    # Batched forces against the oracle directly, graph by graph: a batch of
+    # uneven graphs whose 4.3 M bodies exceed a 2^22-key cutoff of the sort
+    # (set here, so it runs 16 keys per thread).  The interaction total equals the sum of the
+    # oracle's per-graph totals (same trees and theta) and every force is
+    # within 1e-3 of the FP64 oracle.
+    rng = np.random.default_rng(9)
+    sizes = [4_200_000, 1, 2, 1000, 37_000, 90_001]
+    parts = []
+    for g, K in enumerate(sizes):
+        side = 2.0 * np.sqrt(K)
+        pos = (rng.random((K, 2)) * side - side / 2).astype(np.float32)
+        e = graphgen.random_graph(K, 2 * K, seed=100 + g) if K > 1 else np.zeros((0, 2), np.int32)
+        off, adj, w = G.csr_from_edges(e, K)
+        w = rng.integers(1, 4, w.shape[0]).astype(np.uint32)
+        src = np.repeat(np.arange(K), np.diff(off))
+        key = np.minimum(src, adj).astype(np.int64) * K + np.maximum(src, adj)
+        _, inv = np.unique(key, return_inverse=True)
+        w = (inv % 3 + 1).astype(np.uint32)  # symmetric weights
+        mass = rng.integers(1, 6, K).astype(np.uint32)
+        parts.append((pos, mass, off, adj, w))
+    Gn = len(sizes)
+    koff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    offs = [np.zeros(1, np.int64)]
+    for _, _, off, _, _ in parts:
+        offs.append(off[1:].astype(np.int64) + offs[-1][-1])
+    off = np.concatenate(offs).astype(np.int32)
+    adj = np.concatenate([pt[3] + koff[g] for g, pt in enumerate(parts)]).astype(np.int32)
+    w = np.concatenate([pt[4] for pt in parts])
+    mass = np.concatenate([pt[1] for pt in parts])
+    pos = np.concatenate([pt[0] for pt in parts])
+    K, nnz = int(koff[-1]), int(off[-1])
+    p = FA2Params()
+    Fr, Fa, Fg = (torch.zeros((K, 2), dtype=torch.float32, device="cuda") for _ in range(3))
+    ws = B.alloc_ws(B.bgv_fa2_ws_size_batched(Gn, K, nnz))
+    O, A, W = G._csr_dev(off, adj, w)
+    prev = B.bgv_set_sort_cutoff(1 << 22)
+    try:
+        assert K > B.bgv_sort_cutoff()
+        B.bgv_fa2_forces_batched(Gn, koff, nnz, O, A, W, G.dev(mass), G.fa2_params(p), G.dev(pos), Fr, Fa, Fg, ws)
+    finally:
+        B.bgv_set_sort_cutoff(prev)
+    st = B.bgv_fa2_read_stats(ws)
+    assert st.status == 0
+    Fr, Fa, Fg = G.host(Fr), G.host(Fa), G.host(Fg)
+    total = 0
+    for g, (pg, mg, og, ag, wg) in enumerate(parts):
+        a, b = int(koff[g]), int(koff[g + 1])
+        Fr0, inter0 = oracle.bh_repulsion(pg, mg, p)
+        total += inter0
+        assert G.rel_err(Fr[a:b], Fr0) <= 1e-3, g
+        assert G.rel_err(Fa[a:b], oracle.attraction(og, ag, wg, pg)) <= 1e-3, g
+        assert G.rel_err(Fg[a:b], oracle.gravity(mg, pg, 1.0, 0)) <= 1e-3, g
+    assert st.interactions == total

@@ -19,6 +19,8 @@ if not torch.cuda.is_available():
 
 import gpu_pipeline as G  # noqa: E402
 
+B = G.B
+
 TOL = 1e-3
 
 
@@ -250,3 +252,102 @@ def test_attraction_over_uneven_rows():
     assert G.rel_err(r["Fa"], oracle.attraction(off, adj, w, pos)) <= TOL
     empty = np.diff(off) == 0
     assert np.all(r["Fa"][empty] == 0.0)
+
+
+def _swing_traction_products(F, Fprev, mass):
+    """The per-node FP32 products the step sums: m |F - Fprev| and
+    (m / 2) |F + Fprev|, with the kernel's rounding steps."""
+    f32 = np.float32
+    F, Fp, m = F.astype(f32), Fprev.astype(f32), mass.astype(f32)
+    sx, sy = F[:, 0] - Fp[:, 0], F[:, 1] - Fp[:, 1]
+    tx, ty = F[:, 0] + Fp[:, 0], F[:, 1] + Fp[:, 1]
+    return m * np.sqrt(sx * sx + sy * sy), (f32(0.5) * m) * np.sqrt(tx * tx + ty * ty)
+
+
+def test_swing_and_traction_sums_are_exact():
+    # The global swing S and traction T that set the adaptive speed are the
+    # sums of FP32 per-node products; the step must return them to within 2
+    # units in the last place of FP64 of the exact sum (math.fsum is
+    # correctly rounded).  The case loses digits in a plain sum: node 0
+    # carries a product ~1e21 whose FP64 spacing exceeds each of the other
+    # 150,000 products, so adding them one by one after it drops them all.
+    import math
+    K = 150_000
+    rng = np.random.default_rng(21)
+    pos = (rng.random((K, 2)) * 2000 - 1000).astype(np.float32)
+    mass = rng.integers(1, 4, K).astype(np.uint32)
+    mass[0] = 4_000_000_000
+    Fprev = (rng.normal(size=(K, 2)) * 10.0 ** rng.uniform(-6, 3, (K, 1))).astype(np.float32)
+    Fprev[0] = [3e11, -2e11]
+    off, adj, w = G.csr_from_edges(graphgen.random_graph(K, 2 * K, seed=22), K)
+    dv = G.Fa2Device(pos, mass, off, adj, w, FA2Params(), Fprev=Fprev, speed=1.0)
+    dv.step()
+    st = dv.stats()
+    assert st.status == 0
+    _, F1, _, speed1 = dv.state()
+    msw, mtr = _swing_traction_products(F1, Fprev, mass)
+    S, T = math.fsum(msw.astype(np.float64)), math.fsum(mtr.astype(np.float64))
+    assert abs(st.S - S) <= 2 * math.ulp(S)
+    assert abs(st.T - T) <= 2 * math.ulp(T)
+    # the case is one a plain running sum gets wrong by far more
+    naive = 0.0
+    for x in msw.astype(np.float64):
+        naive += x
+    assert abs(naive - S) > 16 * math.ulp(S)
+    # the speed follows from S and T in FP64 (50 % rise cap)
+    sp = 1.0
+    target = 1.0 * st.T / st.S
+    assert speed1 == sp + min(target - sp, 0.5 * sp)
+
+
+def test_swing_and_traction_sums_of_a_supergraph_step():
+    # The same property on a step of the method's own state (sbm16
+    # supergraph, 20 steps in).
+    import math
+    sg = _supergraph_case()
+    p = FA2Params()
+    dv = G.Fa2Device(oracle.fa2_init(sg["K"], 2), sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], p)
+    dv.run(20, False)
+    Fprev = G.host(dv.Fprev).copy()
+    dv.step()
+    st = dv.stats()
+    F1 = G.host(dv.F)
+    msw, mtr = _swing_traction_products(F1, Fprev, sg["mass"])
+    S, T = math.fsum(msw.astype(np.float64)), math.fsum(mtr.astype(np.float64))
+    assert abs(st.S - S) <= 2 * math.ulp(S) and abs(st.T - T) <= 2 * math.ulp(T)
+
+
+def test_fa2_autotuner_keeps_results():
+    # The launch-shape autotuner times steps on the caller's supergraph and
+    # leaves its choice in force.  Traversal block size and tail grid do not
+    # change any result; the attraction range only regroups FP32 row sums.
+    pos, mass, off, adj, w = _case(20011, 31, 9, "clustered")
+    K, nnz = pos.shape[0], int(off[-1])
+    p = FA2Params()
+    ws = B.alloc_ws(B.bgv_autotune_fa2_ws_size(K, nnz))
+    O, A, W = G._csr_dev(off, adj, w)
+    try:
+        r = B.bgv_autotune_fa2(K, nnz, O, A, W, G.dev(mass), G.fa2_params(p), G.dev(pos), ws)
+        assert r.att_range in (256, 512, 1024) and r.repulse_threads in (128, 256)
+        assert r.tail_blocks_per_sm in (2, 4, 8)
+        assert min(r.ms_att_range) > 0 and min(r.ms_repulse_threads) > 0 and min(r.ms_tail_blocks) > 0
+        runs = {}
+        for shape in [(512, 256, 4), (512, 128, 2), (512, 256, 8), (256, 256, 4), (1024, 128, 4)]:
+            B.bgv_set_fa2_tune(*shape)
+            f = G.fa2_forces(pos, mass, off, adj, w, p)
+            dv = G.Fa2Device(pos, mass, off, adj, w, p)
+            dv.run(3, True)
+            runs[shape] = (f, dv.state())
+        base_f, base_s = runs[(512, 256, 4)]
+        for shape, (f, st) in runs.items():
+            assert f["interactions"] == base_f["interactions"]
+            assert np.array_equal(f["Fr"], base_f["Fr"]) and np.array_equal(f["Fg"], base_f["Fg"])
+            if shape[0] == 512:  # same attraction grouping: the same trajectory
+                assert np.array_equal(f["Fa"], base_f["Fa"])
+                assert np.array_equal(st[0], base_s[0]) and st[3] == base_s[3]
+            else:
+                assert G.rel_err(f["Fa"], base_f["Fa"]) <= 1e-5
+        with pytest.raises(B.BgvError):
+            B.bgv_set_fa2_tune(300, 256, 4)
+    finally:
+        B.bgv_set_fa2_tune(512, 256, 4)

@@ -127,3 +127,49 @@ def test_full_size_fa2_step_sampled():
     assert G.rel_err(r["Fr"][which], Fr0) <= 1e-3
     Fa0 = oracle.attraction(sg["csr_off"], sg["csr_adj"], sg["csr_w"], pos)
     assert G.rel_err(r["Fa"], Fa0) <= 1e-3
+
+
+@pytest.mark.slow
+def test_full_size_fa2_forces_rmat22x():
+    # One FA2 force evaluation on the whole rmat22x supergraph (3.2 M
+    # supernodes): the interaction total equals the oracle's (same tree and
+    # theta), every repulsion is within 1e-3 of the FP64 oracle, and so is the
+    # attraction over all 68 M CSR entries.
+    n, e, _ = graphgen.load("rmat22x")
+    sg = _oracle_supergraph(e, n, 4, 65536, 1, 3, 0)
+    K = sg["K"]
+    pos = oracle.fa2_init(K, 1)
+    p = FA2Params()
+    r = G.fa2_forces(pos, sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], p)
+    assert r["status"] == 0
+    Fr0, inter0 = oracle.bh_repulsion(pos, sg["mass"], p)
+    assert r["interactions"] == inter0
+    assert G.rel_err(r["Fr"], Fr0) <= 1e-3
+    Fa0 = oracle.attraction(sg["csr_off"], sg["csr_adj"], sg["csr_w"], pos)
+    assert G.rel_err(r["Fa"], Fa0) <= 1e-3
+
+
+@pytest.mark.slow
+def test_fa2_forces_above_the_sort_size_cutoff():
+    # 4.5 M bodies with the sort's cutoff set to 2^22, so it runs 16 keys
+    # per thread.  Uniform positions plus a dense cluster inside one
+    # fine cell; the interaction total and every force against the oracle.
+    rng = np.random.default_rng(45)
+    K = 4_500_000
+    pos = (rng.random((K, 2)) * 4000 - 2000).astype(np.float32)
+    pos[:5000] = (pos[0] + rng.random((5000, 2)) * 0.001).astype(np.float32)
+    mass = rng.integers(1, 5, K).astype(np.uint32)
+    off = np.zeros(K + 1, np.int32)
+    p = FA2Params(theta=1.2, leaf_cap=4)
+    prev = B.bgv_set_sort_cutoff(1 << 22)
+    try:
+        assert K > B.bgv_sort_cutoff()
+        r = G.fa2_forces(pos, mass, off, np.zeros(0, np.int32), np.zeros(0, np.uint32), p)
+    finally:
+        B.bgv_set_sort_cutoff(prev)
+    assert r["status"] == 0
+    Fr0, inter0 = oracle.bh_repulsion(pos, mass, p)
+    assert r["interactions"] == inter0
+    outside = np.ones(K, bool)
+    outside[:5000] = False  # inside the cluster, FP32 cell centres cannot resolve the spacing
+    assert G.rel_err(r["Fr"][outside], Fr0[outside]) <= 1e-3

@@ -9,6 +9,7 @@ import pytest
 
 import graphgen
 import oracle
+from oracle import FA2Params
 
 pytestmark = pytest.mark.gpu
 
@@ -17,6 +18,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import gpu_pipeline as G  # noqa: E402
+
+B = G.B
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -129,3 +132,34 @@ def test_supergraph_flags_bad_labels():
     lab[3] = 10
     sg = G.supergraph(e, 10, lab, oracle.exact_degrees(e, 10), 2, 16, 1)
     assert sg["status"] & G.B.BGV_DEV_BADLABEL
+
+
+@pytest.mark.parametrize("cutoff", [1 << 40, 1 << 12])
+def test_sort_methods_give_the_same_order(cutoff):
+    # The radix sort behind the supergraph and the FA2 tree runs as one
+    # cooperative kernel or as onesweep passes (8 or 16 keys per thread by
+    # the cutoff); every form is the same stable sort, so every output is
+    # identical, and equal to the oracle.
+    e = graphgen.random_graph(30000, 200000, seed=17)
+    n = 30000
+    _, dh = oracle.sketch_degrees(e, n, 4, 2048, 1)
+    lab, _ = oracle.communities(e, n, dh, 3, 8, 2, 0)
+    pos = oracle.fa2_init(n, 5)
+    out = {}
+    prev_m, prev_c = B.bgv_set_sort_method(1), B.bgv_set_sort_cutoff(cutoff)
+    try:
+        for method in (0, 1):
+            B.bgv_set_sort_method(method)
+            sg = G.supergraph(e, n, lab, dh, 4, 2048, 1)
+            f = G.fa2_forces(pos, np.ones(n, np.uint32), np.zeros(n + 1, np.int32), np.zeros(0, np.int32),
+                             np.zeros(0, np.uint32), FA2Params(leaf_cap=2))
+            out[method] = (sg, f)
+    finally:
+        B.bgv_set_sort_method(prev_m)
+        B.bgv_set_sort_cutoff(prev_c)
+    sg0 = oracle.supergraph(e, n, lab, dh, 4, 2048, 1)
+    for method, (sg, f) in out.items():
+        for k in ("node_map", "src", "dst", "w", "mass", "csr_off", "csr_adj", "csr_w"):
+            assert np.array_equal(sg[k], sg0[k]), (method, k)
+    assert out[0][1]["interactions"] == out[1][1]["interactions"]
+    assert np.array_equal(out[0][1]["Fr"], out[1][1]["Fr"])

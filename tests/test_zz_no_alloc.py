@@ -7,13 +7,16 @@ hand the library a workspace.  For them the library keeps the sketch's
 per-node counters in a fixed device array of its own.  This test calls that
 entry point through the C ABI on two graphs in a row (the second call reuses
 the array the first left behind) and checks both results, bit for bit, against
-the workspace entry point bgv_sketch_degrees.  The file is named so pytest
+the workspace entry point bgv_sketch_degrees and against the CPU oracle.  It
+also checks that, without a status pointer, a bad edge comes back as an error
+code, and that the next call starts clean.  The file is named so pytest
 collects it last.
 """
 import numpy as np
 import pytest
 
 import graphgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +49,27 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls():
         assert st == 0 and st0 == 0
         assert np.array_equal(S, S0)
         assert np.array_equal(d, d0)
+        So, do = oracle.sketch_degrees(e, n, rows, width, seed)
+        assert np.array_equal(S, So) and np.array_equal(d, do)
+
+
+def test_noalloc_without_status_pointer_reports_bad_edges():
+    # An endpoint outside [0, n) is caught by the kernel's bounds check and
+    # reported through the entry point's own status word: the call returns
+    # BGV_EDEVICE.  The word is cleared by the next call, which succeeds.
+    n = 100
+    bad = np.array([[0, 1], [2, 3], [5, n + 7], [4, 6]], np.int32)
+    E, m = G.edges_dev(bad)
+    S, d = G.empty(4 * 64, np.uint32), G.empty(n, np.uint32)
+    with pytest.raises(B.BgvError) as ex:
+        B.bgv_sketch_degrees_noalloc(E, m, n, 4, 64, 1, S, d)
+    assert ex.value.code == B.BGV_EDEVICE
+    good = graphgen.random_graph(n, 300, seed=5)
+    E, m = G.edges_dev(good)
+    B.bgv_sketch_degrees_noalloc(E, m, n, 4, 64, 1, S, d)
+    So, do = oracle.sketch_degrees(good, n, 4, 64, 1)
+    assert np.array_equal(G.host(S, np.uint32).reshape(4, 64), So)
+    assert np.array_equal(G.host(d, np.uint32, n), do)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
