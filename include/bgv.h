@@ -450,18 +450,21 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
 
 /* ------------------------------------------------------------------------
  * 7. Autotuners.  The radix sort of the supergraph and ForceAtlas2 stages
- *    runs either as one cooperative kernel for all its passes (method 1,
- *    the default: per pass, digit counts per block chunk, a scan over the
- *    chunks, then a stable scatter; no look-back) or as one onesweep kernel
- *    per pass with decoupled look-back (method 0), which takes 8 keys per
- *    thread up to a size cutoff and 16 above it.  bgv_autotune_sort times
- *    all three forms on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
+ *    runs either as one onesweep kernel per pass with decoupled look-back
+ *    (method 0), 8 keys per thread up to a size cutoff and 16 above it, or
+ *    as one cooperative kernel for all its passes (method 1: per pass, digit
+ *    counts per block chunk, a scan over the chunks, a stable scatter; no
+ *    look-back), or by size (method 2, the default): cooperative for key
+ *    counts in a range, onesweep otherwise.  bgv_autotune_sort times all
+ *    three forms on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
  *    keys with 32-bit values, SplitMix64 of the index), sets the cutoff to
- *    the largest size at which 8 was not slower and the method to the one
- *    that summed less time.  Both are process wide; the cutoff starts at
- *    2^40 (8 keys per thread at every size, which measured faster on GB300);
+ *    the largest size at which 8 was not slower, and the cooperative range
+ *    to the span of sizes where it was faster (method 0 if none).  All are
+ *    process wide; they start at a cutoff of 2^40 (8 keys per thread at every
+ *    size) and a cooperative range of [2^21, 2^23], as measured on GB300;
  *    workspaces stay valid whatever they are.  bgv_set_sort_cutoff and
- *    bgv_set_sort_method set them directly and return the previous value.
+ *    bgv_set_sort_method (0, 1, 2) set them directly and return the previous
+ *    value.
  *    Synchronises `stream` once per timed sort.  The paper has no
  *    counterpart.
  * ---------------------------------------------------------------------- */
@@ -471,27 +474,30 @@ typedef struct bgv_tune_report {
     float ms8[9];           /* median milliseconds, onesweep, 8 keys per thread */
     float ms16[9];          /* median milliseconds, onesweep, 16 keys per thread */
     float ms_coop[9];       /* median milliseconds, cooperative sort */
-    int32_t method;         /* the method now in force: 1 cooperative, 0 onesweep */
+    int32_t method;         /* the method now in force: 0, 1 or 2 (by size) */
     int64_t cutoff;         /* the cutoff now in force */
+    int64_t coop_lo, coop_hi; /* key counts sorted cooperatively under method 2 */
 } bgv_tune_report;
 
 /* bgv_autotune_fa2 picks the launch shapes of the ForceAtlas2 step on the
- * caller's supergraph: the CSR entries per warp range of the attraction
- * (256, 512, 1024), the threads per block of the Barnes-Hut traversal (128,
- * 256) and the blocks per SM of the persistent tail kernel (2, 4, 8; capped
- * at what stays resident).  One shape at a time, it times whole steps (the
- * median of three after a warm-up step) from positions `pos` (device, not
- * changed: steps run on a copy in `ws`, with Fprev = 0 and speed 1), keeps
- * the fastest, and leaves the choice in force for the process.  The traversal
- * and tail shapes do not change any result; the attraction range changes the
- * grouping of its FP32 row sums (within rounding).  Synchronises `stream`.
- * bgv_set_fa2_tune sets the shapes directly (BGV_EINVAL for other values). */
+ * caller's supergraph: the longest CSR rows the attraction sums one lane
+ * each (8, 16, 32; longer rows take a warp each, or a block above 4,096
+ * entries), the threads per block of the Barnes-Hut traversal (128, 256) and
+ * the blocks per SM of the persistent tail kernel (2, 4, 8; capped at what
+ * stays resident).  One shape at a time, it times whole steps (the median of
+ * three after a warm-up step) from positions `pos` (device, not changed:
+ * steps run on a copy in `ws`, with Fprev = 0 and speed 1), keeps the
+ * fastest, and leaves the choice in force for the process.  The traversal
+ * and tail shapes do not change any result; the row split of the attraction
+ * changes the grouping of some FP32 row sums (within rounding).
+ * Synchronises `stream`.  bgv_set_fa2_tune sets the shapes directly
+ * (BGV_EINVAL for other values). */
 typedef struct bgv_fa2_tune_report {
-    int32_t att_range;          /* chosen CSR entries per attraction warp range */
+    int32_t att_short;          /* chosen: longest rows summed one lane each */
     int32_t repulse_threads;    /* chosen threads per block of the traversal */
     int32_t tail_blocks_per_sm; /* chosen blocks per SM of the step's tail */
     int32_t reserved;
-    float ms_att_range[3];      /* median step ms at 256, 512, 1024 entries */
+    float ms_att_short[3];      /* median step ms at 8, 16, 32 */
     float ms_repulse_threads[2];/* at 128, 256 threads */
     float ms_tail_blocks[3];    /* at 2, 4, 8 blocks per SM */
 } bgv_fa2_tune_report;
@@ -500,7 +506,7 @@ size_t bgv_autotune_fa2_ws_size(int64_t K, int64_t nnz);
 int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
                      const uint32_t *mass, const bgv_fa2_params *p, const float *pos, bgv_fa2_tune_report *out,
                      void *ws, size_t ws_bytes, void *stream);
-int bgv_set_fa2_tune(int32_t att_range, int32_t repulse_threads, int32_t tail_blocks_per_sm);
+int bgv_set_fa2_tune(int32_t att_short, int32_t repulse_threads, int32_t tail_blocks_per_sm);
 
 size_t bgv_autotune_sort_ws_size(int64_t max_keys);
 int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t ws_bytes, void *stream);

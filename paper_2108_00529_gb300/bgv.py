@@ -39,7 +39,7 @@ class bgv_fa2_stats(C.Structure):
 
 class bgv_tune_report(C.Structure):
     _fields_ = [("count", i32), ("sizes_log2", i32 * 9), ("ms8", C.c_float * 9), ("ms16", C.c_float * 9),
-                ("ms_coop", C.c_float * 9), ("method", i32), ("cutoff", i64)]
+                ("ms_coop", C.c_float * 9), ("method", i32), ("cutoff", i64), ("coop_lo", i64), ("coop_hi", i64)]
 
 
 class bgv_layout_params(C.Structure):
@@ -105,8 +105,8 @@ _sig("bgv_fa2_run_batched", C.c_int, [i32, P, i64, P, P, P, P, C.POINTER(bgv_fa2
                                       sz, P])
 
 class bgv_fa2_tune_report(C.Structure):
-    _fields_ = [("att_range", i32), ("repulse_threads", i32), ("tail_blocks_per_sm", i32), ("reserved", i32),
-                ("ms_att_range", C.c_float * 3), ("ms_repulse_threads", C.c_float * 2),
+    _fields_ = [("att_short", i32), ("repulse_threads", i32), ("tail_blocks_per_sm", i32), ("reserved", i32),
+                ("ms_att_short", C.c_float * 3), ("ms_repulse_threads", C.c_float * 2),
                 ("ms_tail_blocks", C.c_float * 3)]
 
 
@@ -488,11 +488,12 @@ def bgv_autotune_fa2(K, nnz, csr_off, csr_adj, csr_w, mass, params, pos, ws, ws_
     return r
 
 
-def bgv_set_fa2_tune(att_range: int, repulse_threads: int, tail_blocks_per_sm: int):
-    _chk(_lib.bgv_set_fa2_tune(att_range, repulse_threads, tail_blocks_per_sm), "bgv_set_fa2_tune")
+def bgv_set_fa2_tune(att_short: int, repulse_threads: int, tail_blocks_per_sm: int):
+    _chk(_lib.bgv_set_fa2_tune(att_short, repulse_threads, tail_blocks_per_sm), "bgv_set_fa2_tune")
 
 
 def bgv_set_sort_method(method: int) -> int:
-    """1: all radix passes in one cooperative kernel, 0: onesweep passes with
-    decoupled look-back; returns the previous method."""
+    """0: onesweep passes with decoupled look-back, 1: all radix passes in one
+    cooperative kernel, 2: cooperative for key counts in the tuned range;
+    returns the previous method."""
     return int(_lib.bgv_set_sort_method(method))

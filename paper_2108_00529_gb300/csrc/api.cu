@@ -976,8 +976,8 @@ size_t bgv_autotune_fa2_ws_size(int64_t K, int64_t nnz) {
     return c.used();
 }
 
-int bgv_set_fa2_tune(int32_t att_range, int32_t repulse_threads, int32_t tail_blocks_per_sm) {
-    return set_fa2_tune(Fa2Tune{att_range, repulse_threads, tail_blocks_per_sm});
+int bgv_set_fa2_tune(int32_t att_short, int32_t repulse_threads, int32_t tail_blocks_per_sm) {
+    return set_fa2_tune(Fa2Tune{att_short, repulse_threads, tail_blocks_per_sm});
 }
 
 int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
@@ -1025,15 +1025,15 @@ int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32
     bgv_fa2_tune_report r;
     memset(&r, 0, sizeof(r));
     Fa2Tune best = fa2_tune();
-    const int ranges[3] = {256, 512, 1024}, threads[2] = {128, 256}, tails[3] = {2, 4, 8};
+    const int shorts[3] = {8, 16, 32}, threads[2] = {128, 256}, tails[3] = {2, 4, 8};
     int rc = BGV_OK;
     float best_ms = 0.0f;
     for (int i = 0; i < 3 && rc == BGV_OK; ++i) {
         Fa2Tune t = best;
-        t.att_range = ranges[i];
+        t.att_short = shorts[i];
         set_fa2_tune(t);
-        rc = time_steps(&r.ms_att_range[i]);
-        if (rc == BGV_OK && (i == 0 || r.ms_att_range[i] < best_ms)) best_ms = r.ms_att_range[i], best.att_range = ranges[i];
+        rc = time_steps(&r.ms_att_short[i]);
+        if (rc == BGV_OK && (i == 0 || r.ms_att_short[i] < best_ms)) best_ms = r.ms_att_short[i], best.att_short = shorts[i];
     }
     for (int i = 0; i < 2 && rc == BGV_OK; ++i) {
         Fa2Tune t = best;
@@ -1055,7 +1055,7 @@ int bgv_autotune_fa2(int64_t K, int64_t nnz, const int32_t *csr_off, const int32
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BGV_TRY(rc);
-    r.att_range = best.att_range;
+    r.att_short = best.att_short;
     r.repulse_threads = best.repulse_threads;
     r.tail_blocks_per_sm = best.tail_blocks_per_sm;
     if (out) *out = r;
@@ -1083,6 +1083,7 @@ int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t w
                           &count, &method));
     r.count = count;
     r.method = method;
+    sort_coop_range(&r.coop_lo, &r.coop_hi);
     r.cutoff = sort_cutoff();
     if (out) *out = r;
     return BGV_OK;
@@ -1096,7 +1097,7 @@ int64_t bgv_set_sort_cutoff(int64_t cutoff) {
 }
 
 int32_t bgv_set_sort_method(int32_t method) {
-    if (method != 0 && method != 1) return -1;
+    if (method < 0 || method > 2) return -1;
     return set_sort_method(method);
 }
 

@@ -176,18 +176,21 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const i
 // Sort autotuner: times the onesweep passes at 8 and at 16 keys per thread
 // and the cooperative sort for 2^14, 2^16, ... up to max_keys; sets the
 // cutoff between 8 and 16 (the largest size at which 8 was not slower) and
-// the method that summed less time, for the whole process.  Per size k
-// (count of them in *count): ms8[k], ms16[k], ms_coop[k], sizes_log2[k]
-// (host arrays, may be NULL; 9 entries suffice); *method: 1 cooperative, 0
-// onesweep.  b must hold max_keys pairs.
+// the span of sizes where the cooperative sort was faster (method 2), or
+// onesweep everywhere (method 0), for the whole process.  Per size k (count
+// of them in *count): ms8[k], ms16[k], ms_coop[k], sizes_log2[k] (host
+// arrays, may be NULL; 9 entries suffice).  b must hold max_keys pairs.
 int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
                   float *ms_coop, int32_t *sizes_log2, int32_t *count, int32_t *method);
 int64_t sort_cutoff();
 int64_t set_sort_cutoff(int64_t cutoff);  // returns the previous cutoff
-// 1: all passes in one cooperative kernel (default), 0: onesweep passes with
-// decoupled look-back.  Process wide; returns the previous method.
+// 0: onesweep passes with decoupled look-back, 1: all passes in one
+// cooperative kernel, 2 (default): cooperative for key counts in the range
+// sort_coop_range gives, onesweep otherwise.  Process wide; returns the
+// previous method.
 int set_sort_method(int method);
 int sort_method();
+void sort_coop_range(int64_t *lo, int64_t *hi);
 
 
 
@@ -322,12 +325,13 @@ int run_supergraph(const int32_t *edges, int64_t m, int32_t n, const int32_t *la
                    uint32_t *csr_w, uint64_t *vol, uint32_t *count, int32_t *comm_label,
                    const SuperScratch &s, uint32_t *status, cudaStream_t st, const BatchView *batch = nullptr);
 
-// Launch shapes of a FA2 step (process wide; chosen by the autotuner):
-// CSR entries per attraction warp range (256, 512, 1024), threads per block
-// of the Barnes-Hut traversal (128, 256), blocks per SM of the persistent
-// tail kernel (1..8, at most what stays resident).
+// Launch shapes of a FA2 step (process wide; chosen by the autotuner): the
+// longest rows the attraction sums one lane each (8, 16, 32; longer ones take
+// a warp or a block), threads per block of the Barnes-Hut traversal (128,
+// 256), blocks per SM of the persistent tail kernel (1..8, at most what
+// stays resident).
 struct Fa2Tune {
-    int att_range, repulse_threads, tail_blocks_per_sm;
+    int att_short, repulse_threads, tail_blocks_per_sm;
 };
 Fa2Tune fa2_tune();
 int set_fa2_tune(const Fa2Tune &t);

@@ -22,11 +22,10 @@
 //               subtree, open -> next element); every body takes its own
 //               opening decisions, so its interaction set is exactly the
 //               one the definition gives
-//   k_attract   attraction over fixed 512-entry ranges of the CSR, one warp
-//               per range (balanced whatever the degrees): segmented scan by
-//               row, row pieces kept per range; k_long_rows sums the rows
-//               spread over many ranges.  Both run on a second stream while
-//               the tree is built and walked.
+//   k_att_*     attraction, rows by length class: short rows one lane
+//               each, medium rows one warp each, long rows one block each
+//               (the class lists are made once per CSR).  They run on a
+//               second stream while the tree is built and walked.
 //   k_tail      one persistent kernel (cooperative launch, bounded grid
 //               barriers): per node gravity, total force, swing and
 //               traction, summed exactly (integer accumulation); the global
@@ -739,311 +738,187 @@ __global__ void __launch_bounds__(kRT) k_repulse(const float4 *__restrict__ geo,
 }
 
 // ------------------------------------------------------------ attraction
-// The CSR entries are cut into fixed ranges of `range` consecutive entries,
-// one warp per range whatever the row lengths (a hub row spreads over many
-// warps, short rows share one).  The warp takes its range kStep entries at a
-// time, 4 consecutive entries per lane: 16-byte loads of the neighbours and
-// weights, gathers of the positions, w_ij (p_j - p_i), sums of the row runs
-// inside the lane, then a segmented inclusive scan over the lanes by row
-// (rows ascend along the entries), with the partial sum of the row still
-// open at the last lane carried to the next step.  A row that starts and ends inside the range is written to `full`;
-// the piece of a row that continues past the range goes to tail[range], the
-// piece of a row that began before it to head[range].  k_node adds a row's
-// pieces in range order, so every sum has a fixed order.
-constexpr int kChunk = 8;     // entries per plan record
-constexpr int kRangeMin = 256;   // entries per warp range: 256, 512 or 1024 (process-wide, tuned)
-constexpr int kLaneEntries = 4;                 // consecutive entries per lane and step
-constexpr int kStep = 32 * kLaneEntries;
+// F^a_i = sum over row i's CSR entries (j, w) of w (p_j - p_i), in FP32.
+// Every row is summed by one worker in an order that depends only on the
+// row's own entries (deterministic, and the same whatever else the CSR
+// holds).  The plan, made once per CSR, lists the rows by length: short rows
+// (at most `att_short` entries) take one lane each, 32 rows to a warp, and
+// add their entries in order; medium rows (up to kAttMedium entries) take
+// one warp each: lane l adds entries l, l + 32, ... in order, then a fixed
+// butterfly; long rows take one block each (thread t adds t, t + 256, ...,
+// then a fixed tree).  Every worker first issues kAttIn loads of neighbour
+// ids and weights, then their position gathers, so they are in flight
+// together.  An empty row is a short row of sum 0.
+constexpr int kAttMedium = 4096;
+constexpr int kAttIn = 8;
 
-// The plan, written once per CSR:
-//   chunk_row[g]   row of entry 8g (the thread of row r writes r into every
-//                  chunk that starts inside the row; a warp shares the writes
-//                  of rows that cover many chunks);
-//   chunk_meta[g]  byte k (1..7): row of entry 8g + k minus chunk_row[g], or
-//                  kMetaWalk in byte 0 when a gap between rows (empty rows)
-//                  exceeds 255 inside the chunk: those entries find their
-//                  row by binary search on the offsets;
-//   long_rows      the rows spread over more than kLongRowRanges ranges.
-constexpr int kLongRowRanges = 8;
-constexpr unsigned kMetaWalk = 4u;
-
-__global__ void __launch_bounds__(kThreads) k_chunk_rows(int64_t K, int64_t nnz, int range,
-                                                         const int32_t *__restrict__ off,
-                                                         int32_t *__restrict__ chunk_row, int32_t *__restrict__ long_rows,
-                                                         int32_t *long_count) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); base < K; base += stride) {
-        const int64_t r = base + lane;
-        int64_t g0 = 0, g1 = 0;
-        bool spread = false;
-        if (r < K) {
-            const int64_t b = off[r], e = off[r + 1] < nnz ? off[r + 1] : nnz;
-            g0 = (b + kChunk - 1) / kChunk;
-            g1 = (e + kChunk - 1) / kChunk;
-            spread = e > b && (e - 1) / range - b / range > kLongRowRanges;
-        }
-        if (spread) long_rows[atomicAdd(long_count, 1)] = int32_t(r);
-        const bool longrow = g1 - g0 > 32;
-        if (!longrow)
-            for (int64_t g = g0; g < g1; ++g) chunk_row[g] = int32_t(r);
-        unsigned lm = __ballot_sync(0xFFFFFFFFu, longrow);
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int64_t a = __shfl_sync(0xFFFFFFFFu, g0, src), z = __shfl_sync(0xFFFFFFFFu, g1, src);
-            for (int64_t g = a + lane; g < z; g += 32) chunk_row[g] = int32_t(base + src);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_chunk_meta(int64_t K, int64_t nnz, const int32_t *__restrict__ off,
-                                                         const int32_t *__restrict__ chunk_row,
-                                                         unsigned long long *__restrict__ chunk_meta) {
-    const int64_t chunks = (nnz + kChunk - 1) / kChunk;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < chunks; g += stride) {
-        const int64_t e0 = g * kChunk, e1 = e0 + kChunk < nnz ? e0 + kChunk : nnz;
-        const int64_t r0 = chunk_row[g];
-        unsigned long long meta = 0;
-        int64_t r = r0;
-        for (int64_t e = e0 + 1; e < e1; ++e) {
-            while (r + 1 < K && e >= off[r + 1]) ++r;
-            const int64_t d = r - r0;
-            if (d > 255) meta |= kMetaWalk;
-            meta |= static_cast<unsigned long long>(d > 255 ? 255 : d) << (8 * (e - e0));
-        }
-        chunk_meta[g] = meta;
-    }
-}
-
-// Row of CSR entry e from the plan (binary search in the rare chunks that
-// span long runs of empty rows).
-__device__ __forceinline__ int32_t entry_row(int64_t e, int64_t K, const int32_t *__restrict__ off,
-                                             const int32_t *__restrict__ chunk_row,
-                                             const unsigned long long *__restrict__ chunk_meta) {
-    const int64_t g = e / kChunk;
-    const int32_t r0 = chunk_row[g];
-    const unsigned long long meta = chunk_meta[g];
-    if (!(meta & kMetaWalk)) {
-        const int k = int(e - g * kChunk);
-        return r0 + int32_t(k ? unsigned(meta >> (8 * k)) & 0xFFu : 0u);
-    }
-    int64_t lo = r0, hi = K - 1;  // the largest r with off[r] <= e
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    return int32_t(lo);
-}
-
-__device__ __forceinline__ void put_piece(bool first, bool last, bool began, bool goes_on, int64_t q, int32_t row,
-                                          float x, float y, float2 *full, float2 *head, float2 *tail) {
-    const float2 v = make_float2(x, y);
-    if (first && began) head[q] = v;
-    else if (last && goes_on) tail[q] = v;
-    else full[row] = v;
-}
-
-// One lane's kLaneEntries consecutive entries of a step (one plan chunk):
-// neighbours, weights and rows; nv of them exist.
-struct LaneEntries {
-    int32_t j[kLaneEntries], r[kLaneEntries];
-    uint32_t wt[kLaneEntries];
-    int nv;
-};
-
-__device__ __forceinline__ void load_lane(int64_t b, int64_t e1, int lane, int64_t K, const int32_t *__restrict__ off,
-                                          const int32_t *__restrict__ chunk_row,
-                                          const unsigned long long *__restrict__ chunk_meta,
-                                          const int32_t *__restrict__ adj, const uint32_t *__restrict__ w, bool vec,
-                                          LaneEntries &le) {
-    const int64_t ea = b + int64_t(lane) * kLaneEntries;
-    const int nv = ea >= e1 ? 0 : (e1 - ea < kLaneEntries ? int(e1 - ea) : kLaneEntries);
-    le.nv = nv;
-    if (nv == kLaneEntries && vec) {
-        const int4 a4 = __ldcs(reinterpret_cast<const int4 *>(adj + ea));
-        const uint4 w4 = __ldcs(reinterpret_cast<const uint4 *>(w + ea));
-        le.j[0] = a4.x; le.j[1] = a4.y; le.j[2] = a4.z; le.j[3] = a4.w;
-        le.wt[0] = w4.x; le.wt[1] = w4.y; le.wt[2] = w4.z; le.wt[3] = w4.w;
-    } else {
-#pragma unroll
-        for (int k = 0; k < kLaneEntries; ++k) {
-            le.j[k] = k < nv ? __ldcs(adj + ea + k) : -1;
-            le.wt[k] = k < nv ? __ldcs(w + ea + k) : 0u;
-        }
-    }
-    if (nv > 0) {
-        const int64_t g = ea / kChunk;
-        const int32_t r0 = chunk_row[g];
-        const unsigned long long meta = chunk_meta[g];
-        const int k0 = int(ea - g * kChunk);
-#pragma unroll
-        for (int k = 0; k < kLaneEntries; ++k) {
-            const int kk = k0 + k;
-            le.r[k] = (meta & kMetaWalk) ? (k < nv ? entry_row(ea + k, K, off, chunk_row, chunk_meta) : r0)
-                                         : r0 + int32_t(kk ? unsigned(meta >> (8 * kk)) & 0xFFu : 0u);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kLaneEntries; ++k) le.r[k] = INT32_MAX;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_attract(int64_t K, int64_t nnz, int range, const int32_t *__restrict__ off,
-                                                      const int32_t *__restrict__ chunk_row,
-                                                      const unsigned long long *__restrict__ chunk_meta,
-                                                      const int32_t *__restrict__ adj,
-                                                      const uint32_t *__restrict__ w, const float2 *__restrict__ pos,
-                                                      float2 *__restrict__ full, float2 *__restrict__ head,
-                                                      float2 *__restrict__ tail) {
-    const int lane = threadIdx.x & 31;
-    const int64_t ranges = (nnz + range - 1) / range;
-    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const bool vec = ((reinterpret_cast<uintptr_t>(adj) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
-    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < ranges; q += warps) {
-        const int64_t e0 = q * range, e1 = e0 + range < nnz ? e0 + range : nnz;
-        const int32_t row_first = entry_row(e0, K, off, chunk_row, chunk_meta);
-        const int32_t row_last = entry_row(e1 - 1, K, off, chunk_row, chunk_meta);
-        const bool began = off[row_first] < e0;
-        const bool goes_on = off[row_last + 1] > e1;
-        int32_t crow = -1;  // row open at the end of the previous step, and its sum
-        float cx = 0.0f, cy = 0.0f;
-        LaneEntries le;
-        load_lane(e0, e1, lane, K, off, chunk_row, chunk_meta, adj, w, vec, le);
-        for (int64_t b = e0; b < e1; b += kStep) {
-            // the next step's entries are requested before this step's work
-            LaneEntries nxt;
-            if (b + kStep < e1) load_lane(b + kStep, e1, lane, K, off, chunk_row, chunk_meta, adj, w, vec, nxt);
-            const int nv = le.nv;
-            float vx[kLaneEntries], vy[kLaneEntries];
-#pragma unroll
-            for (int k = 0; k < kLaneEntries; ++k) {
-                vx[k] = 0.0f;
-                vy[k] = 0.0f;
-                if (k < nv && static_cast<uint64_t>(le.j[k]) < static_cast<uint64_t>(K)) {  // else an invalid entry
-                    const float2 pj = pos[le.j[k]], pi = pos[le.r[k]];
-                    const float wf = __uint2float_rn(le.wt[k]);
-                    vx[k] = wf * (pj.x - pi.x);
-                    vy[k] = wf * (pj.y - pi.y);
-                }
-            }
-            // In-lane runs: the first row's run (ra, pa), rows complete inside
-            // the lane (written at once), the last row's run (rb, pb).
-            const int32_t ra = le.r[0];
-            int32_t rb = INT32_MAX;
-#pragma unroll
-            for (int k = 0; k < kLaneEntries; ++k)
-                if (k < nv) rb = le.r[k];
-            float pax = 0.0f, pay = 0.0f, pbx = 0.0f, pby = 0.0f;
-            {
-                int32_t cur = ra;
-                float ax = 0.0f, ay = 0.0f;
-#pragma unroll
-                for (int k = 0; k < kLaneEntries; ++k) {
-                    if (k < nv) {
-                        if (le.r[k] != cur) {
-                            if (cur == ra) {
-                                pax = ax;
-                                pay = ay;
-                            } else {
-                                put_piece(false, false, began, goes_on, q, cur, ax, ay, full, head, tail);
-                            }
-                            cur = le.r[k];
-                            ax = 0.0f;
-                            ay = 0.0f;
-                        }
-                        ax += vx[k];
-                        ay += vy[k];
-                    }
-                }
-                pbx = ax;
-                pby = ay;
-            }
-            // the carried row ended with the previous step: emit it
-            const int32_t ra0 = __shfl_sync(0xFFFFFFFFu, ra, 0);
-            if (crow >= 0 && ra0 != crow) {
-                if (lane == 0) put_piece(crow == row_first, false, began, goes_on, q, crow, cx, cy, full, head, tail);
-                crow = -1;
-            }
-            // segmented inclusive scan of the last runs by row (rows ascend
-            // along the lanes, so equal rows are one segment)
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float ox = __shfl_up_sync(0xFFFFFFFFu, pbx, d), oy = __shfl_up_sync(0xFFFFFFFFu, pby, d);
-                const int32_t orow = __shfl_up_sync(0xFFFFFFFFu, rb, d);
-                if (lane >= d && orow == rb) {
-                    pbx += ox;
-                    pby += oy;
-                }
-            }
-            if (rb == crow) {  // the leading lanes continue the carried row
-                pbx = cx + pbx;
-                pby = cy + pby;
-            }
-            // a lane whose first run closes inside it takes what precedes it
-            int32_t prb = __shfl_up_sync(0xFFFFFFFFu, rb, 1);
-            float ppx = __shfl_up_sync(0xFFFFFFFFu, pbx, 1), ppy = __shfl_up_sync(0xFFFFFFFFu, pby, 1);
-            if (lane == 0) {
-                prb = crow;
-                ppx = cx;
-                ppy = cy;
-            }
-            if (nv > 0 && ra != rb) {
-                const bool cont = prb == ra;
-                put_piece(ra == row_first, false, began, goes_on, q, ra, cont ? ppx + pax : pax,
-                          cont ? ppy + pay : pay, full, head, tail);
-            }
-            const int L = int((e1 - 1 - b) / kLaneEntries < 31 ? (e1 - 1 - b) / kLaneEntries : 31);  // last valid lane
-            const int32_t nra = __shfl_down_sync(0xFFFFFFFFu, ra, 1);
-            if (lane < L && nra != rb)
-                put_piece(rb == row_first, false, began, goes_on, q, rb, pbx, pby, full, head, tail);
-            crow = __shfl_sync(0xFFFFFFFFu, rb, L);
-            cx = __shfl_sync(0xFFFFFFFFu, pbx, L);
-            cy = __shfl_sync(0xFFFFFFFFu, pby, L);
-            le = nxt;
-        }
-        if (lane == 0) put_piece(crow == row_first, true, began, goes_on, q, crow, cx, cy, full, head, tail);
-    }
-}
-
-// Rows spread over more than kLongRowRanges ranges, one block of
-// kLongThreads each: the threads add strided subsets of the row's middle
-// pieces in range order, the warps a fixed butterfly, thread 0 the warp sums
-// in order after the row's first piece.  k_node reads the result from
-// full[].
-constexpr int kLongThreads = 128;
-
-__global__ void __launch_bounds__(kLongThreads) k_long_rows(int range, const int32_t *__restrict__ off,
-                                                            const int32_t *__restrict__ long_rows,
-                                                            const int32_t *__restrict__ long_count,
-                                                            const float2 *__restrict__ head,
-                                                            const float2 *__restrict__ tail,
-                                                            float2 *__restrict__ full) {
-    __shared__ float2 wsum[kLongThreads / 32];
+// Block-aggregated append of row r to the list of class c (one atomic per
+// class per block).
+__global__ void __launch_bounds__(kThreads) k_att_plan(int64_t K, const int32_t *__restrict__ off, int att_short,
+                                                       int32_t *__restrict__ rows_short, int32_t *__restrict__ rows_med,
+                                                       int32_t *__restrict__ rows_long, uint32_t *counts) {
+    __shared__ uint32_t wn[3][kThreads / 32], base[3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t count = *long_count;
-    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
-        const int32_t r = long_rows[q];
-        const int64_t a = off[r] / range, z = (off[r + 1] - 1) / range;
-        float px = 0.0f, py = 0.0f;
-        for (int64_t g = a + 1 + threadIdx.x; g <= z; g += kLongThreads) {
-            const float2 v = head[g];
-            px += v.x;
-            py += v.y;
+    for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x; r0 < K; r0 += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = r0 + threadIdx.x;
+        int c = -1;
+        if (r < K) {
+            const int64_t len = int64_t(off[r + 1]) - off[r];
+            c = len <= att_short ? 0 : (len <= kAttMedium ? 1 : 2);
+        }
+        unsigned m[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            m[k] = __ballot_sync(0xFFFFFFFFu, c == k);
+            if (lane == 0) wn[k][warp] = uint32_t(__popc(m[k]));
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int k = threadIdx.x;
+            uint32_t t = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t x = wn[k][w];
+                wn[k][w] = t;
+                t += x;
+            }
+            base[k] = t ? atomicAdd(&counts[k], t) : 0u;
+        }
+        __syncthreads();
+        if (c >= 0) {
+            int32_t *list = c == 0 ? rows_short : (c == 1 ? rows_med : rows_long);
+            list[base[c] + wn[c][warp] + __popc(m[c] & ((1u << lane) - 1u))] = int32_t(r);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool valid_row(int32_t j, int64_t K) {
+    return static_cast<uint64_t>(int64_t(j)) < static_cast<uint64_t>(K);  // an invalid entry adds nothing
+}
+
+// Short rows: one lane each.
+__global__ void __launch_bounds__(kThreads) k_att_short(int64_t K, const int32_t *__restrict__ off,
+                                                        const int32_t *__restrict__ adj,
+                                                        const uint32_t *__restrict__ w,
+                                                        const float2 *__restrict__ pos,
+                                                        const int32_t *__restrict__ rows, const uint32_t *counts,
+                                                        float2 *__restrict__ full) {
+    const int64_t count = counts[0];
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const int32_t r = rows[q];
+        const int64_t b = off[r], e = off[r + 1];
+        const float2 pi = pos[r];
+        float ax = 0.0f, ay = 0.0f;
+        for (int64_t e0 = b; e0 < e; e0 += kAttIn) {
+            int32_t j[kAttIn];
+            uint32_t wt[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                j[k] = e0 + k < e ? __ldcs(adj + e0 + k) : -1;
+                wt[k] = e0 + k < e ? __ldcs(w + e0 + k) : 0u;
+            }
+            float2 pj[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) pj[k] = valid_row(j[k], K) ? pos[j[k]] : pi;
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                const float wf = valid_row(j[k], K) ? __uint2float_rn(wt[k]) : 0.0f;
+                ax += wf * (pj[k].x - pi.x);
+                ay += wf * (pj[k].y - pi.y);
+            }
+        }
+        full[r] = make_float2(ax, ay);
+    }
+}
+
+// Medium rows: one warp each.
+__global__ void __launch_bounds__(kThreads) k_att_medium(int64_t K, const int32_t *__restrict__ off,
+                                                         const int32_t *__restrict__ adj,
+                                                         const uint32_t *__restrict__ w,
+                                                         const float2 *__restrict__ pos,
+                                                         const int32_t *__restrict__ rows, const uint32_t *counts,
+                                                         float2 *__restrict__ full) {
+    const int lane = threadIdx.x & 31;
+    const int64_t count = counts[1];
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < count; q += warps) {
+        const int32_t r = rows[q];
+        const int64_t b = off[r], e = off[r + 1];
+        const float2 pi = pos[r];
+        float ax = 0.0f, ay = 0.0f;
+        for (int64_t e0 = b + lane; e0 < e; e0 += 32 * kAttIn) {
+            int32_t j[kAttIn];
+            uint32_t wt[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                const int64_t x = e0 + 32 * k;
+                j[k] = x < e ? __ldcs(adj + x) : -1;
+                wt[k] = x < e ? __ldcs(w + x) : 0u;
+            }
+            float2 pj[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) pj[k] = valid_row(j[k], K) ? pos[j[k]] : pi;
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                const float wf = valid_row(j[k], K) ? __uint2float_rn(wt[k]) : 0.0f;
+                ax += wf * (pj[k].x - pi.x);
+                ay += wf * (pj[k].y - pi.y);
+            }
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            px += __shfl_xor_sync(0xFFFFFFFFu, px, d);
-            py += __shfl_xor_sync(0xFFFFFFFFu, py, d);
+            ax += __shfl_xor_sync(0xFFFFFFFFu, ax, d);
+            ay += __shfl_xor_sync(0xFFFFFFFFu, ay, d);
         }
-        if (lane == 0) wsum[warp] = make_float2(px, py);
+        if (lane == 0) full[r] = make_float2(ax, ay);
+    }
+}
+
+// Long rows: one block each.
+__global__ void __launch_bounds__(kThreads) k_att_long(int64_t K, const int32_t *__restrict__ off,
+                                                       const int32_t *__restrict__ adj, const uint32_t *__restrict__ w,
+                                                       const float2 *__restrict__ pos, const int32_t *__restrict__ rows,
+                                                       const uint32_t *counts, float2 *__restrict__ full) {
+    __shared__ float2 wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t count = counts[2];
+    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
+        const int32_t r = rows[q];
+        const int64_t b = off[r], e = off[r + 1];
+        const float2 pi = pos[r];
+        float ax = 0.0f, ay = 0.0f;
+        for (int64_t e0 = b + threadIdx.x; e0 < e; e0 += int64_t(kThreads) * kAttIn) {
+            int32_t j[kAttIn];
+            uint32_t wt[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                const int64_t x = e0 + int64_t(kThreads) * k;
+                j[k] = x < e ? __ldcs(adj + x) : -1;
+                wt[k] = x < e ? __ldcs(w + x) : 0u;
+            }
+            float2 pj[kAttIn];
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) pj[k] = valid_row(j[k], K) ? pos[j[k]] : pi;
+#pragma unroll
+            for (int k = 0; k < kAttIn; ++k) {
+                const float wf = valid_row(j[k], K) ? __uint2float_rn(wt[k]) : 0.0f;
+                ax += wf * (pj[k].x - pi.x);
+                ay += wf * (pj[k].y - pi.y);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            ax += __shfl_xor_sync(0xFFFFFFFFu, ax, d);
+            ay += __shfl_xor_sync(0xFFFFFFFFu, ay, d);
+        }
+        if (lane == 0) wsum[warp] = make_float2(ax, ay);
         __syncthreads();
         if (threadIdx.x == 0) {
-            float2 t = tail[a];
-            for (int w = 0; w < kLongThreads / 32; ++w) {
-                t.x += wsum[w].x;
-                t.y += wsum[w].y;
+            float2 t = wsum[0];
+            for (int k = 1; k < kThreads / 32; ++k) {
+                t.x += wsum[k].x;
+                t.y += wsum[k].y;
             }
             full[r] = t;
         }
@@ -1193,33 +1068,10 @@ __device__ __forceinline__ float2 swing_traction(float m, float fx, float fy, fl
 // block per graph sums that graph's rows, then a second barrier); then per
 // node the local speed and the displacement, Fprev = F.  The barrier waits
 // are bounded and report BGV_DEV_TIMEOUT.
-// The attraction of row i from the pieces k_attract / k_long_rows left:
-// rows over many ranges (or inside one) in full[], the others as the tail
-// piece of their first range plus the head pieces of the next ones, added in
-// range order.  off == nullptr: no CSR entries, no attraction.
-struct AttPieces {
-    const int32_t *off;
-    const float2 *full, *head, *tail;
-    int range;
-};
-__device__ __forceinline__ float2 attraction_of(int64_t i, const AttPieces &a) {
-    if (!a.off) return make_float2(0.0f, 0.0f);
-    const int64_t b = a.off[i], e = a.off[i + 1];
-    if (e <= b) return make_float2(0.0f, 0.0f);
-    const int64_t g1 = b / a.range, g2 = (e - 1) / a.range;
-    if (g1 == g2 || g2 - g1 > kLongRowRanges) return a.full[i];
-    float2 v = a.tail[g1];
-    for (int64_t g = g1 + 1; g <= g2; ++g) {
-        const float2 h = a.head[g];
-        v.x += h.x;
-        v.y += h.y;
-    }
-    return v;
-}
-
-__device__ __forceinline__ float2 node_force(int64_t i, const AttPieces &att, float m, float2 pi, float2 fr, float kg,
-                                             int strong) {
-    const float2 fa = attraction_of(i, att);
+// full == nullptr: no CSR entries, no attraction.
+__device__ __forceinline__ float2 node_force(int64_t i, const float2 *__restrict__ full, float m, float2 pi, float2 fr,
+                                             float kg, int strong) {
+    const float2 fa = full ? full[i] : make_float2(0.0f, 0.0f);
     float gx, gy;
     if (strong) {
         gx = -kg * m * pi.x;
@@ -1244,7 +1096,7 @@ __device__ __forceinline__ float2 displaced(float2 p, float2 f, float2 fp, float
 }
 
 // Forces only (no state change): repulsion, attraction and gravity per node.
-__global__ void __launch_bounds__(kThreads) k_node(int64_t K, const AttPieces att,
+__global__ void __launch_bounds__(kThreads) k_node(int64_t K, const float2 *__restrict__ att,
                                                    const uint32_t *__restrict__ mass, const float2 *__restrict__ pos,
                                                    const float2 *__restrict__ Frep, float kg, int strong,
                                                    float2 *__restrict__ Fr_out, float2 *__restrict__ Fa_out,
@@ -1254,15 +1106,12 @@ __global__ void __launch_bounds__(kThreads) k_node(int64_t K, const AttPieces at
         const float m = __uint2float_rn(mass[i]);
         const float2 pi = pos[i];
         if (Fr_out) Fr_out[i] = Frep[i];
-        if (Fa_out) Fa_out[i] = attraction_of(i, att);
-        if (Fg_out) {
-            const AttPieces none = {nullptr, nullptr, nullptr, nullptr, 0};
-            Fg_out[i] = node_force(i, none, m, pi, make_float2(0.0f, 0.0f), kg, strong);
-        }
+        if (Fa_out) Fa_out[i] = att ? att[i] : make_float2(0.0f, 0.0f);
+        if (Fg_out) Fg_out[i] = node_force(i, nullptr, m, pi, make_float2(0.0f, 0.0f), kg, strong);
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const AttPieces att,
+__global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const float2 *__restrict__ att,
                                                    const uint32_t *__restrict__ mass, float2 *__restrict__ pos,
                                                    const float2 *__restrict__ Frep, float kg, int strong,
                                                    float2 *__restrict__ F, float2 *__restrict__ Fprev, XPart *part,
@@ -1420,18 +1269,14 @@ struct Fa2Scratch {
     float4 *geo;           // pre-order elements (cells and bodies)
     int32_t *skip;         // pre-order index after each element's subtree
     float2 *Frep;
-    float2 *full, *head, *tail;
-    int32_t *chunk_row;   // plan: row of each chunk's first entry
-    unsigned long long *chunk_meta;  // plan: rows of the chunk's entries, flags
-    int32_t *long_rows;   // plan: rows over more than kLongRowRanges ranges
-    int32_t *long_count;
+    float2 *full;          // attraction per row
+    int32_t *rows_short, *rows_med, *rows_long;  // plan: rows by length class
+    uint32_t *att_counts;  // plan: the three list lengths
     XPart *part;  // per node-kernel block: exact S and T partials
 };
 
 static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
     const size_t k = size_t(K > 0 ? K : 1);
-    const size_t chunks = size_t((nnz > 0 ? nnz : 1) + kChunk - 1) / kChunk;
-    const size_t ranges = size_t((nnz > 0 ? nnz : 1) + kRangeMin - 1) / kRangeMin;
     const bool batched = G > 1;
     s.frame = c.take<float4>(size_t(G > 1 ? G : 1));
     s.frame_part = c.take<float4>(kMaxFrameBlocks);
@@ -1457,12 +1302,10 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.skip = c.take<int32_t>(2 * k);
     s.Frep = c.take<float2>(k);
     s.full = c.take<float2>(k);
-    s.head = c.take<float2>(ranges);
-    s.tail = c.take<float2>(ranges);
-    s.chunk_row = c.take<int32_t>(chunks);
-    s.chunk_meta = c.take<unsigned long long>(chunks);
-    s.long_rows = c.take<int32_t>(ranges / kLongRowRanges + 1);
-    s.long_count = c.take<int32_t>(1);
+    s.rows_short = c.take<int32_t>(k);
+    s.rows_med = c.take<int32_t>(k);
+    s.rows_long = c.take<int32_t>(k);
+    s.att_counts = c.take<uint32_t>(4);
     s.part = c.take<XPart>(2 * size_t(kMaxNodeBlocks));
 }
 
@@ -1552,20 +1395,20 @@ int wait_check_moments(void *scratch, uint32_t *dev_status, cudaStream_t st) {
 }
 
 // Launch shapes of the step, process wide (bgv_autotune_fa2 picks them):
-// CSR entries per attraction warp range, threads per block of the
-// traversal, blocks per SM of the persistent tail.  Packed in one word so a
+// the longest rows the attraction sums one lane each, threads per block of
+// the traversal, blocks per SM of the persistent tail.  Packed in one word so a
 // step reads a consistent set.
-static std::atomic<uint32_t> g_fa2_tune{(512u << 16) | (256u << 4) | 4u};
+static std::atomic<uint32_t> g_fa2_tune{(32u << 16) | (256u << 4) | 4u};
 Fa2Tune fa2_tune() {
     const uint32_t w = g_fa2_tune.load(std::memory_order_relaxed);
     return Fa2Tune{int(w >> 16), int((w >> 4) & 0xFFFu), int(w & 0xFu)};
 }
 int set_fa2_tune(const Fa2Tune &t) {
-    if ((t.att_range != 256 && t.att_range != 512 && t.att_range != 1024) ||
+    if ((t.att_short != 8 && t.att_short != 16 && t.att_short != 32) ||
         (t.repulse_threads != 128 && t.repulse_threads != 256) || t.tail_blocks_per_sm < 1 ||
         t.tail_blocks_per_sm > 8)
         return BGV_EINVAL;
-    g_fa2_tune.store((uint32_t(t.att_range) << 16) | (uint32_t(t.repulse_threads) << 4) | uint32_t(t.tail_blocks_per_sm),
+    g_fa2_tune.store((uint32_t(t.att_short) << 16) | (uint32_t(t.repulse_threads) << 4) | uint32_t(t.tail_blocks_per_sm),
                      std::memory_order_relaxed);
     return BGV_OK;
 }
@@ -1667,21 +1510,19 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
         guard.from = aux;
         guard.into = st;
         if (build_plan) {
-            BGV_CUDA(cudaMemsetAsync(s.long_count, 0, sizeof(int32_t), aux));
-            note_launch(), k_chunk_rows<<<grid_for(K, kThreads, sm_count() * 16), kThreads, 0, aux>>>(
-                K, nnz, tune.att_range, csr_off, s.chunk_row, s.long_rows, s.long_count);
-            BGV_TRY(launch_status());
-            note_launch(), k_chunk_meta<<<grid_for((nnz + kChunk - 1) / kChunk, kThreads, sm_count() * 16), kThreads, 0,
-                                          aux>>>(K, nnz, csr_off, s.chunk_row, s.chunk_meta);
+            BGV_CUDA(cudaMemsetAsync(s.att_counts, 0, 4 * sizeof(uint32_t), aux));
+            note_launch(), k_att_plan<<<grid_for(K, kThreads), kThreads, 0, aux>>>(
+                K, csr_off, tune.att_short, s.rows_short, s.rows_med, s.rows_long, s.att_counts);
             BGV_TRY(launch_status());
         }
-        const int64_t nranges = (nnz + tune.att_range - 1) / tune.att_range;
-        note_launch(), k_attract<<<grid_for(nranges * 32, kThreads, (nranges * 32 + kThreads - 1) / kThreads), kThreads,
-                                   0, aux>>>(K, nnz, tune.att_range, csr_off, s.chunk_row, s.chunk_meta, csr_adj,
-                                             csr_w, pos, s.full, s.head, s.tail);
+        note_launch(), k_att_short<<<grid_for(K, kThreads), kThreads, 0, aux>>>(K, csr_off, csr_adj, csr_w, pos,
+                                                                                s.rows_short, s.att_counts, s.full);
         BGV_TRY(launch_status());
-        note_launch(), k_long_rows<<<sm_count() * 16, kLongThreads, 0, aux>>>(tune.att_range, csr_off, s.long_rows,
-                                                                              s.long_count, s.head, s.tail, s.full);
+        note_launch(), k_att_medium<<<grid_for(K * 32, kThreads), kThreads, 0, aux>>>(
+            K, csr_off, csr_adj, csr_w, pos, s.rows_med, s.att_counts, s.full);
+        BGV_TRY(launch_status());
+        note_launch(), k_att_long<<<sm_count() * 2, kThreads, 0, aux>>>(K, csr_off, csr_adj, csr_w, pos, s.rows_long,
+                                                                        s.att_counts, s.full);
         BGV_TRY(launch_status());
     }
     if (batched)
@@ -1744,7 +1585,7 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
     BGV_TRY(mark(6));
     BGV_TRY(guard.join());  // the attraction ran alongside on the second stream
     BGV_TRY(mark(7));
-    AttPieces att = {nnz > 0 ? csr_off : nullptr, s.full, s.head, s.tail, tune.att_range};
+    const float2 *att = nnz > 0 ? s.full : nullptr;
     if (mode == 0) {
         note_launch(), k_node<<<grid_for(K, kThreads, node_blocks()), kThreads, 0, st>>>(
             K, att, mass, pos, s.Frep, p.kg, p.strong_gravity, reinterpret_cast<float2 *>(Fr),

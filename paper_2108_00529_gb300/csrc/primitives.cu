@@ -482,7 +482,11 @@ __global__ void __launch_bounds__(kSortThreads, kVals ? 3 : 4) k_sort_coop(unsig
                                                                  const int64_t *d_count, int first_pass, int passes,
                                                                  uint32_t *chunk_hist, uint32_t *chunk_pre,
                                                                  uint32_t *totals, GridBar *bar, uint32_t *dev_status,
-                                                                 int spin_limit) {
+                                                                 int spin_limit, const uint32_t *guard,
+                                                                 uint32_t guard_min) {
+    // guarded launch: runs only when *guard exceeds guard_min (every block
+    // reads the same word, so all leave together, before any barrier)
+    if (guard && *guard <= guard_min) return;
     constexpr int kItems = kSortItemsSmall;
     constexpr int kTileKeys = kSortThreads * kItems;
     __shared__ uint32_t cnt[kSortWarps][kBins];
@@ -602,16 +606,25 @@ __global__ void __launch_bounds__(kSortThreads, kVals ? 3 : 4) k_sort_coop(unsig
     }
 }
 
-// Which sort runs the passes: the cooperative one (1, the default) or the
-// onesweep passes with decoupled look-back (0); process wide.
-std::atomic<int> g_sort_method{1};
+// Which sort runs the passes: onesweep passes with decoupled look-back (0),
+// the cooperative kernel (1), or by size (2, the default): cooperative for
+// key counts in [g_coop_lo, g_coop_hi], where it measured faster on GB300
+// (its three grid barriers per pass cost more than the look-back below that,
+// its second read of the keys more above); process wide.
+std::atomic<int> g_sort_method{2};
+std::atomic<int64_t> g_coop_lo{int64_t(1) << 21}, g_coop_hi{int64_t(1) << 23};
+inline bool use_coop(int64_t cap) {
+    const int m = g_sort_method.load(std::memory_order_relaxed);
+    if (m != 2) return m == 1;
+    return cap >= g_coop_lo.load(std::memory_order_relaxed) && cap <= g_coop_hi.load(std::memory_order_relaxed);
+}
 
 // Launches the cooperative sort over passes first..passes-1 from buffer
 // pair 0; the result is in pair (passes - first) % 2.  Its counter words
 // (totals, barrier) must be zero: radix_sort clears them, the FA2 step's
 // keys kernel clears them in its graph.
 int coop_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int first, int passes, cudaStream_t s,
-              uint32_t *dev_status) {
+              uint32_t *dev_status, const uint32_t *guard = nullptr, uint32_t guard_min = 0) {
     const int64_t tiles = tiles_for(cap, kSortItemsSmall);
     const void *kernel = b.vals[0] ? reinterpret_cast<const void *>(k_sort_coop<true>)
                                    : reinterpret_cast<const void *>(k_sort_coop<false>);
@@ -627,7 +640,7 @@ int coop_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int first, in
     uint32_t *v0 = b.vals[0], *v1 = b.vals[1];
     int limit = spin_limit();
     void *args[] = {&k0, &k1, &v0, &v1, &cap, &d_count, &first, &passes, &chunk_hist, &chunk_pre, &totals,
-                    &bar, &dev_status, &limit};
+                    &bar, &dev_status, &limit, &guard, &guard_min};
     return launch_coop(kernel, blocks, kSortThreads, args, s);
 }
 
@@ -683,7 +696,7 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
     if (passes > kMaxPasses) return BGV_EINVAL;
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
-    if (g_sort_method.load(std::memory_order_relaxed) == 1) {
+    if (use_coop(cap)) {
         BGV_TRY(coop_sort(b, cap, d_count, 0, passes, s, dev_status));
         *result_buffer = passes & 1;
         return BGV_OK;
@@ -718,6 +731,10 @@ namespace {
 constexpr int kShortRun = 8;
 constexpr int kWarpRun = 256;
 constexpr int kFixThreads = 256;
+// A run longer than this is not sorted by one block (its time would grow
+// with the run, e.g. many bodies inside one cell of side 2^-16 of the
+// frame): the whole array gets a full LSD sort instead.
+constexpr uint32_t kFixGuard = 16384;
 
 __device__ __forceinline__ unsigned long long run_key(unsigned long long k, int64_t pos) {
     return ((k & 0xFFFFull) << 32) | static_cast<unsigned long long>(pos);
@@ -832,7 +849,10 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__
         }
         if (!__any_sync(0xFFFFFFFFu, marked)) continue;
         if (len > kWarpRun) {
-            if (lane == 0) big[atomicAdd(big_count, 1u)] = uint32_t(start);
+            if (lane == 0) {
+                big[atomicAdd(big_count, 1u)] = uint32_t(start);
+                atomicMax(big_count + 1, uint32_t(len));
+            }
             continue;
         }
         const unsigned long long hi = keys[start] >> 16;
@@ -879,6 +899,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
                                                            uint32_t *__restrict__ alt_vals, int64_t cap,
                                                            const int64_t *d_count, const uint32_t *__restrict__ big,
                                                            const uint32_t *big_count) {
+    if (big_count[1] > kFixGuard) return;  // the whole array was sorted again instead
     const int64_t n = load_count(d_count, cap);
     constexpr int kWarps = kFixThreads / 32;
     constexpr int kGroups = kBlockItems * kWarps;
@@ -972,7 +993,7 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r) {
     r.descent = c.take<uint8_t>(size_t((cap + 31) / 32 + 16));
     r.runs = c.take<uint32_t>(size_t(cap / (kShortRun + 1) + 1));
     r.big = c.take<uint32_t>(size_t(cap / (kWarpRun + 1) + 1));
-    r.counts = c.take<uint32_t>(2);
+    r.counts = c.take<uint32_t>(3);  // runs, big runs, longest big run
 }
 
 // digit counts of every pass, tile counters, then the grid-barrier words of
@@ -989,15 +1010,15 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const i
     if (!counters_cleared)
         BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
     int cur = 0;
-    if (g_sort_method.load(std::memory_order_relaxed) == 1) {
-        BGV_CUDA(cudaMemsetAsync(r.counts, 0, 2 * sizeof(uint32_t), s));
+    if (use_coop(cap)) {
+        BGV_CUDA(cudaMemsetAsync(r.counts, 0, 3 * sizeof(uint32_t), s));
         BGV_TRY(coop_sort(b, cap, d_count, 2, passes, s, dev_status));
         cur = (passes - 2) & 1;
     } else {
         const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;  // >= tiles
         note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0,
                                       s>>>(b.keys[0], cap, d_count, 2, passes, b.counts, b.status,
-                                           tiles_for(cap, items), r.counts, 2);
+                                           tiles_for(cap, items), r.counts, 3);
         BGV_TRY(launch_status());
         for (int p = 2; p < passes; ++p) {
             BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p),
@@ -1011,6 +1032,14 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const i
         note_launch(), k_fix_warp<<<sm_count() * 8, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], cap, d_count,
                                                                          r.descent, r.runs, r.counts, r.big,
                                                                          r.counts + 1);
+        // the guard: a run too long for one block -> a full LSD sort of the
+        // array (an even number of passes, so the result stays in `cur`)
+        SortBuffers g = b;
+        if (cur == 1) {
+            std::swap(g.keys[0], g.keys[1]);
+            std::swap(g.vals[0], g.vals[1]);
+        }
+        BGV_TRY(coop_sort(g, cap, d_count, 0, (passes + 1) & ~1, s, dev_status, r.counts + 2, kFixGuard));
         note_launch(), k_fix_block<<<sm_count() * 2, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
                                                                           b.vals[cur ^ 1], cap, d_count, r.big,
                                                                           r.counts + 1);
@@ -1069,6 +1098,10 @@ int64_t sort_cutoff() { return g_small_sort_cutoff.load(std::memory_order_relaxe
 int64_t set_sort_cutoff(int64_t cutoff) { return g_small_sort_cutoff.exchange(cutoff, std::memory_order_relaxed); }
 int set_sort_method(int method) { return g_sort_method.exchange(method, std::memory_order_relaxed); }
 int sort_method() { return g_sort_method.load(std::memory_order_relaxed); }
+void sort_coop_range(int64_t *lo, int64_t *hi) {
+    *lo = g_coop_lo.load(std::memory_order_relaxed);
+    *hi = g_coop_hi.load(std::memory_order_relaxed);
+}
 
 int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *dev_status, float *ms8, float *ms16,
                   float *ms_coop, int32_t *sizes_log2, int32_t *count, int32_t *method) {
@@ -1080,8 +1113,7 @@ int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *de
     }
     const int method_before = g_sort_method.load(std::memory_order_relaxed);
     int rc = BGV_OK;
-    int64_t cutoff = 0;
-    double sum_onesweep = 0.0, sum_coop = 0.0;
+    int64_t cutoff = 0, coop_lo = -1, coop_hi = -1;
     int k = 0;
     for (int lg = 14; lg <= 30 && (int64_t(1) << lg) <= max_keys && rc == BGV_OK; lg += 2, ++k) {
         const int64_t n = int64_t(1) << lg;
@@ -1112,17 +1144,26 @@ int autotune_sort(int64_t max_keys, SortBuffers &b, cudaStream_t s, uint32_t *de
         if (ms_coop) ms_coop[k] = best[2];
         if (sizes_log2) sizes_log2[k] = lg;
         if (best[0] <= best[1]) cutoff = n;
-        sum_onesweep += best[0] < best[1] ? best[0] : best[1];
-        sum_coop += best[2];
+        if (best[2] < (best[0] < best[1] ? best[0] : best[1])) {  // cooperative faster at this size
+            if (coop_lo < 0) coop_lo = n;
+            coop_hi = n;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (count) *count = k;
     if (rc == BGV_OK) {
-        // the cutoff of the onesweep passes, and whichever method summed less
-        // time over the sizes timed
+        // the cutoff of the onesweep passes, and the cooperative sort for the
+        // span of sizes from the first to the last at which it was faster
+        // (reaching halfway to the neighbouring sizes timed)
         g_small_sort_cutoff.store(cutoff, std::memory_order_relaxed);
-        g_sort_method.store(k > 0 && sum_coop > sum_onesweep ? 0 : 1, std::memory_order_relaxed);
+        if (coop_lo > 0) {
+            g_coop_lo.store(coop_lo - coop_lo / 2, std::memory_order_relaxed);
+            g_coop_hi.store(coop_hi * 2 - 1, std::memory_order_relaxed);
+            g_sort_method.store(2, std::memory_order_relaxed);
+        } else {
+            g_sort_method.store(0, std::memory_order_relaxed);
+        }
     } else {
         g_sort_method.store(method_before, std::memory_order_relaxed);
     }

@@ -47,7 +47,7 @@ def test_struct_layouts(lib):
     assert C.sizeof(bgv.bgv_layout_params) == 96
     assert C.sizeof(bgv.bgv_fa2_stats) == 56
     assert C.sizeof(bgv.bgv_fa2_tune_report) == 48
-    assert C.sizeof(bgv.bgv_tune_report) == 160
+    assert C.sizeof(bgv.bgv_tune_report) == 176
     p = bgv.bgv_layout_default_params()
     assert (p.rows, p.width, p.passes, p.growth, p.iterations) == (4, 4096, 3, 2, 200)
     assert (p.threshold_mode, p.jumps, p.use_graph) == (0, 0, 1)

@@ -116,9 +116,9 @@ def _oracle_batch(graphs):
 
 
 def test_batched_forces_equal_separate_calls():
-    # Same positions, same tree per graph: repulsion and gravity are bit
-    # identical to the single-graph call; attraction differs only in the
-    # grouping of its FP32 sums (its ranges start at other offsets).
+    # Same positions, same tree per graph: every force is bit identical to
+    # the single-graph call (each row's attraction is summed in an order set
+    # by the row's own entries alone).
     graphs = _mixed_batch()
     sgs, koff, off, adj, w, mass = _oracle_batch(graphs)
     Gn, K = len(graphs), int(koff[-1])
@@ -136,7 +136,7 @@ def test_batched_forces_equal_separate_calls():
         r = G.fa2_forces(pos[a:b], s["mass"], s["csr_off"], s["csr_adj"], s["csr_w"], FA2Params())
         assert np.array_equal(Fr[a:b].astype(np.float64), r["Fr"]), g
         assert np.array_equal(Fg[a:b].astype(np.float64), r["Fg"]), g
-        assert G.rel_err(Fa[a:b], r["Fa"]) <= 1e-5, g
+        assert np.array_equal(Fa[a:b].astype(np.float64), r["Fa"]), g
 
 
 def test_batched_run_tracks_separate_runs():
@@ -161,9 +161,9 @@ def test_batched_run_tracks_separate_runs():
         dv = G.Fa2Device(oracle.fa2_init(s["K"], 1), s["mass"], s["csr_off"], s["csr_adj"], s["csr_w"], FA2Params())
         dv.run(steps, 0)
         ref, _, _, ref_speed = dv.state()
-        ext = max(float(np.ptp(ref)), 1.0)
-        assert np.max(np.abs(out[koff[g]:koff[g + 1]] - ref)) <= 1e-4 * ext, g
-        assert sp[g] == pytest.approx(ref_speed, rel=1e-4), g
+        # the same forces and exact swing/traction sums: the same trajectory
+        assert np.array_equal(out[koff[g]:koff[g + 1]], ref), g
+        assert sp[g] == ref_speed, g
 
 
 def test_batched_reports_edges_outside_their_graph():
