@@ -454,14 +454,16 @@ int bgv_fa2_run_batched(int32_t G, const int64_t *koff, int64_t nnz, const int32
  *    (method 0), 8 keys per thread up to a size cutoff and 16 above it, or
  *    as one cooperative kernel for all its passes (method 1: per pass, digit
  *    counts per block chunk, a scan over the chunks, a stable scatter; no
- *    look-back), or by size (method 2, the default): cooperative for key
- *    counts in a range, onesweep otherwise.  bgv_autotune_sort times all
+ *    look-back), or by size (method 2, the default): cooperative for keys
+ *    with values in a range of counts and for keys alone from its lower
+ *    end up, onesweep otherwise.  bgv_autotune_sort times all
  *    three forms on this GPU for 2^14, 2^16, ... <= max_keys keys (48-bit
  *    keys with 32-bit values, SplitMix64 of the index), sets the cutoff to
  *    the largest size at which 8 was not slower, and the cooperative range
  *    to the span of sizes where it was faster (method 0 if none).  All are
  *    process wide; they start at a cutoff of 2^40 (8 keys per thread at every
- *    size) and a cooperative range of [2^21, 2^23], as measured on GB300;
+ *    size) and a cooperative range of [2^21, 2^23] (keys alone: from 2^21
+ *    up), as measured on GB300;
  *    workspaces stay valid whatever they are.  bgv_set_sort_cutoff and
  *    bgv_set_sort_method (0, 1, 2) set them directly and return the previous
  *    value.

@@ -359,7 +359,7 @@ __device__ __forceinline__ Mom mom_warp_sum(Mom v) {
 // Staging slot of tile element e: one 16-byte pad after every 8 elements, so
 // the per-thread writes (stride 8) fall in different banks.
 __device__ __forceinline__ int stage_slot(int e) { return e + (e >> 3); }
-__global__ void __launch_bounds__(kThreads, 3) k_gather_moments(
+__global__ void __launch_bounds__(kThreads, 4) k_gather_moments(
     const uint32_t *__restrict__ perm, int64_t K, const float2 *__restrict__ pos, const uint32_t *__restrict__ mass,
     const float4 *__restrict__ frames, const int32_t *__restrict__ bgraph, float4 *__restrict__ body,
     MomP *__restrict__ P, uint32_t *__restrict__ start_count, uint32_t *__restrict__ start_levels, uint32_t *flags, MomTile *agg,
@@ -750,6 +750,8 @@ __global__ void __launch_bounds__(kRT) k_repulse(const float4 *__restrict__ geo,
 // ids and weights, then their position gathers, so they are in flight
 // together.  An empty row is a short row of sum 0.
 constexpr int kAttMedium = 4096;
+// loads in flight per worker; with 5 blocks of 256 per SM (at most 51
+// registers) that is 320 outstanding gathers per SM
 constexpr int kAttIn = 8;
 
 // Block-aggregated append of row r to the list of class c (one atomic per
@@ -797,7 +799,7 @@ __device__ __forceinline__ bool valid_row(int32_t j, int64_t K) {
 }
 
 // Short rows: one lane each.
-__global__ void __launch_bounds__(kThreads) k_att_short(int64_t K, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads, 5) k_att_short(int64_t K, const int32_t *__restrict__ off,
                                                         const int32_t *__restrict__ adj,
                                                         const uint32_t *__restrict__ w,
                                                         const float2 *__restrict__ pos,
@@ -833,7 +835,7 @@ __global__ void __launch_bounds__(kThreads) k_att_short(int64_t K, const int32_t
 }
 
 // Medium rows: one warp each.
-__global__ void __launch_bounds__(kThreads) k_att_medium(int64_t K, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(kThreads, 5) k_att_medium(int64_t K, const int32_t *__restrict__ off,
                                                          const int32_t *__restrict__ adj,
                                                          const uint32_t *__restrict__ w,
                                                          const float2 *__restrict__ pos,
@@ -1398,7 +1400,7 @@ int wait_check_moments(void *scratch, uint32_t *dev_status, cudaStream_t st) {
 // the longest rows the attraction sums one lane each, threads per block of
 // the traversal, blocks per SM of the persistent tail.  Packed in one word so a
 // step reads a consistent set.
-static std::atomic<uint32_t> g_fa2_tune{(32u << 16) | (256u << 4) | 4u};
+static std::atomic<uint32_t> g_fa2_tune{(32u << 16) | (128u << 4) | 4u};  // measured best on GB300 (rmat22x)
 Fa2Tune fa2_tune() {
     const uint32_t w = g_fa2_tune.load(std::memory_order_relaxed);
     return Fa2Tune{int(w >> 16), int((w >> 4) & 0xFFFu), int(w & 0xFu)};

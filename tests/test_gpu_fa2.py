@@ -351,7 +351,7 @@ def test_fa2_autotuner_keeps_results():
         with pytest.raises(B.BgvError):
             B.bgv_set_fa2_tune(300, 256, 4)
     finally:
-        B.bgv_set_fa2_tune(32, 256, 4)
+        B.bgv_set_fa2_tune(32, 128, 4)
 
 
 def test_sort_guard_for_one_long_unordered_run():
