@@ -107,6 +107,42 @@ def test_supergraph_random_labels_bit_exact(seed):
     _check_super(sg, oracle.supergraph(e, n, lab, dh, 3, 97, seed))
 
 
+def _shape_cases():
+    # Supergraph shapes beyond the random graphs: one row of 20,000 distinct
+    # columns, three supernodes joined by runs of tens of thousands of one
+    # repeated pair, a dense cluster whose row holds few cut pairs among many
+    # intra-community edges, 200,000 mostly empty rows, and ids that need 24
+    # bits (keys of 48 bits).
+    n = 30000
+    star = np.stack([np.zeros(20000, np.int32), np.arange(1, 20001, dtype=np.int32)], 1)
+    e = np.concatenate([star, graphgen.random_graph(n, 40000, seed=12)]).astype(np.int32)
+    yield "star-20k", e, n, np.arange(n, dtype=np.int32)
+    e = graphgen.random_graph(n, 150000, seed=13)
+    lab = (np.random.default_rng(13).integers(0, 3, n) * 7).astype(np.int32)
+    yield "three-communities", e, n, lab
+    iu = np.triu_indices(200, 1)
+    clique = np.stack([iu[0], iu[1]], 1).astype(np.int32)
+    e = np.concatenate([clique, graphgen.random_graph(n, 60000, seed=14)]).astype(np.int32)
+    lab = np.arange(n, dtype=np.int32)
+    lab[:200] = 0
+    yield "dense-cluster", e, n, lab
+    n = 200000
+    yield "sparse-rows", graphgen.random_graph(n, 30000, seed=15), n, np.arange(n, dtype=np.int32)
+    n = (1 << 23) + 5
+    e = graphgen.random_graph(n, 100000, seed=16)
+    yield "24-bit-ids", e, n, (np.arange(n, dtype=np.int64) // 3 * 3).astype(np.int32)
+
+
+SHAPE_CASES = list(_shape_cases())
+
+
+@pytest.mark.parametrize("name,e,n,lab", SHAPE_CASES, ids=[c[0] for c in SHAPE_CASES])
+def test_supergraph_shapes_bit_exact(name, e, n, lab):
+    dh = oracle.exact_degrees(e, n)
+    sg = G.supergraph(e, n, lab, dh, 2, 256, 3)
+    _check_super(sg, oracle.supergraph(e, n, lab, dh, 2, 256, 3))
+
+
 def test_supergraph_identity_labels_is_the_graph():
     e = graphgen.random_graph(3000, 12000, seed=9)
     n = 3000
