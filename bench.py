@@ -434,9 +434,9 @@ def gpu_arm(args, dist: Dist):
                           "(launched one by one; the others replay a captured step)",
         "roofline": roofline,
         "edge_roofline": edge_roofline,
-        "e2e": {"value": round(aggregate_throughput(m, dist.world, e2e_ms), 1), "unit": "edges/s",
-                "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(8 * m),
-                "d2h_bytes_per_step": int(4 * n + 12 * K2), "entry": "bgv_layout_host"},
+        "e2e": ({"value": round(aggregate_throughput(m, dist.world, e2e_ms), 1), "unit": "edges/s",
+                 "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(8 * m),
+                 "d2h_bytes_per_step": int(4 * n + 12 * K2), "entry": "bgv_layout_host"} if e2e else None),
         "gpu_launches": int(launches),
         "gpu_launches_per_step": int(launches // max(args.steps, 1)),
         "clocks": clk,
@@ -850,6 +850,18 @@ def reference_arm(args, dist: Dist):
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def finite(x):
+    """The line as strict JSON: a number that is not finite (a leg that did
+    not run) becomes null."""
+    if isinstance(x, dict):
+        return {k: finite(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [finite(v) for v in x]
+    if isinstance(x, float) and not math.isfinite(x):
+        return None
+    return x
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -888,7 +900,7 @@ def main():
     finally:
         dist.close()
     if out is not None and dist.rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(finite(out), allow_nan=False))
 
 
 if __name__ == "__main__":
