@@ -8,7 +8,8 @@ CUDA events on the launching stream; L2 is flushed (a 256 MiB write) before
 every timed step.  `value` is edges per second of whole steps (m * N / the
 slowest rank's mean step time).  `e2e` repeats the step through
 bgv_layout_host from pinned host memory (host-to-device copy of the edges and
-device-to-host copy of the layout inside the timed region).
+device-to-host copy of the layout inside the timed region), after one untimed
+call of its own.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22x]
     python bench.py --impl reference ...   # the CPU oracle, bounded sample
@@ -401,6 +402,10 @@ def gpu_arm(args, dist: Dist):
     hxy = torch.zeros((n, 2), dtype=torch.float32).pin_memory()
     hrad = torch.zeros(n, dtype=torch.float32).pin_memory()
     e2e = []
+    if not args.no_e2e:  # one untimed call first: the first host-buffer call of a process pays one-time costs
+        with torch.cuda.stream(s):
+            B.bgv_layout_host(he, m, n, lp, hmap, hxy, hrad, ws_e2e, stream=s)
+        s.synchronize()
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
