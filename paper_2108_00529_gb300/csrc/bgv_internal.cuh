@@ -157,9 +157,10 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
                int *result_buffer, uint32_t *dev_status, int items = 0);
 
 // The same order (keys, with values when b.vals[0] is set) when the keys
-// are nearly always told apart above their low 16 bits: LSD passes on bits
-// 16.. only, then every run of equal high bits sorted locally on its low
-// bits.  Count = *d_count if given, else cap.
+// are nearly always told apart above their low kLowBits bits: LSD passes on
+// the bits above them only, then every run of equal high bits sorted
+// locally on its low bits.  Count = *d_count if given, else cap.
+constexpr int kLowBits = 24;
 struct RunFixBuffers {
     uint8_t *descent;   // per 32-key chunk: holds a key below its predecessor in the same run
     uint32_t *runs;     // starts of runs too long for one thread

@@ -5,7 +5,7 @@
 //   k_keys      fixed-point coordinates U and 2L-bit Morton keys; clears the
 //               step's counters (the captured step has no memset nodes)
 //   radix sort  (key, body) pairs -> Morton order: LSD passes on the bits
-//               above 16, then each run of equal high bits ordered locally
+//               above 24, then each run of equal high bits ordered locally
 //   k_gather_moments
 //               bodies in Morton order, and exact prefix sums of (m, m*Ux,
 //               m*Uy) in 64/128-bit integers over that order (one pass,

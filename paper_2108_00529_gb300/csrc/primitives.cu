@@ -721,37 +721,42 @@ int radix_sort(SortBuffers &b, int64_t cap, const int64_t *d_count, int end_bit,
 }
 
 // ----------------------------------------------- sort with a local finish
-// For keys whose order is almost always decided above their lowest 16 bits
-// (Morton keys of spread-out points): LSD passes on bits 16 and up only,
-// which leave every run of equal high bits contiguous and in input order,
-// then each run put in order of its low 16 bits on its own, stably, so the
-// result is the stable sort of the whole key.  A pass over all keys marks
+// For keys whose order is almost always decided above their lowest
+// kLowBits = 24 bits (Morton keys of spread-out points: in rmat22x layouts
+// at 1 to 500 FA2 iterations, 86 to 97 % of the bodies are alone in their
+// cell of side 2^-12 of the frame and the longest run held 42 bodies): LSD
+// passes on bits 24 and up only, which leave every run of equal high bits
+// contiguous and in input order, then each run put in order of its low 24
+// bits on its own, stably, so the result is the stable sort of the whole key.  A pass over all keys marks
 // every 32-key chunk holding a descent (a key whose low bits are below its
 // predecessor's in the same run) and sorts runs of up to kShortRun keys in
 // registers; a warp skips the longer runs without a marked chunk (equal or
 // already ordered keys: coincident bodies) and ranks those of up to
-// kWarpRun keys; a block sorts each longer run by four 4-bit LSD passes
+// kWarpRun keys; a block sorts each longer run by six 4-bit LSD passes
 // through the idle half of the ping-pong buffers.
 namespace {
 constexpr int kShortRun = 8;
+constexpr int kLowDigits = kLowBits / 4;  // 4-bit passes of the block finish (even: the run ends in place)
+static_assert(kLowBits % 8 == 0 && kLowDigits % 2 == 0, "whole LSD passes above, an even count below");
+constexpr unsigned long long kLowMask = (1ull << kLowBits) - 1ull;
 constexpr int kWarpRun = 256;
 constexpr int kFixThreads = 256;
 // A run longer than this is not sorted by one block (its time would grow
-// with the run, e.g. many bodies inside one cell of side 2^-16 of the
+// with the run, e.g. many bodies inside one cell of side 2^-12 of the
 // frame): the whole array gets a full LSD sort instead.
 constexpr uint32_t kFixGuard = 16384;
 
 __device__ __forceinline__ unsigned long long run_key(unsigned long long k, int64_t pos) {
-    return ((k & 0xFFFFull) << 32) | static_cast<unsigned long long>(pos);
+    return ((k & kLowMask) << 32) | static_cast<unsigned long long>(pos);
 }
 
 // End of the run of equal high bits that starts at `start` (the array is
 // sorted on the high bits): galloping from the start (probes at +1, +2, +4,
 // ... stay near the run), then a binary search inside the last step.
 __device__ __forceinline__ int64_t run_end(const unsigned long long *keys, int64_t n, int64_t start) {
-    const unsigned long long hi = keys[start] >> 16;
+    const unsigned long long hi = keys[start] >> kLowBits;
     int64_t step = 1, lo = start + 1;  // keys[lo - 1] is in the run
-    while (lo < n && (keys[lo] >> 16) == hi) {
+    while (lo < n && (keys[lo] >> kLowBits) == hi) {
         lo += step;
         step <<= 1;
     }
@@ -760,7 +765,7 @@ __device__ __forceinline__ int64_t run_end(const unsigned long long *keys, int64
     if (lo < start + 1) lo = start + 1;
     while (lo < up) {
         const int64_t mid = (lo + up) >> 1;
-        if ((keys[mid] >> 16) <= hi) lo = mid + 1; else up = mid;
+        if ((keys[mid] >> kLowBits) <= hi) lo = mid + 1; else up = mid;
     }
     return lo;
 }
@@ -777,21 +782,21 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__
         unsigned long long hi = 0;
         if (i < n) {
             const unsigned long long k = keys[i];
-            hi = k >> 16;
+            hi = k >> kLowBits;
             if (i > 0) {
                 const unsigned long long p = keys[i - 1];
-                desc = (p >> 16) == hi && (k & 0xFFFFull) < (p & 0xFFFFull);
-                head = (p >> 16) != hi;
+                desc = (p >> kLowBits) == hi && (k & kLowMask) < (p & kLowMask);
+                head = (p >> kLowBits) != hi;
             } else {
                 head = true;
             }
-            head = head && i + 1 < n && (keys[i + 1] >> 16) == hi;  // runs of one need nothing
+            head = head && i + 1 < n && (keys[i + 1] >> kLowBits) == hi;  // runs of one need nothing
         }
         const unsigned mask = __ballot_sync(0xFFFFFFFFu, desc);
         if (lane == 0) descent[i >> 5] = mask != 0u;
         if (!head) continue;
         int r = 2;
-        while (r <= kShortRun && i + r < n && (keys[i + r] >> 16) == hi) ++r;
+        while (r <= kShortRun && i + r < n && (keys[i + r] >> kLowBits) == hi) ++r;
         if (r > kShortRun) {
             runs[atomicAdd(run_count, 1u)] = uint32_t(i);
             continue;
@@ -812,7 +817,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_runs(unsigned long long *__
                 uint32_t rk = 0;
 #pragma unroll
                 for (int c = 0; c < kShortRun; ++c) rk += kk[c] < kk[a] ? 1u : 0u;
-                keys[i + rk] = (hi << 16) | (kk[a] >> 32);
+                keys[i + rk] = (hi << kLowBits) | (kk[a] >> 32);
                 if (vals) vals[i + rk] = vv[a];
             }
         }
@@ -860,7 +865,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__
             }
             continue;
         }
-        const unsigned long long hi = keys[start] >> 16;
+        const unsigned long long hi = keys[start] >> kLowBits;
         unsigned long long kk[kPer];
         uint32_t vv[kPer], rank[kPer];
 #pragma unroll
@@ -883,16 +888,16 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_warp(unsigned long long *__
         for (int j = 0; j < kPer; ++j) {
             const int64_t t = lane + 32 * j;
             if (t < len) {
-                keys[start + rank[j]] = (hi << 16) | (kk[j] >> 32);
+                keys[start + rank[j]] = (hi << kLowBits) | (kk[j] >> 32);
                 if (vals) vals[start + rank[j]] = vv[j];
             }
         }
     }
 }
 
-// One block per listed run: four stable counting passes on 4-bit digits of
-// the low 16 bits, from the run to the same range of the other ping-pong
-// buffer and back.  The digit counts of all four passes come from one read
+// One block per listed run: six stable counting passes on 4-bit digits of
+// the low 24 bits, from the run to the same range of the other ping-pong
+// buffer and back.  The digit counts of all six passes come from one read
 // (a stable pass does not change them).  A tile holds kBlockItems keys per
 // thread; a key's place among equal digits comes from __match_any_sync in
 // its warp and the counts of the (item, warp) groups before it, so input
@@ -908,7 +913,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
     const int64_t n = load_count(d_count, cap);
     constexpr int kWarps = kFixThreads / 32;
     constexpr int kGroups = kBlockItems * kWarps;
-    __shared__ uint32_t hist[4][16];
+    __shared__ uint32_t hist[kLowDigits][16];
     __shared__ uint32_t base[16];
     __shared__ uint32_t wcount[kGroups][17];
     __shared__ int64_t end_sh;
@@ -918,7 +923,7 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
     for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int64_t start = big[q];
         if (threadIdx.x == 0) end_sh = run_end(keys, n, start);
-        if (threadIdx.x < 64) (&hist[0][0])[threadIdx.x] = 0;
+        if (threadIdx.x < kLowDigits * 16) (&hist[0][0])[threadIdx.x] = 0;
         __syncthreads();
         const int64_t len = end_sh - start;
         unsigned long long *sk = keys + start, *dk = alt_keys + start;
@@ -927,14 +932,14 @@ __global__ void __launch_bounds__(kFixThreads) k_fix_block(unsigned long long *_
             const int64_t t = t0 + threadIdx.x;
             const unsigned long long k = t < len ? sk[t] : 0ull;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
+            for (int p = 0; p < kLowDigits; ++p) {
                 const int d = t < len ? int((k >> (4 * p)) & 15) : 16;
                 const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
                 if (d < 16 && (peers & lt_mask) == 0u) atomicAdd(&hist[p][d], __popc(peers));
             }
         }
         __syncthreads();
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < kLowDigits; ++p) {
             const int shift = 4 * p;
             if (threadIdx.x == 0) {
                 uint32_t run = 0;
@@ -1008,24 +1013,25 @@ int64_t sort_counter_words() { return int64_t(kMaxPasses) * kBins + kMaxPasses +
 int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const int64_t *d_count, int end_bit,
                     cudaStream_t s, int *result_buffer, uint32_t *dev_status, bool counters_cleared) {
     const int passes = (end_bit + 7) / 8;
-    if (end_bit <= 16 || passes > kMaxPasses || cap >= (int64_t(1) << 32))
+    if (end_bit <= kLowBits || passes > kMaxPasses || cap >= (int64_t(1) << 32))
         return radix_sort(b, cap, d_count, end_bit, s, result_buffer, dev_status);
     const int items = sort_items(cap);
     uint32_t *tile_counters = b.counts + kMaxPasses * kBins;
     if (!counters_cleared)
         BGV_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * size_t(sort_counter_words()), s));
+    constexpr int first = kLowBits / 8;
     int cur = 0;
     if (use_coop(cap, b.vals[0] != nullptr)) {
         BGV_CUDA(cudaMemsetAsync(r.counts, 0, 3 * sizeof(uint32_t), s));
-        BGV_TRY(coop_sort(b, cap, d_count, 2, passes, s, dev_status));
-        cur = (passes - 2) & 1;
+        BGV_TRY(coop_sort(b, cap, d_count, first, passes, s, dev_status));
+        cur = (passes - first) & 1;
     } else {
         const int64_t count_blocks = (cap + kCountTile - 1) / kCountTile;  // >= tiles
         note_launch(), k_sort_count<<<static_cast<unsigned>(count_blocks > 0 ? count_blocks : 1), kSortThreads, 0,
-                                      s>>>(b.keys[0], cap, d_count, 2, passes, b.counts, b.status,
+                                      s>>>(b.keys[0], cap, d_count, first, passes, b.counts, b.status,
                                            tiles_for(cap, items), r.counts, 3);
         BGV_TRY(launch_status());
-        for (int p = 2; p < passes; ++p) {
+        for (int p = first; p < passes; ++p) {
             BGV_TRY(onesweep_pass(b, cap, d_count, cur, 8 * p, b.counts + p * kBins, tile_counters + p, pass_tag(p),
                                   items, s, dev_status));
             cur ^= 1;

@@ -82,8 +82,8 @@ def test_coincident_points_and_duplicates():
 
 @pytest.mark.parametrize("sizes", [(3000,), (100, 150, 40), (5, 7, 3, 9, 12)])
 def test_dense_clusters_inside_one_fine_cell(sizes):
-    # Clusters smaller than 2^-16 of the frame (side 2000, cells of 0.03 at
-    # that level) share the Morton bits above 16: long runs that the sort
+    # Clusters smaller than 2^-12 of the frame (side 2000, cells of 0.49 at
+    # that level) share the Morton bits above 24: long runs that the sort
     # orders run by run on the low bits (in registers up to 8 keys, by a warp
     # up to 256, by a block above).  The tree must equal the oracle's: the
     # interaction counts are equal exactly.  Inside such a cluster the
@@ -355,8 +355,8 @@ def test_fa2_autotuner_keeps_results():
 
 
 def test_sort_guard_for_one_long_unordered_run():
-    # 80,000 of 200,000 bodies inside one cell of side 2^-16 of the frame:
-    # after the LSD passes on the bits above 16 they form one unordered run
+    # 80,000 of 200,000 bodies inside one cell of side 2^-12 of the frame:
+    # after the LSD passes on the bits above 24 they form one unordered run
     # far longer than one block should sort, so the whole array is sorted
     # again instead.  The tree must still be the oracle's (equal interaction
     # counts) and the forces outside the cluster within 1e-3.
