@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(kRT) k_repulse(const float4 *__restrict__ geo,
 // holds).  The plan, made once per CSR, lists the rows by length: short rows
 // (at most `att_short` entries) take one lane each, 32 rows to a warp, and
 // add their entries in order; medium rows (up to kAttMedium entries) take
-// one warp each: lane l adds entries l, l + 32, ... in order, then a fixed
+// one warp each, two rows at a time: lane l adds entries l, l + 32, ... in order, then a fixed
 // butterfly; long rows take one block each (thread t adds t, t + 256, ...,
 // then a fixed tree).  Every worker first issues kAttIn loads of neighbour
 // ids and weights, then their position gathers, so they are in flight
@@ -834,46 +834,66 @@ __global__ void __launch_bounds__(kThreads, 5) k_att_short(int64_t K, const int3
     }
 }
 
-// Medium rows: one warp each.
-__global__ void __launch_bounds__(kThreads, 5) k_att_medium(int64_t K, const int32_t *__restrict__ off,
+// Medium rows: one warp each, two rows at a time (each lane keeps
+// kAttIn / 2 loads in flight per row, so a warp waits on two rows' round
+// trips at once).  Lane l adds entries l, l + 32, ... of a row in order, then
+// a fixed butterfly: the sums do not depend on how the rows are paired.
+__global__ void __launch_bounds__(kThreads, 4) k_att_medium(int64_t K, const int32_t *__restrict__ off,
                                                          const int32_t *__restrict__ adj,
                                                          const uint32_t *__restrict__ w,
                                                          const float2 *__restrict__ pos,
                                                          const int32_t *__restrict__ rows, const uint32_t *counts,
                                                          float2 *__restrict__ full) {
+    constexpr int kIn = kAttIn / 2;
     const int lane = threadIdx.x & 31;
     const int64_t count = counts[1];
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < count; q += warps) {
-        const int32_t r = rows[q];
-        const int64_t b = off[r], e = off[r + 1];
-        const float2 pi = pos[r];
-        float ax = 0.0f, ay = 0.0f;
-        for (int64_t e0 = b + lane; e0 < e; e0 += 32 * kAttIn) {
-            int32_t j[kAttIn];
-            uint32_t wt[kAttIn];
+    for (int64_t q = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 2; q < count; q += warps * 2) {
+        const bool two = q + 1 < count;
+        const int32_t r0 = rows[q], r1 = two ? rows[q + 1] : r0;
+        const int64_t b0 = off[r0], len0 = int64_t(off[r0 + 1]) - b0;
+        const int64_t b1 = off[r1], len1 = two ? int64_t(off[r1 + 1]) - b1 : 0;
+        const float2 p0 = pos[r0], p1 = pos[r1];
+        float ax0 = 0.0f, ay0 = 0.0f, ax1 = 0.0f, ay1 = 0.0f;
+        const int64_t len = len0 > len1 ? len0 : len1;
+        for (int64_t t0 = lane; t0 < len; t0 += 32 * kIn) {
+            int32_t j0[kIn], j1[kIn];
+            uint32_t w0[kIn], w1[kIn];
 #pragma unroll
-            for (int k = 0; k < kAttIn; ++k) {
-                const int64_t x = e0 + 32 * k;
-                j[k] = x < e ? __ldcs(adj + x) : -1;
-                wt[k] = x < e ? __ldcs(w + x) : 0u;
+            for (int k = 0; k < kIn; ++k) {
+                const int64_t t = t0 + 32 * k;
+                j0[k] = t < len0 ? __ldcs(adj + b0 + t) : -1;
+                w0[k] = t < len0 ? __ldcs(w + b0 + t) : 0u;
+                j1[k] = t < len1 ? __ldcs(adj + b1 + t) : -1;
+                w1[k] = t < len1 ? __ldcs(w + b1 + t) : 0u;
             }
-            float2 pj[kAttIn];
+            float2 q0[kIn], q1[kIn];
 #pragma unroll
-            for (int k = 0; k < kAttIn; ++k) pj[k] = valid_row(j[k], K) ? pos[j[k]] : pi;
+            for (int k = 0; k < kIn; ++k) {
+                q0[k] = valid_row(j0[k], K) ? pos[j0[k]] : p0;
+                q1[k] = valid_row(j1[k], K) ? pos[j1[k]] : p1;
+            }
 #pragma unroll
-            for (int k = 0; k < kAttIn; ++k) {
-                const float wf = valid_row(j[k], K) ? __uint2float_rn(wt[k]) : 0.0f;
-                ax += wf * (pj[k].x - pi.x);
-                ay += wf * (pj[k].y - pi.y);
+            for (int k = 0; k < kIn; ++k) {
+                const float wf0 = valid_row(j0[k], K) ? __uint2float_rn(w0[k]) : 0.0f;
+                const float wf1 = valid_row(j1[k], K) ? __uint2float_rn(w1[k]) : 0.0f;
+                ax0 += wf0 * (q0[k].x - p0.x);
+                ay0 += wf0 * (q0[k].y - p0.y);
+                ax1 += wf1 * (q1[k].x - p1.x);
+                ay1 += wf1 * (q1[k].y - p1.y);
             }
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            ax += __shfl_xor_sync(0xFFFFFFFFu, ax, d);
-            ay += __shfl_xor_sync(0xFFFFFFFFu, ay, d);
+            ax0 += __shfl_xor_sync(0xFFFFFFFFu, ax0, d);
+            ay0 += __shfl_xor_sync(0xFFFFFFFFu, ay0, d);
+            ax1 += __shfl_xor_sync(0xFFFFFFFFu, ax1, d);
+            ay1 += __shfl_xor_sync(0xFFFFFFFFu, ay1, d);
         }
-        if (lane == 0) full[r] = make_float2(ax, ay);
+        if (lane == 0) {
+            full[r0] = make_float2(ax0, ay0);
+            if (two) full[r1] = make_float2(ax1, ay1);
+        }
     }
 }
 
