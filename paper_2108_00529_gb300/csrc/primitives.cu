@@ -1038,7 +1038,7 @@ int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const i
         }
     }
     if (cap > 1) {
-        note_launch(), k_fix_runs<<<grid_for(cap, kFixThreads, sm_count() * 8), kFixThreads, 0, s>>>(
+        note_launch(), k_fix_runs<<<grid_for(cap, kFixThreads, sm_count() * 64), kFixThreads, 0, s>>>(
             b.keys[cur], b.vals[cur], cap, d_count, r.descent, r.runs, r.counts);
         note_launch(), k_fix_warp<<<sm_count() * 8, kFixThreads, 0, s>>>(b.keys[cur], b.vals[cur], cap, d_count,
                                                                          r.descent, r.runs, r.counts, r.big,
