@@ -1091,9 +1091,7 @@ __device__ __forceinline__ float2 swing_traction(float m, float fx, float fy, fl
 // node the local speed and the displacement, Fprev = F.  The barrier waits
 // are bounded and report BGV_DEV_TIMEOUT.
 // full == nullptr: no CSR entries, no attraction.
-__device__ __forceinline__ float2 node_force(int64_t i, const float2 *__restrict__ full, float m, float2 pi, float2 fr,
-                                             float kg, int strong) {
-    const float2 fa = full ? full[i] : make_float2(0.0f, 0.0f);
+__device__ __forceinline__ float2 force_sum(float2 fa, float m, float2 pi, float2 fr, float kg, int strong) {
     float gx, gy;
     if (strong) {
         gx = -kg * m * pi.x;
@@ -1104,6 +1102,13 @@ __device__ __forceinline__ float2 node_force(int64_t i, const float2 *__restrict
         gy = rr > 0.0f ? -kg * m * pi.y / rr : 0.0f;
     }
     return make_float2(fr.x + fa.x + gx, fr.y + fa.y + gy);
+}
+
+// Total force on node i: repulsion fr, attraction full[i] (none if null),
+// gravity.
+__device__ __forceinline__ float2 node_force(int64_t i, const float2 *__restrict__ full, float m, float2 pi, float2 fr,
+                                             float kg, int strong) {
+    return force_sum(full ? full[i] : make_float2(0.0f, 0.0f), m, pi, fr, kg, strong);
 }
 
 __device__ __forceinline__ float2 displaced(float2 p, float2 f, float2 fp, float sp, float ks, float ksmax) {
@@ -1133,6 +1138,7 @@ __global__ void __launch_bounds__(kThreads) k_node(int64_t K, const float2 *__re
     }
 }
 
+constexpr int kTailItems = 4;  // nodes a thread takes per pass
 __global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const float2 *__restrict__ att,
                                                    const uint32_t *__restrict__ mass, float2 *__restrict__ pos,
                                                    const float2 *__restrict__ Frep, float kg, int strong,
@@ -1146,17 +1152,36 @@ __global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const float2 *__re
     const bool batched = rowst != nullptr;
     const double sp_old = batched ? 0.0 : *speed;  // read by every block before anyone writes it
     XSum S = xsum_zero(), T = xsum_zero();
-    for (int64_t i = t0; i < K; i += stride) {
-        const float m = __uint2float_rn(mass[i]);
-        const float2 f = node_force(i, att, m, pos[i], Frep[i], kg, strong);
-        F[i] = f;
-        const float2 fp = Fprev[i];
-        const float2 st = swing_traction(m, f.x, f.y, fp.x, fp.y);
-        if (batched) {
-            rowst[i] = st;
-        } else {
-            xsum_add(S, st.x);
-            xsum_add(T, st.y);
+    // kTailItems nodes per pass, every load issued before the arithmetic (the
+    // exact sums do not depend on the order of the terms)
+    for (int64_t i0 = t0; i0 < K; i0 += stride * kTailItems) {
+        uint32_t mk[kTailItems];
+        float2 pk[kTailItems], rk[kTailItems], ak[kTailItems], qk[kTailItems];
+#pragma unroll
+        for (int k = 0; k < kTailItems; ++k) {
+            const int64_t i = i0 + stride * k;
+            const bool in = i < K;
+            const float2 z = make_float2(0.0f, 0.0f);
+            mk[k] = in ? mass[i] : 0u;
+            pk[k] = in ? pos[i] : z;
+            rk[k] = in ? Frep[i] : z;
+            ak[k] = in && att ? att[i] : z;
+            qk[k] = in ? Fprev[i] : z;
+        }
+#pragma unroll
+        for (int k = 0; k < kTailItems; ++k) {
+            const int64_t i = i0 + stride * k;
+            if (i >= K) continue;
+            const float m = __uint2float_rn(mk[k]);
+            const float2 f = force_sum(ak[k], m, pk[k], rk[k], kg, strong);
+            F[i] = f;
+            const float2 st = swing_traction(m, f.x, f.y, qk[k].x, qk[k].y);
+            if (batched) {
+                rowst[i] = st;
+            } else {
+                xsum_add(S, st.x);
+                xsum_add(T, st.y);
+            }
         }
     }
     if (!batched) {
@@ -1208,11 +1233,26 @@ __global__ void __launch_bounds__(kThreads) k_tail(int64_t K, const float2 *__re
         if (!grid_barrier(&hdr->bar, spin_limit, &hdr->status)) return;
     }
     const float sp_all = float(sp_sh);
-    for (int64_t i = t0; i < K; i += stride) {
-        const float sp = batched ? float(__ldcg(&speed[bgraph[i]])) : sp_all;
-        const float2 f = F[i], fp = Fprev[i];
-        pos[i] = displaced(pos[i], f, fp, sp, ks, ksmax);
-        Fprev[i] = f;
+    for (int64_t i0 = t0; i0 < K; i0 += stride * kTailItems) {
+        float2 fk[kTailItems], qk[kTailItems], pk[kTailItems];
+        float sk[kTailItems];
+#pragma unroll
+        for (int k = 0; k < kTailItems; ++k) {
+            const int64_t i = i0 + stride * k;
+            const bool in = i < K;
+            const float2 z = make_float2(0.0f, 0.0f);
+            fk[k] = in ? __ldcg(&F[i]) : z;  // written by this kernel before the barrier
+            qk[k] = in ? Fprev[i] : z;
+            pk[k] = in ? pos[i] : z;
+            sk[k] = in && batched ? float(__ldcg(&speed[bgraph[i]])) : sp_all;
+        }
+#pragma unroll
+        for (int k = 0; k < kTailItems; ++k) {
+            const int64_t i = i0 + stride * k;
+            if (i >= K) continue;
+            pos[i] = displaced(pk[k], fk[k], qk[k], sk[k], ks, ksmax);
+            Fprev[i] = fk[k];
+        }
     }
 }
 
