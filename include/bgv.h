@@ -78,6 +78,7 @@ extern "C" {
 #define BGV_DEV_BADLABEL 2u    /* a label outside [0, n) */
 /* bit 4u is unused: the Barnes-Hut traversal keeps no stack */
 #define BGV_DEV_TIMEOUT 8u     /* a bounded device-side wait gave up */
+#define BGV_DEV_BADHINT 16u    /* a sort hint entry outside [0, K) */
 
 /* Library version, (major << 16) | minor. */
 int bgv_version(void);
@@ -515,6 +516,40 @@ int bgv_autotune_sort(int64_t max_keys, bgv_tune_report *out, void *ws, size_t w
 int64_t bgv_sort_cutoff(void);
 int64_t bgv_set_sort_cutoff(int64_t cutoff);
 int32_t bgv_set_sort_method(int32_t method);
+
+/* ------------------------------------------------------------------------
+ * Hinted sort.  The radix tree of the Barnes-Hut repulsion (§3.1, the
+ * quadtree of ForceAtlas2's repulsion) is built over the bodies in Morton
+ * order.  A body moves little between two steps, so from the second step of
+ * a run on (bgv_fa2_run, bgv_layout*) the library finds that order with a
+ * sample sort whose buckets follow the previous step's order, instead of a
+ * full radix sort; both give the same order, (key, id).  The paper has no
+ * counterpart.
+ *
+ * bgv_sort_hinted sorts the pairs (keys[id], id), id in [0, K), into (key, id)
+ * order and writes them to out_keys and out_ids.  `hint` is an order of the
+ * ids (a permutation of [0, K)) that only guides the work: the closer it is
+ * to the sorted order, the more even the buckets.  keys: device, K uint64;
+ * hint: device, K uint32; out_keys/out_ids: device, K entries each, aliasing
+ * neither input nor each other (BGV_EINVAL).  0 <= K <=
+ * bgv_sort_hinted_max_keys() (4,194,304; BGV_EINVAL above).  A hint entry
+ * >= K raises BGV_DEV_BADHINT in the workspace's status word and is read as
+ * 0, and the call returns BGV_EDEVICE; a hint with a repeated id gives an
+ * unspecified order but no access outside the arrays.  Synchronises
+ * `stream`.  ws: bgv_sort_hinted_ws_size(K) bytes (0 for a K out of range),
+ * header zeroed by bgv_ws_init.
+ *
+ * bgv_set_fa2_order(1) (the default) makes ForceAtlas2 runs use the hinted
+ * sort from their second step on (for K up to the same limit); 0 makes every
+ * step use the full radix sort.  Process wide; returns the previous value
+ * (-1 and no change for other values).  A CUDA graph captured earlier keeps
+ * the method it was captured with.
+ * ---------------------------------------------------------------------- */
+int64_t bgv_sort_hinted_max_keys(void);
+size_t bgv_sort_hinted_ws_size(int64_t K);
+int bgv_sort_hinted(const uint64_t *keys, const uint32_t *hint, int64_t K, uint64_t *out_keys, uint32_t *out_ids,
+                    void *ws, size_t ws_bytes, void *stream);
+int32_t bgv_set_fa2_order(int32_t method);
 
 /* ------------------------------------------------------------------------
  * 8. Bounded waits.  Every decoupled look-back wait in the library (radix

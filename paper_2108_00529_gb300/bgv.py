@@ -20,7 +20,7 @@ if not _LIB_PATH.exists():
 _lib = C.CDLL(str(_LIB_PATH))
 
 BGV_OK, BGV_EINVAL, BGV_ENOSPC, BGV_EDEVICE, BGV_ECUDA, BGV_ELIMIT = 0, 1, 2, 3, 4, 5
-BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_TIMEOUT = 1, 2, 8
+BGV_DEV_BADEDGE, BGV_DEV_BADLABEL, BGV_DEV_TIMEOUT, BGV_DEV_BADHINT = 1, 2, 8, 16
 
 P = C.c_void_p
 i32, i64, u32, u64, sz = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_size_t
@@ -119,6 +119,10 @@ _sig("bgv_autotune_sort", C.c_int, [i64, C.POINTER(bgv_tune_report), P, sz, P])
 _sig("bgv_sort_cutoff", i64, [])
 _sig("bgv_set_sort_cutoff", i64, [i64])
 _sig("bgv_set_sort_method", i32, [i32])
+_sig("bgv_sort_hinted_max_keys", i64, [])
+_sig("bgv_sort_hinted_ws_size", sz, [i64])
+_sig("bgv_sort_hinted", C.c_int, [P, P, i64, P, P, P, sz, P])
+_sig("bgv_set_fa2_order", i32, [i32])
 _sig("bgv_set_spin_limit", i32, [i32])
 _sig("bgv_check_wait_timeout_ws_size", sz, [])
 _sig("bgv_check_wait_timeout", C.c_int, [i32, P, sz, P])
@@ -136,6 +140,7 @@ EXPORTS = ["bgv_version", "bgv_strerror", "bgv_ws_init", "bgv_status", "bgv_sket
            "bgv_fa2_ws_size_batched", "bgv_fa2_init_batched", "bgv_fa2_forces_batched", "bgv_fa2_run_batched",
            "bgv_autotune_fa2_ws_size", "bgv_autotune_fa2", "bgv_set_fa2_tune",
            "bgv_autotune_sort_ws_size", "bgv_autotune_sort", "bgv_sort_cutoff", "bgv_set_sort_cutoff", "bgv_set_sort_method",
+           "bgv_sort_hinted_max_keys", "bgv_sort_hinted_ws_size", "bgv_sort_hinted", "bgv_set_fa2_order",
            "bgv_set_spin_limit", "bgv_check_wait_timeout_ws_size", "bgv_check_wait_timeout"]
 
 
@@ -490,6 +495,26 @@ def bgv_autotune_fa2(K, nnz, csr_off, csr_adj, csr_w, mass, params, pos, ws, ws_
 
 def bgv_set_fa2_tune(att_short: int, repulse_threads: int, tail_blocks_per_sm: int):
     _chk(_lib.bgv_set_fa2_tune(att_short, repulse_threads, tail_blocks_per_sm), "bgv_set_fa2_tune")
+
+
+def bgv_sort_hinted_max_keys() -> int:
+    return int(_lib.bgv_sort_hinted_max_keys())
+
+
+def bgv_sort_hinted_ws_size(K: int) -> int:
+    return _lib.bgv_sort_hinted_ws_size(K)
+
+
+def bgv_sort_hinted(keys, hint, K, out_keys, out_ids, ws, ws_bytes=None, stream=None):
+    _chk(_lib.bgv_sort_hinted(_p(keys), _p(hint), K, _p(out_keys), _p(out_ids), _p(ws), _nbytes(ws, ws_bytes),
+                              _s(stream)), "bgv_sort_hinted")
+
+
+def bgv_set_fa2_order(method: int) -> int:
+    """1: ForceAtlas2 runs sort with the previous step's order as the hint
+    from their second step on, 0: the full radix sort every step; returns
+    the previous value."""
+    return int(_lib.bgv_set_fa2_order(method))
 
 
 def bgv_set_sort_method(method: int) -> int:

@@ -135,11 +135,12 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
     if (!use_graph || st == nullptr || iterations < 2) {
         for (int32_t t = 0; t < iterations; ++t)
             BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr,
-                            scratch, st, nullptr, t == 0, G, koff));
+                            scratch, st, nullptr, t == 0, G, koff, t > 0));
         return BGV_OK;
     }
-    // The first step runs outside the graph and builds the attraction plan;
-    // the captured step reuses it.
+    // The first step runs outside the graph, builds the attraction plan and
+    // sorts the bodies with the full radix sort; the captured step reuses the
+    // plan and takes the previous step's order as its sort hint.
     BGV_TRY(run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch,
                     st, nullptr, true, G, koff));
     if (iterations == 1) return BGV_OK;
@@ -148,7 +149,7 @@ int fa2_loop(int64_t K, int64_t nnz, const int32_t *off, const int32_t *adj, con
     BGV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const unsigned long long before = launches_issued();
     int rc = run_fa2(1, K, nnz, off, adj, w, mass, p, pos, F, Fprev, speed, nullptr, nullptr, nullptr, hdr, scratch, st,
-                     nullptr, false, G, koff);
+                     nullptr, false, G, koff, true);
     const unsigned long long per_step = launches_issued() - before;  // captured, not yet run
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (rc != BGV_OK || ce != cudaSuccess) {
@@ -766,7 +767,8 @@ int bgv_fa2_run_timed(int64_t K, int64_t nnz, const int32_t *csr_off, const int3
         }
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
         rc = run_fa2(1, K, nnz, csr_off, csr_adj, csr_w, mass, *p, pos, F, Fprev, speed, nullptr, nullptr, nullptr,
-                     header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per, t == 0);
+                     header(ws), static_cast<char *>(ws) + kHeaderBytes, st, ev + size_t(t) * per, t == 0, 1, nullptr,
+                     t > 0);
     if (rc == BGV_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = BGV_ECUDA;
     for (int32_t t = 0; t < iterations && rc == BGV_OK; ++t)
         for (int k = 0; k < kFa2Stages; ++k) {

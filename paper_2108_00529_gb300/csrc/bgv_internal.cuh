@@ -173,6 +173,8 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r);
 int64_t sort_counter_words();
 int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const int64_t *d_count, int end_bit,
                     cudaStream_t s, int *result_buffer, uint32_t *dev_status, bool counters_cleared = false);
+// The buffer pair radix_sort_high(cap, end_bit) leaves its result in.
+int radix_sort_high_result(int64_t cap, int end_bit);
 
 // Sort autotuner: times the onesweep passes at 8 and at 16 keys per thread
 // and the cooperative sort for 2^14, 2^16, ... up to max_keys; sets the
@@ -356,7 +358,13 @@ constexpr int kFa2Stages = 8;
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos, float *F, float *Fprev, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st,
-            cudaEvent_t *marks = nullptr, bool build_plan = true, int32_t G = 1, const int64_t *koff = nullptr);
+            cudaEvent_t *marks = nullptr, bool build_plan = true, int32_t G = 1, const int64_t *koff = nullptr,
+            bool hinted = false);
+// `hinted`: the scratch holds the previous step's Morton order of the same
+// bodies (the step before ran on this scratch with the same K and G), which
+// then serves as the hint of the hinted sort (when fa2_order() is 1).
+int fa2_order();
+int set_fa2_order(int method);  // 0 or 1; returns the previous method, -1 for others
 
 // Bounded-wait self checks: one block of a look-back kernel whose
 // predecessor tile never publishes (sort pass, FA2 moment pass, CSR pass).

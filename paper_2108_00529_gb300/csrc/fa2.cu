@@ -40,6 +40,7 @@
 #include <atomic>
 
 #include "bgv_internal.cuh"
+#include "hsort.cuh"
 
 namespace bgv {
 
@@ -180,6 +181,24 @@ __device__ __forceinline__ uint2 fixed_point(float2 p, float4 fr) {
 // Morton key of the body's fixed-point position in its graph's frame; in the
 // batched form the graph id sits above the 2L Morton bits, so each graph's
 // bodies stay together and form their own subtree.
+__device__ __forceinline__ unsigned long long morton_key(const float2 *__restrict__ pos,
+                                                         const float4 *__restrict__ frames,
+                                                         const int32_t *__restrict__ bgraph, int L, int64_t i) {
+    const int g = bgraph ? bgraph[i] : 0;
+    const uint2 U = fixed_point(pos[i], frames[g]);
+    const uint32_t qx = U.x >> (32 - L), qy = U.y >> (32 - L);
+    return (static_cast<unsigned long long>(g) << (2 * L)) | (spread_bits(qx) << 1) | spread_bits(qy);
+}
+
+// The same key by body id, for the hinted sort.
+struct MortonOf {
+    const float2 *pos;
+    const float4 *frames;
+    const int32_t *bgraph;
+    int L;
+    __device__ unsigned long long operator()(uint32_t id) const { return morton_key(pos, frames, bgraph, L, id); }
+};
+
 // Also clears, for the kernels after it, the step's counters (2 words), the
 // moment look-back flags and the sort's digit counters: the launches that
 // would otherwise clear them sit on the step's dependency chain.
@@ -198,10 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float2 *__restrict__ po
         if (t < n_b) clear_b[t] = 0u;
     }
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < K; i += stride) {
-        const int g = bgraph ? bgraph[i] : 0;
-        const uint2 U = fixed_point(pos[i], frames[g]);
-        const uint32_t qx = U.x >> (32 - L), qy = U.y >> (32 - L);
-        keys[i] = (static_cast<unsigned long long>(g) << (2 * L)) | (spread_bits(qx) << 1) | spread_bits(qy);
+        keys[i] = morton_key(pos, frames, bgraph, L, i);
         vals[i] = uint32_t(i);
     }
 }
@@ -1335,6 +1351,7 @@ struct Fa2Scratch {
     int32_t *rows_short, *rows_med, *rows_long;  // plan: rows by length class
     uint32_t *att_counts;  // plan: the three list lengths
     XPart *part;  // per node-kernel block: exact S and T partials
+    HsBuffers hs;  // hinted sort of the Morton keys
 };
 
 static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &s) {
@@ -1369,6 +1386,7 @@ static void carve_fa2(Carver &c, int64_t K, int64_t nnz, int32_t G, Fa2Scratch &
     s.rows_long = c.take<int32_t>(k);
     s.att_counts = c.take<uint32_t>(4);
     s.part = c.take<XPart>(2 * size_t(kMaxNodeBlocks));
+    carve_hs(c, s.hs);
 }
 
 size_t fa2_scratch_bytes(int64_t K, int64_t nnz, int32_t G) {
@@ -1475,6 +1493,16 @@ int set_fa2_tune(const Fa2Tune &t) {
     return BGV_OK;
 }
 
+// How a step after the first of a run finds the Morton order, process
+// wide: 1 (default) the hinted sort from the previous step's order, 0 the
+// full radix sort every step.  Both give the same order.
+static std::atomic<int> g_fa2_order{1};
+int fa2_order() { return g_fa2_order.load(std::memory_order_relaxed); }
+int set_fa2_order(int method) {
+    if (method != 0 && method != 1) return -1;
+    return g_fa2_order.exchange(method, std::memory_order_relaxed);
+}
+
 // A second stream per host thread and device, made on first use.
 cudaStream_t aux_stream() {
     static thread_local cudaStream_t streams[64] = {};
@@ -1519,7 +1547,8 @@ struct ForkJoin {
 static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj,
                         const uint32_t *csr_w, const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f,
                         float *Fprev_f, double *speed, float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch,
-                        cudaStream_t st, cudaEvent_t *marks, bool build_plan, int32_t G, const int64_t *koff) {
+                        cudaStream_t st, cudaEvent_t *marks, bool build_plan, int32_t G, const int64_t *koff,
+                        bool hinted) {
     if (K <= 0) return BGV_OK;
     const bool batched = G > 1;
     if (!fa2_batch_fits(G, p.max_depth)) return BGV_EINVAL;
@@ -1592,15 +1621,38 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
     else
         note_launch(), k_frame<<<frame_blocks(), kThreads, 0, st>>>(pos, K, s.frame_part, s.frame, &hdr->bbox_ticket);
     BGV_TRY(launch_status());
-    const int gk = grid_for(K, kThreads, sm_count() * 16);
     const int64_t mom_tiles = (K + kMomTile - 1) / kMomTile;
-    note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
-                                                   &hdr->interactions, s.mom_flags, mom_tiles + 2, s.sort.counts,
-                                                   sort_counter_words());
-    BGV_TRY(launch_status());
-    BGV_TRY(mark(1));
-    int res = 0;
-    BGV_TRY(radix_sort_high(s.sort, s.runfix, K, nullptr, 2 * L + gbits, st, &res, &hdr->status, true));
+    // the sorted order lands in the buffer pair the radix sort ends in, so
+    // the next iteration finds its hint there whichever sort made it
+    const int res = radix_sort_high_result(K, 2 * L + gbits);
+    if (hinted && fa2_order() == 1 && K <= hs_max_keys()) {
+        // the previous iteration's sorted ids are the hint; the sort also
+        // clears the step counters and the moment flags, as k_keys does
+        const MortonOf key_of{pos, s.frame, s.bgraph, L};
+        HsClears clr;
+        clr.u64 = &hdr->interactions;  // interactions, tree_nodes
+        clr.n_u64 = 2;
+        clr.u32 = s.mom_flags;
+        clr.n_u32 = mom_tiles + 2;
+        const uint32_t *hint = s.sort.vals[res];
+        BGV_TRY(hinted_sort_samples(key_of, hint, K, s.hs, &hdr->status, st, clr));
+        BGV_TRY(mark(1));
+        // the pre-order arrays are free until k_preorder: the buckets' slots
+        unsigned long long *slot_key = reinterpret_cast<unsigned long long *>(s.geo);
+        uint32_t *slot_id = reinterpret_cast<uint32_t *>(slot_key + K);
+        BGV_TRY(hinted_sort_place(key_of, hint, K, s.hs, s.sort.keys[res ^ 1], s.sort.vals[res ^ 1], slot_key, slot_id,
+                                  s.sort.keys[res], s.sort.vals[res], &hdr->status, st));
+    } else {
+        const int gk = grid_for(K, kThreads, sm_count() * 16);
+        note_launch(), k_keys<<<gk, kThreads, 0, st>>>(pos, K, s.frame, s.bgraph, L, s.sort.keys[0], s.sort.vals[0],
+                                                       &hdr->interactions, s.mom_flags, mom_tiles + 2, s.sort.counts,
+                                                       sort_counter_words());
+        BGV_TRY(launch_status());
+        BGV_TRY(mark(1));
+        int got = 0;
+        BGV_TRY(radix_sort_high(s.sort, s.runfix, K, nullptr, 2 * L + gbits, st, &got, &hdr->status, true));
+        if (got != res) return BGV_EINVAL;  // radix_sort_high_result disagrees with the sort
+    }
     BGV_TRY(mark(2));
     {
         note_launch(), k_gather_moments<<<unsigned(mom_tiles), kThreads, 0, st>>>(
@@ -1679,7 +1731,7 @@ static int run_fa2_body(int mode, int64_t K, int64_t nnz, const int32_t *csr_off
 int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *csr_adj, const uint32_t *csr_w,
             const uint32_t *mass, const bgv_fa2_params &p, float *pos_f, float *F_f, float *Fprev_f, double *speed,
             float *Fr, float *Fa, float *Fg, WsHeader *hdr, void *scratch, cudaStream_t st, cudaEvent_t *marks,
-            bool build_plan, int32_t G, const int64_t *koff) {
+            bool build_plan, int32_t G, const int64_t *koff, bool hinted) {
     if (K <= 0) return BGV_OK;
     cudaStream_t hp = priority_stream();
     ForkJoin ev;
@@ -1687,7 +1739,7 @@ int run_fa2(int mode, int64_t K, int64_t nnz, const int32_t *csr_off, const int3
     BGV_CUDA(cudaEventRecord(ev.fork, st));
     BGV_CUDA(cudaStreamWaitEvent(hp, ev.fork, 0));
     const int rc = run_fa2_body(mode, K, nnz, csr_off, csr_adj, csr_w, mass, p, pos_f, F_f, Fprev_f, speed, Fr, Fa, Fg,
-                                hdr, scratch, hp, marks, build_plan, G, koff);
+                                hdr, scratch, hp, marks, build_plan, G, koff, hinted);
     BGV_CUDA(cudaEventRecord(ev.join, hp));
     BGV_CUDA(cudaStreamWaitEvent(st, ev.join, 0));
     return rc;

@@ -1010,6 +1010,12 @@ void carve_run_fix(Carver &c, int64_t cap, RunFixBuffers &r) {
 // the cooperative sort
 int64_t sort_counter_words() { return int64_t(kMaxPasses) * kBins + kMaxPasses + 4; }
 
+int radix_sort_high_result(int64_t cap, int end_bit) {
+    const int passes = (end_bit + 7) / 8;
+    if (end_bit <= kLowBits || passes > kMaxPasses || cap >= (int64_t(1) << 32)) return passes & 1;
+    return (passes - kLowBits / 8) & 1;
+}
+
 int radix_sort_high(SortBuffers &b, const RunFixBuffers &r, int64_t cap, const int64_t *d_count, int end_bit,
                     cudaStream_t s, int *result_buffer, uint32_t *dev_status, bool counters_cleared) {
     const int passes = (end_bit + 7) / 8;
