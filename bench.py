@@ -450,7 +450,9 @@ def gpu_arm(args, dist: Dist):
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "fa2_stage_us_per_iteration": {k: round(1000 * v, 2) for k, v in fa2_stage_ms.items()},
         "fa2_stage_note": f"CUDA events at the stage boundaries of the last {sampled} iterations of every timed step "
-                          "(launched one by one; the others replay a captured step)",
+                          "(launched one by one; the others replay a captured step); the first of them sorts the "
+                          "bodies with the radix sort, the rest with the hinted sort, as every run's steps after "
+                          "its first do",
         "roofline": roofline,
         "edge_roofline": edge_roofline,
         "e2e": ({"value": round(aggregate_throughput(m, dist.world, e2e_ms), 1), "unit": "edges/s",
