@@ -531,7 +531,8 @@ int32_t bgv_set_sort_method(int32_t method);
  * ids (a permutation of [0, K)) that only guides the work: the closer it is
  * to the sorted order, the more even the buckets.  keys: device, K uint64;
  * hint: device, K uint32; out_keys/out_ids: device, K entries each, aliasing
- * neither input nor each other (BGV_EINVAL).  0 <= K <=
+ * neither input nor each other; keys and out_keys 8-byte aligned, hint and
+ * out_ids 4-byte aligned, ws 256-byte aligned (BGV_EINVAL otherwise).  0 <= K <=
  * bgv_sort_hinted_max_keys() (4,194,304; BGV_EINVAL above).  A hint entry
  * >= K raises BGV_DEV_BADHINT in the workspace's status word and is read as
  * 0, and the call returns BGV_EDEVICE; a hint with a repeated id gives an

@@ -25,6 +25,8 @@ void carve_hs_ws(Carver &c, int64_t K, HsWs &w) {
     w.slot_id = c.take<uint32_t>(k);
 }
 
+bool aligned_to(const void *p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
     const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
     return x < y + nb && y < x + na;
@@ -49,10 +51,12 @@ size_t bgv_sort_hinted_ws_size(int64_t K) {
 
 int bgv_sort_hinted(const uint64_t *keys, const uint32_t *hint, int64_t K, uint64_t *out_keys, uint32_t *out_ids,
                     void *ws, size_t ws_bytes, void *stream) {
-    if (K < 0 || K > hs_max_keys() || !ws) return BGV_EINVAL;
+    if (K < 0 || K > hs_max_keys() || !ws || !aligned_to(ws, kAlign)) return BGV_EINVAL;
     if (ws_bytes < bgv_sort_hinted_ws_size(K)) return BGV_ENOSPC;
     if (K == 0) return BGV_OK;
     if (!keys || !hint || !out_keys || !out_ids) return BGV_EINVAL;
+    if (!aligned_to(keys, 8) || !aligned_to(out_keys, 8) || !aligned_to(hint, 4) || !aligned_to(out_ids, 4))
+        return BGV_EINVAL;
     const size_t kb = sizeof(uint64_t) * size_t(K), ib = sizeof(uint32_t) * size_t(K);
     if (overlaps(out_keys, kb, keys, kb) || overlaps(out_keys, kb, hint, ib) || overlaps(out_ids, ib, keys, kb) ||
         overlaps(out_ids, ib, hint, ib) || overlaps(out_keys, kb, out_ids, ib))

@@ -117,6 +117,22 @@ def test_hinted_sort_at_the_size_limit_and_above():
         _sort(np.zeros(K + 1, np.uint64), np.arange(K + 1, dtype=np.uint32))
 
 
+def test_bad_arguments_are_refused_on_the_host():
+    K = 3000
+    keys = G.dev(np.arange(K, dtype=np.uint64))
+    hint = G.dev(np.arange(K, dtype=np.uint32))
+    ok, oi = G.empty(K + 1, np.uint64), G.empty(K, np.uint32)
+    ws = B.alloc_ws(B.bgv_sort_hinted_ws_size(K))
+    lib, P = B._lib, B._p
+    n = B.bgv_sort_hinted_ws_size(K)
+    # misaligned output, output aliasing the keys, a short workspace, a null hint
+    assert lib.bgv_sort_hinted(P(keys), P(hint), K, ok.data_ptr() + 4, P(oi), P(ws), n, None) == B.BGV_EINVAL
+    assert lib.bgv_sort_hinted(P(keys), P(hint), K, P(keys), P(oi), P(ws), n, None) == B.BGV_EINVAL
+    assert lib.bgv_sort_hinted(P(keys), P(hint), K, P(ok), P(oi), P(ws), n - 256, None) == B.BGV_ENOSPC
+    assert lib.bgv_sort_hinted(P(keys), None, K, P(ok), P(oi), P(ws), n, None) == B.BGV_EINVAL
+    assert B.bgv_status(ws) == 0
+
+
 def test_hint_entry_out_of_range_is_reported():
     K = 5000
     keys = np.random.default_rng(1).integers(0, 1 << 40, K, dtype=np.uint64)
