@@ -116,3 +116,30 @@ def test_batched_host_validation(lib):
                                  C.c_void_p(256), 1 << 30, None) == bgv.BGV_EINVAL
     # more graphs need more workspace (frames, speeds, per-body graph ids)
     assert bgv.bgv_fa2_ws_size_batched(1, 1000, 10) <= bgv.bgv_fa2_ws_size_batched(100, 1000, 10)
+
+
+def test_hinted_sort_queries_and_host_validation(lib):
+    # Workspace queries, the order setting and every refusal happen on the
+    # host, before any CUDA call.
+    from paper_2108_00529_gb300 import bgv
+    L = bgv._lib
+    kmax = bgv.bgv_sort_hinted_max_keys()
+    assert kmax == 4096 * 1024
+    a, b = bgv.bgv_sort_hinted_ws_size(0), bgv.bgv_sort_hinted_ws_size(kmax)
+    assert 256 <= a < b and b % 256 == 0
+    assert bgv.bgv_sort_hinted_ws_size(kmax + 1) == 0 and bgv.bgv_sort_hinted_ws_size(-1) == 0
+    K = 1000
+    n = bgv.bgv_sort_hinted_ws_size(K)
+    ws = C.c_void_p(1 << 20)  # never dereferenced: validation fails first
+    keys, hint, ok, oi = (C.c_void_p(v) for v in (1 << 24, 1 << 25, 1 << 26, 1 << 27))
+    assert L.bgv_sort_hinted(keys, hint, 0, ok, oi, ws, n, None) == bgv.BGV_OK  # nothing to sort
+    assert L.bgv_sort_hinted(keys, hint, K, ok, oi, C.c_void_p((1 << 20) + 8), n, None) == bgv.BGV_EINVAL
+    assert L.bgv_sort_hinted(keys, hint, kmax + 1, ok, oi, ws, 1 << 40, None) == bgv.BGV_EINVAL
+    assert L.bgv_sort_hinted(keys, hint, K, ok, oi, ws, n - 256, None) == bgv.BGV_ENOSPC
+    assert L.bgv_sort_hinted(keys, None, K, ok, oi, ws, n, None) == bgv.BGV_EINVAL
+    assert L.bgv_sort_hinted(C.c_void_p((1 << 24) + 4), hint, K, ok, oi, ws, n, None) == bgv.BGV_EINVAL
+    assert L.bgv_sort_hinted(keys, hint, K, C.c_void_p((1 << 24) + 8), oi, ws, n, None) == bgv.BGV_EINVAL  # overlap
+    prev = bgv.bgv_set_fa2_order(0)
+    assert prev in (0, 1)
+    assert bgv.bgv_set_fa2_order(2) == -1
+    assert bgv.bgv_set_fa2_order(prev) == 0
