@@ -5,9 +5,9 @@
 // iteration's Morton order of the bodies is such a hint for the next one:
 // on the 3.2 M-body rmat22x supergraph, 98.3 % (first iterations) to 99.8 %
 // (iteration 500) of the bodies end within 4,096 places of where the
-// previous order had them.  The LSD radix
-// sort ignores that; this sort uses it to cut the global passes to two
-// (count, scatter) and to sort the rest in shared memory.
+// previous order had them.  The LSD radix sort ignores that; this sort uses
+// it to cut the global passes to two (count, scatter) and to sort the rest
+// in shared memory, with kernels that need no grid-wide residency.
 //
 // Method: a sample sort whose buckets follow the hint.
 //   1. Samples: the ids at ns evenly spaced places of the hint and their
