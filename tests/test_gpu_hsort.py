@@ -182,6 +182,32 @@ def test_fa2_runs_equal_with_either_sort(use_graph):
     assert sa.interactions_total == sb.interactions_total and sa.tree_nodes == sb.tree_nodes
 
 
+@pytest.mark.parametrize("blocks", [12, 50])
+def test_a_hinted_step_matches_the_oracle(blocks):
+    # A run's second step sorts with the hinted sort.  Its input state is the
+    # state after the run's first step, which a one-step run reproduces (the
+    # steps are deterministic); the oracle takes the same step from there.
+    sg = _sg(blocks, 6)
+    K = sg["K"]
+    args = (sg["mass"], sg["csr_off"], sg["csr_adj"], sg["csr_w"], FA2Params())
+    warm = G.Fa2Device(oracle.fa2_init(K, 8), *args)
+    warm.run(6, False)
+    pos0, _, Fprev0, speed0 = warm.state()
+    start = dict(Fprev=Fprev0.astype(np.float32), speed=speed0)
+    one = G.Fa2Device(pos0.astype(np.float32), *args, **start)
+    one.run(1, False)
+    pos1, _, Fprev1, speed1 = one.state()
+    two = G.Fa2Device(pos0.astype(np.float32), *args, **start)
+    two.run(2, False)
+    st = oracle.FA2State(pos1.astype(np.float32), Fprev1.astype(np.float32), speed1)
+    r0 = oracle.fa2_step(st, sg["csr_off"], sg["csr_adj"], sg["csr_w"], sg["mass"], FA2Params())
+    _, F2, _, speed2 = two.state()
+    stats = two.stats()
+    assert stats.status == 0 and stats.interactions == r0["interactions"]
+    assert G.rel_err(F2, r0["F"]) <= 1e-3
+    assert abs(speed2 - st.speed) <= 1e-3 * st.speed
+
+
 def test_fa2_run_with_coincident_bodies_equal_with_either_sort():
     # many bodies on one point: long runs of equal keys, split across buckets
     sg = _sg(12, 4)
