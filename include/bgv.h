@@ -339,8 +339,10 @@ int bgv_fa2_run(int64_t K, int64_t nnz, const int32_t *csr_off, const int32_t *c
  * BGV_FA2_STAGES stages of each step (on the library stream that runs the
  * main chain); synchronises `stream` and returns in stage_ms[BGV_FA2_STAGES]
  * the summed milliseconds per stage:
- *   0 frame + Morton keys, 1 radix sort, 2 gather into Morton order and
- *   moment prefix sums, 3 radix tree and quadtree cells, 4 pre-order layout,
+ *   0 frame + Morton keys (from the second step on: frame + the hinted
+ *   sort's samples), 1 sort (the radix sort in the first step, the rest of
+ *   the hinted sort in the others), 2 gather into Morton order and moment
+ *   prefix sums, 3 radix tree and quadtree cells, 4 pre-order layout,
  *   5 Barnes-Hut repulsion, 6 the wait for the attraction (which runs beside
  *   stages 0-5), 7 total force, swing/traction, speed and displacement (one
  *   persistent kernel).
